@@ -1,0 +1,205 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) phase-field lattice Boltzmann library.
+ *
+ * The library advances the phase-field two-phase lattice Boltzmann model of
+ * Yuan, Chai, Wang and Shi (arXiv:1902.08933), Sec. 3: the order-parameter
+ * distribution h_i (Cahn-Hilliard, Eqs. 10, 11, 14, 18) and the flow
+ * distribution g_i with mass source and force terms (Eqs. 24, 33, 34, 27a), with
+ * the pressure of Eq. 28 (or Eq. 29), the isotropic finite differences of Eq. 30,
+ * the chemical potential of Eq. 8, and the surface-tension, buoyancy and source
+ * forcing of Secs. 3.1, 4.2 and 4.4, on a D2Q9 lattice (Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an lbm_status and never aborts the process. After an
+ *    error, lbm_last_error() gives a one-line reason.
+ *  - Device memory is allocated and owned by the context (lbm_create) and
+ *    released by lbm_destroy. Host buffers passed in are owned by the caller,
+ *    read or written during the call only, and never retained.
+ *  - Work is queued on the context's CUDA stream (the caller's stream given to
+ *    lbm_create, or a stream the library creates when that is NULL). Calls that
+ *    return host data synchronise that stream.
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3. phi = 1 is phase A, phi = 0 is
+ *    phase B (Sec. 3.1). x is periodic; y is periodic or closed by halfway
+ *    bounce-back walls at y = -1/2 and y = ny - 1/2 (Sec. 4.3).
+ *  - Grid arrays are row-major, a[y * nx + x].
+ *  - Not thread-safe per context: one host thread at a time may use a context.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,      /* invalid argument or parameter set                          */
+    LBM_ENOMEM = 2,      /* device or host allocation failed                           */
+    LBM_ECUDA = 3,       /* a CUDA runtime call or kernel failed                       */
+    LBM_ENONFINITE = 4,  /* diagnostics found a non-finite population                  */
+    LBM_ETIMEOUT = 5,    /* reserved for bounded device waits                          */
+    LBM_ESTATE = 6,      /* call out of order (e.g. step before init)                  */
+    LBM_EIO = 7          /* checkpoint file could not be read or written               */
+} lbm_status;
+
+/* Boundary in y (x is always periodic). */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
+/* Incompressible model (S1 = 0) or quasi-incompressible model
+ * (S1 = -gamma div(M grad mu), Sec. 3.2.1). */
+enum { LBM_IM = 0, LBM_QIM = 1 };
+/* Pressure: Eq. 28 with the simplified G_0 printed after Eq. 34; Eq. 28 with
+ * G_0 from Eq. 34 at i = 0 (equal to Eq. 28aa); or the previous scheme, Eq. 29. */
+enum { LBM_P_MODIFIED_PRINTED = 0, LBM_P_MODIFIED_LITERAL = 1, LBM_P_PREVIOUS = 2 };
+/* Surface tension: F_s = mu grad(phi) (Sec. 3.1) or -phi grad(mu) (Sec. 4.2). */
+enum { LBM_FS_MU_GRADPHI = 0, LBM_FS_PHI_GRADMU = 1 };
+/* Viscosity: inverse-linear 1/nu in phi (Sec. 3.2.2), or step dynamic viscosity
+ * mu_A (phi >= 1/2) / mu_B (Sec. 4.3). */
+enum { LBM_VISC_INV_LINEAR = 0, LBM_VISC_STEP = 1 };
+
+/* Storage and arithmetic form of a context.
+ *  LBM_F64      populations and auxiliary fields in FP64, FP64 arithmetic.
+ *  LBM_F32      populations and auxiliary fields in FP32, FP32 arithmetic.
+ *  LBM_F32_G16  FP32 arithmetic; h in FP32; g in FP16, scaled by a power of
+ *               two chosen per instance (g is stored shifted: g_0 - rho_0).
+ *  LBM_F32_H16  FP32 arithmetic; g as in LBM_F32_G16; h_1..h_8 in FP16 and h_0
+ *               in FP32, with h_0 stored as phi* - sum of the rounded h_1..h_8 so
+ *               that rounding cannot create or destroy phi.                          */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_G16 = 2, LBM_F32_H16 = 3 };
+
+/* Field selection bits for lbm_get_fields*: outputs are written field-major in
+ * this bit order, each field nx*ny doubles. P is the Laplace-law pressure of
+ * Sec. 4.2, P = p_0 - kappa phi lap(phi) + kappa |grad phi|^2 / 2 + p. */
+enum {
+    LBM_FIELD_PHI = 1, LBM_FIELD_UX = 2, LBM_FIELD_UY = 4, LBM_FIELD_P = 8,
+    LBM_FIELD_RHO = 16, LBM_FIELD_MU = 32, LBM_FIELD_PLAP = 64
+};
+
+/* Parameters of one simulation instance (Sec. 3; values per experiment in Sec. 4).
+ * Validation (lbm_create, lbm_validate_params): nx >= 3, ny >= 3, nx*ny < 2^31,
+ * rho_A, rho_B, nu_A, nu_B, W > 0, sigma >= 0, mobility >= 0, tau_h > 1/2,
+ * every enum in range; all values finite. */
+typedef struct lbm_params {
+    int32_t nx, ny;
+    int32_t bc_y;             /* LBM_BC_*                                                */
+    int32_t variant;          /* LBM_IM / LBM_QIM                                         */
+    int32_t pressure_scheme;  /* LBM_P_*                                                  */
+    int32_t surface_force;    /* LBM_FS_*                                                 */
+    int32_t viscosity_model;  /* LBM_VISC_*                                               */
+    int32_t reserved;         /* must be 0                                                */
+    double rho_A, rho_B;      /* densities of phase A (phi = 1) and phase B (phi = 0)    */
+    double nu_A, nu_B;        /* kinematic viscosities; tau_g = nu / c_s^2 + 1/2         */
+    double sigma, W;          /* surface tension, interface width: beta = 12 sigma / W,
+                                 kappa = 3 sigma W / 2 (Eqs. 6-7)                         */
+    double tau_h;             /* relaxation time of h (Eq. 10)                            */
+    double mobility;          /* M_phi; eta = M_phi / (c_s^2 (tau_h - 1/2)) (Eq. 17)      */
+    double force_x, force_y;  /* uniform body-force density                               */
+    double gravity;           /* buoyancy F_b,y = -(rho - rho_A) g (Sec. 4.4)             */
+} lbm_params;
+
+/* FP64 diagnostics of one instance at the current time (reductions on the GPU
+ * in FP64, in a fixed order, so repeated calls give identical results). */
+typedef struct lbm_diag {
+    double sum_phi, sum_rho, kinetic_energy, max_u;
+    double centroid_A_x, centroid_A_y;   /* phi-weighted centroid                       */
+    double centroid_B_x, centroid_B_y;   /* (1 - phi)-weighted centroid                 */
+    double mass_A, mass_B;               /* sum phi, sum (1 - phi)                      */
+    double P_bulk_A, P_bulk_B;           /* mean Laplace-law pressure P over cells with
+                                            phi > 1 - 1e-3 (bulk A) and phi < 1e-3 (bulk B) */
+    double n_bulk_A, n_bulk_B;           /* cell counts of those bulks                  */
+    int32_t nonfinite;                   /* 1 if any population is NaN or infinite      */
+    int32_t reserved;
+    int64_t time;                        /* steps taken since lbm_init                  */
+} lbm_diag;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Checks one parameter block on the host only (no CUDA call). */
+lbm_status lbm_validate_params(const lbm_params* params);
+
+/* Creates a context holding n_instances independent simulations (one parameter
+ * block each, sizes may differ), all advanced together by lbm_step.
+ * params:      host array of n_instances blocks, copied.
+ * precision:   LBM_F64 / LBM_F32 / LBM_F32_G16 / LBM_F32_H16.
+ * cuda_stream: a cudaStream_t to queue work on, or NULL for a library stream.
+ * out:         receives the context; *out is NULL on failure.
+ * Errors: LBM_EINVAL (bad arguments; *out stays NULL and no CUDA call is made),
+ * LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(const lbm_params* params, int n_instances, int precision,
+                      void* cuda_stream, lbm_ctx** out);
+
+/* Sets the initial state of one instance from the order parameter phi0 (host
+ * array of nx*ny doubles, copied): u = 0, p = 0, mu_0 from Eq. 8,
+ * h = h^eq(phi0, mu_0, u = 0) (Eq. 11), g = g^eq(p = 0, u = 0) (Eq. 33), and the
+ * stored phi*u of the previous step = 0. Resets the instance's time to 0.
+ * Errors: LBM_EINVAL (bad instance or NULL), LBM_ECUDA. */
+lbm_status lbm_init(lbm_ctx* ctx, int instance, const double* phi0_host);
+
+/* As lbm_init, with phi0 already in device memory (nx*ny doubles, caller-owned;
+ * read on the context's stream before the call's work completes). */
+lbm_status lbm_init_device(lbm_ctx* ctx, int instance, const double* phi0_device);
+
+/* Advances every instance by nsteps time steps (one step = collision of h and g
+ * with all forcing, then streaming: Eqs. 10 and 24). Asynchronous: returns once
+ * the work is queued. Returns an error left by earlier asynchronous work
+ * (LBM_ECUDA). nsteps >= 0; every instance must have been initialised (else
+ * LBM_ESTATE). */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Macroscopic fields of one instance at the current time, computed from the
+ * current populations exactly as the next step's macroscopic stage would
+ * (phi by Eq. 18, u by Eq. 27a, p by Eq. 28/29 with grad p from the previous
+ * step's p). mask: LBM_FIELD_* bits; host_out: caller-owned, popcount(mask) *
+ * nx * ny doubles, written field-major in bit order. Synchronises the stream. */
+lbm_status lbm_get_fields(lbm_ctx* ctx, int instance, unsigned mask, double* host_out);
+
+/* As lbm_get_fields into caller-owned device memory (asynchronous, on the
+ * context's stream). */
+lbm_status lbm_get_fields_device(lbm_ctx* ctx, int instance, unsigned mask, double* dev_out);
+
+/* FP64 diagnostics of one instance (see lbm_diag). Synchronises the stream.
+ * Returns LBM_ENONFINITE (with *out filled) if a population is not finite. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, int instance, lbm_diag* out);
+
+/* Raw populations of one instance, converted to FP64 (debugging and tests):
+ * host_h and host_g receive 9*nx*ny doubles each (plane i at i*nx*ny), g with
+ * g_0 - rho_0 (rho_0 = 0). Either pointer may be NULL. Synchronises. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, int instance, double* host_h, double* host_g);
+
+/* Checkpoint: writes / reads the complete state (populations, stored phi*u and
+ * p of the previous step, time, parameters) as a little-endian binary file
+ * with a header. lbm_load requires a context created with the same parameters
+ * and precision. Errors: LBM_EIO, LBM_EINVAL. */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Launch shape of the fused step: columns per thread block (strip width) and
+ * rows per block. tile_x in {32, 64, 128, 256}; rows >= 1. 0 selects the
+ * built-in choice. Takes effect at the next lbm_step. */
+lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
+
+/* Times the candidate launch shapes on the current state (the state is saved
+ * and restored around the trials) and keeps the fastest. best_tile_x / best_rows
+ * may be NULL. Synchronises. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int* best_tile_x, int* best_rows);
+
+/* Kernel launches queued by one lbm_step(1) (for accounting). */
+int lbm_launches_per_step(const lbm_ctx* ctx);
+
+/* Steps taken by an instance since its lbm_init. */
+int64_t lbm_time(const lbm_ctx* ctx, int instance);
+
+/* Waits for all queued work. Returns LBM_ECUDA if it failed. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Last error message of the context ("" if none); valid until the next call. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Releases the context and all its device memory. NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

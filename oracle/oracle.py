@@ -1,0 +1,263 @@
+"""ctypes binding of the plain FP64 CPU oracle (``oracle.c``).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+legs of ``bench.py`` may import this module. It shares nothing with the CUDA
+path; the only thing both sides take in common is the seeded input recipe of
+``paper_1902_08933_gb300.workloads`` (parameter dictionaries and initial order
+parameter fields), which holds none of the method's arithmetic.
+
+Arrays: float64, C-contiguous, grid arrays shaped (ny, nx), population arrays
+shaped (9, ny, nx) in the D2Q9 order of Sec. 2.2 of arXiv:1902.08933.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+HDR = os.path.join(HERE, "oracle.h")
+LIB = os.path.join(HERE, "liboracle.so")
+
+_lock = threading.Lock()
+_lib = None
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``orc_params`` in oracle.h (field order matters)."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls_y", ctypes.c_int),
+        ("qim", ctypes.c_int), ("pressure", ctypes.c_int), ("surface_force", ctypes.c_int),
+        ("viscosity", ctypes.c_int),
+        ("rho_A", ctypes.c_double), ("rho_B", ctypes.c_double),
+        ("nu_A", ctypes.c_double), ("nu_B", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("W", ctypes.c_double),
+        ("tau_h", ctypes.c_double), ("M", ctypes.c_double),
+        ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
+        ("gravity", ctypes.c_double), ("rho0", ctypes.c_double),
+    ]
+
+
+class Derived(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("eta", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "sum_phi", "sum_rho", "kinetic_energy", "max_u",
+        "centroid_A_x", "centroid_A_y", "centroid_B_x", "centroid_B_y",
+        "mass_A", "mass_B", "P_bulk_A", "P_bulk_B", "n_bulk_A", "n_bulk_B")] + [
+        ("nonfinite", ctypes.c_int)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (FP contraction off, so a*b+c rounds twice
+    exactly as written). Rebuilds when the sources are newer than the library."""
+    with _lock:
+        stale = (not os.path.exists(LIB) or
+                 os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+        if force or stale:
+            tmp = LIB + ".tmp.%d" % os.getpid()
+            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                   "-shared", "-std=c11", SRC, "-o", tmp, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        P = ctypes.POINTER(Params)
+        L.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  _DP, ctypes.POINTER(ctypes.c_int)]
+        L.orc_derive.argtypes = [P, ctypes.POINTER(Derived)]
+        L.orc_s.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_s.restype = ctypes.c_double
+        L.orc_geq.argtypes = [ctypes.c_double] * 5 + [_DP]
+        L.orc_heq.argtypes = [ctypes.c_double] * 5 + [_DP]
+        L.orc_force_dist.argtypes = [ctypes.c_double] * 9 + [_DP]
+        L.orc_G0_printed.argtypes = [ctypes.c_double] * 8
+        L.orc_G0_printed.restype = ctypes.c_double
+        L.orc_source_R.argtypes = [ctypes.c_double] * 3 + [_DP]
+        L.orc_pressure.argtypes = [ctypes.c_int, _DP] + [ctypes.c_double] * 6
+        L.orc_pressure.restype = ctypes.c_double
+        L.orc_tau_g.argtypes = [P, ctypes.c_double, ctypes.c_double]
+        L.orc_tau_g.restype = ctypes.c_double
+        L.orc_grad.argtypes = [P, _DP, _DP, _DP]
+        L.orc_lap.argtypes = [P, _DP, _DP]
+        L.orc_stream.argtypes = [P, _DP, _DP]
+        L.orc_init.argtypes = [P, _DP, _DP, _DP, _DP, _DP]
+        L.orc_step.argtypes = [P, _DP, _DP, _DP, _DP, ctypes.c_int]
+        L.orc_fields.argtypes = [P, _DP, _DP, _DP] + [_DP] * 7
+        L.orc_diagnostics.argtypes = [P, _DP, _DP, _DP, ctypes.POINTER(Diag)]
+        L.orc_layered_ux.argtypes = [ctypes.c_double] * 5
+        L.orc_layered_ux.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+_INT_KEYS = ("nx", "ny", "walls_y", "qim", "pressure", "surface_force", "viscosity")
+_DBL_KEYS = ("rho_A", "rho_B", "nu_A", "nu_B", "sigma", "W", "tau_h", "M",
+             "force_x", "force_y", "gravity", "rho0")
+
+
+def params(cfg: dict, **over) -> Params:
+    """Build ``orc_params`` from a workload dictionary (missing keys default to 0)."""
+    d = dict(cfg)
+    d.update(over)
+    P = Params()
+    for k in _INT_KEYS:
+        setattr(P, k, int(d.get(k, 0)))
+    for k in _DBL_KEYS:
+        setattr(P, k, float(d.get(k, 0.0)))
+    return P
+
+
+# ---------------------------------------------------------------- building blocks
+def lattice():
+    L = lib()
+    cx = (ctypes.c_int * 9)()
+    cy = (ctypes.c_int * 9)()
+    w = (ctypes.c_double * 9)()
+    op = (ctypes.c_int * 9)()
+    L.orc_lattice(cx, cy, w, op)
+    return np.array(cx[:]), np.array(cy[:]), np.array(w[:]), np.array(op[:])
+
+
+def derive(P: Params) -> Derived:
+    D = Derived()
+    if lib().orc_derive(ctypes.byref(P), ctypes.byref(D)):
+        raise ValueError("invalid parameters")
+    return D
+
+
+def s(i, ux, uy):
+    return lib().orc_s(i, ux, uy)
+
+
+def geq(p, rho, ux, uy, rho0=0.0):
+    out = np.zeros(9)
+    lib().orc_geq(p, rho, ux, uy, rho0, _ptr(out))
+    return out
+
+
+def heq(phi, mu, eta, ux, uy):
+    out = np.zeros(9)
+    lib().orc_heq(phi, mu, eta, ux, uy, _ptr(out))
+    return out
+
+
+def force_dist(S, rho, S1, Fx, Fy, Ftx, Fty, ux, uy):
+    out = np.zeros(9)
+    lib().orc_force_dist(S, rho, S1, Fx, Fy, Ftx, Fty, ux, uy, _ptr(out))
+    return out
+
+
+def G0_printed(rho, S1, Fx, Fy, dpx, dpy, ux, uy):
+    return lib().orc_G0_printed(rho, S1, Fx, Fy, dpx, dpy, ux, uy)
+
+
+def source_R(tau_h, dx, dy):
+    out = np.zeros(9)
+    lib().orc_source_R(tau_h, dx, dy, _ptr(out))
+    return out
+
+
+def pressure(scheme, g, S, rho, ux, uy, tau_g, G0):
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return lib().orc_pressure(scheme, _ptr(g), S, rho, ux, uy, tau_g, G0)
+
+
+def tau_g(P: Params, phi, rho):
+    return lib().orc_tau_g(ctypes.byref(P), phi, rho)
+
+
+def grad(P: Params, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    gx = np.zeros_like(f)
+    gy = np.zeros_like(f)
+    lib().orc_grad(ctypes.byref(P), _ptr(f), _ptr(gx), _ptr(gy))
+    return gx, gy
+
+
+def lap(P: Params, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros_like(f)
+    lib().orc_lap(ctypes.byref(P), _ptr(f), _ptr(out))
+    return out
+
+
+def stream(P: Params, post):
+    post = np.ascontiguousarray(post, dtype=np.float64)
+    pre = np.zeros_like(post)
+    lib().orc_stream(ctypes.byref(P), _ptr(post), _ptr(pre))
+    return pre
+
+
+def layered_ux(y, hh, G, mu_up, mu_down):
+    return lib().orc_layered_ux(y, hh, G, mu_up, mu_down)
+
+
+# ---------------------------------------------------------------- whole grid
+def init(P: Params, phi0) -> dict:
+    ny, nx = P.ny, P.nx
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(ny, nx)
+    st = {"h": np.zeros((9, ny, nx)), "g": np.zeros((9, ny, nx)),
+          "phiu_prev": np.zeros((2, ny, nx)), "p_prev": np.zeros((ny, nx))}
+    rc = lib().orc_init(ctypes.byref(P), _ptr(phi0), _ptr(st["h"]), _ptr(st["g"]),
+                        _ptr(st["phiu_prev"]), _ptr(st["p_prev"]))
+    if rc:
+        raise ValueError("orc_init failed (%d)" % rc)
+    return st
+
+
+def step(P: Params, st: dict, n: int) -> dict:
+    rc = lib().orc_step(ctypes.byref(P), _ptr(st["h"]), _ptr(st["g"]),
+                        _ptr(st["phiu_prev"]), _ptr(st["p_prev"]), int(n))
+    if rc:
+        raise ValueError("orc_step failed (%d)" % rc)
+    return st
+
+
+def fields(P: Params, st: dict) -> dict:
+    ny, nx = P.ny, P.nx
+    out = {k: np.zeros((ny, nx)) for k in ("phi", "ux", "uy", "p", "rho", "mu", "P")}
+    rc = lib().orc_fields(ctypes.byref(P), _ptr(st["h"]), _ptr(st["g"]), _ptr(st["p_prev"]),
+                          *[_ptr(out[k]) for k in ("phi", "ux", "uy", "p", "rho", "mu", "P")])
+    if rc:
+        raise ValueError("orc_fields failed (%d)" % rc)
+    return out
+
+
+def diagnostics(P: Params, st: dict) -> dict:
+    D = Diag()
+    rc = lib().orc_diagnostics(ctypes.byref(P), _ptr(st["h"]), _ptr(st["g"]),
+                               _ptr(st["p_prev"]), ctypes.byref(D))
+    if rc:
+        raise ValueError("orc_diagnostics failed (%d)" % rc)
+    return {k: getattr(D, k) for k, _ in Diag._fields_}
+
+
+def run(cfg: dict, phi0, nsteps: int, **over):
+    """Initialise from phi0 and advance nsteps; returns (params, state)."""
+    P = params(cfg, **over)
+    st = init(P, phi0)
+    if nsteps:
+        step(P, st, nsteps)
+    return P, st
