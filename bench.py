@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: MLUPS and fraction of the HBM roofline of the fused phase-field
+lattice Boltzmann step (arXiv:1902.08933, Sec. 3) on one GB300, with FP64, FP32,
+FP16-storage and batched forms side by side, their error against FP64, the
+end-to-end rate through the C ABI with host buffers, and the FP64 CPU oracle
+timed on the host cores.
+
+Workload (headline): rising bubble, 1024 x 4096, bounce-back walls in y,
+periodic x, R = 128 at y = 512, density ratio 10, Eo = 10, Re = 35, W = 5,
+quasi-incompressible model, pressure of Eq. 28; FP32 storage and arithmetic.
+One step = one lattice time step of the whole grid (both population sets).
+The state (2 x 352 MB ping-pong in FP32) is larger than the 129 MB L2, so no
+L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own independent replica of the
+workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176}
+METRIC = "MLUPS and % of HBM peak, FP64 vs FP32/FP16-storage vs batched, at stated error"
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f32", choices=list(BYTES_PER_LUP))
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the side-by-side forms, e2e and CPU legs")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.1)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- helpers
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source
+    has not changed since it was captured (else None)."""
+    src = os.path.join(ROOT, "paper_1902_08933_gb300", "csrc", "lbm_device.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "step_kernel_bubble_1024x4096.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9.eE+]+)" % re.escape(kernel_key), text)
+    if not m or not t or m.group(1) != sha:
+        return None
+    return float(t.group(1))
+
+
+def rel_err(a, b):
+    import numpy as np
+    den = float(np.max(np.abs(b)))
+    return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
+
+
+def time_steps(lbm, sim, stream, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        sim.step(1)
+    sim.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+# ------------------------------------------------------------------------- CPU oracle
+def oracle_rate(cfg, target_s=15.0):
+    """FP64 oracle on the host cores: one step of the full grid timed once, then as
+    many whole steps as fit in about target_s seconds."""
+    from oracle import oracle as orc
+    from paper_1902_08933_gb300 import workloads as wl
+    orc.build()
+    P = orc.params(cfg)
+    st = orc.init(P, wl.initial_phi(cfg))
+    t0 = time.perf_counter()
+    orc.step(P, st, 1)
+    t1 = time.perf_counter()
+    n = max(1, min(200, int(target_s / max(t1 - t0, 1e-6)) - 1))
+    t2 = time.perf_counter()
+    orc.step(P, st, n)
+    t3 = time.perf_counter()
+    cells = cfg["nx"] * cfg["ny"]
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return cells * n / (t3 - t2) / 1e6, threads, n, t3 - t2
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores, each
+    step one time step of a bounded horizontal slab of the bubble workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1902_08933_gb300 import workloads as wl
+    orc.build()
+    full = wl.rising_bubble()
+    # slab: full width, rows sized so one step takes about 40 ms on this host
+    probe = dict(full, ny=64, init=dict(full["init"], cy=32.0))
+    P = orc.params(probe)
+    st = orc.init(P, wl.initial_phi(probe))
+    t0 = time.perf_counter()
+    orc.step(P, st, 2)
+    per_row = (time.perf_counter() - t0) / 2 / 64
+    rows = int(max(16, min(full["ny"], 0.04 / max(per_row, 1e-9))))
+    cfg = dict(full, ny=rows, init=dict(full["init"], cy=rows / 2.0))
+    P = orc.params(cfg)
+    st = orc.init(P, wl.initial_phi(cfg))
+    orc.step(P, st, args.warmup)
+    t0 = time.perf_counter()
+    orc.step(P, st, args.steps)
+    dt = time.perf_counter() - t0
+    cells = cfg["nx"] * cfg["ny"]
+    mlups = cells * args.steps / dt / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%d x %d slab of the 1024 x 4096 bubble (walls in y), %d steps" % (
+        cfg["nx"], cfg["ny"], args.steps)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rising_bubble_1024x4096_rho10_qim (CPU slab sample)",
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1902_08933_gb300 import build, lbm
+    from paper_1902_08933_gb300 import workloads as wl
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cfg = wl.rising_bubble()
+    cells = cfg["nx"] * cfg["ny"]
+    phi0 = wl.initial_phi(cfg)
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+
+    # ---- headline: K steps of the fused kernel, CUDA events on its stream
+    sim = lbm.Simulation(cfg, args.form, stream=stream.cuda_stream, phi0=[phi0])
+    launches = lbm.lbm_launches_per_step(sim.ctx)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    d = sim.diagnostics()
+    sim.close()
+    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / (args.steps * launches)
+    achieved = BYTES_PER_LUP[args.form] * cells / per_launch_s / 1e9
+    traffic = traffic_record("%s" % args.form)
+    result = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.form == "f64" else "f32", "data": "synthetic",
+        "config": {"workload": "rising_bubble_1024x4096_rho10_qim", "nx": cfg["nx"], "ny": cfg["ny"],
+                   "form": args.form, "storage": {"f64": "f64", "f32": "f32",
+                                                  "f32_g16": "h0 2xf32, h1-8 f32, g f16",
+                                                  "f32_h16": "h0 2xf32, h1-8 f16, g f16",
+                                                  "f32_c": "h0 2xf32, h1-8 f32, g f32"}[args.form],
+                   "l2": "state %.0f MB > 129 MB L2, no flush" % (
+                       2 * BYTES_PER_LUP[args.form] / 2 * cells / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_lup": BYTES_PER_LUP[args.form]},
+        "clocks": clk,
+        "gpu_launches": args.steps * launches,
+        "mass_drift": abs(d["sum_phi"] - phi0.sum()) / phi0.sum(),
+    }
+
+    if not args.headline_only and rank == 0:
+        result.update(side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak))
+
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
+    """Other forms on the same workload, their error against FP64 on the GPU after
+    the same steps, the batched mixed-size configuration, the end-to-end rate
+    through the C ABI with host buffers, and the CPU oracle."""
+    import numpy as np
+    import torch
+    out = {}
+    cells = cfg["nx"] * cfg["ny"]
+    K = max(50, args.steps // 4)
+    acc_steps = 200
+    ref = None
+    forms = {}
+    for form in ("f64", "f32", "f32_c", "f32_g16", "f32_h16"):
+        with lbm.Simulation(cfg, form, stream=stream.cuda_stream, phi0=[phi0]) as sim:
+            sim.step(acc_steps)
+            f = sim.fields(0, ("phi", "ux", "uy", "p"))
+            if form == "f64":
+                ref = f
+            ms = time_steps(lbm, sim, stream, K, 5)
+            mlups = cells * K / (ms * 1e-3) / 1e6
+            gbs = BYTES_PER_LUP[form] * cells / (ms * 1e-3 / K) / 1e9
+            forms[form] = {"MLUPS": mlups, "GBps": gbs, "frac_hbm": gbs / hbm_peak,
+                           "steps": K,
+                           "err_vs_f64_after_%d_steps" % acc_steps: (
+                               None if form == "f64" else
+                               {k: rel_err(f[k], ref[k]) for k in ("phi", "ux", "uy", "p")})}
+    out["forms"] = forms
+
+    # batched: 512 independent droplets / bubbles of mixed size, one launch per size class
+    cfgs = wl.batched_mixed(512)
+    lups_per_step = wl.lups(cfgs, 1)
+    batched = {}
+    for form in ("f32", "f32_g16"):
+        with lbm.Simulation(cfgs, form, stream=stream.cuda_stream,
+                            phi0=[wl.initial_phi(c) for c in cfgs]) as sim:
+            Kb = 100
+            ms = time_steps(lbm, sim, stream, Kb, 5)
+            batched[form] = {"MLUPS": lups_per_step * Kb / (ms * 1e-3) / 1e6,
+                             "launches_per_step": lbm.lbm_launches_per_step(sim.ctx)}
+    batched["instances"] = len(cfgs)
+    batched["cells"] = int(lups_per_step)
+    out["batched"] = batched
+
+    # end to end through the C ABI with host buffers: init from pinned host phi0,
+    # each step one lbm_step plus an FP64 diagnostics record read to the host,
+    # fields read back to the host at the end.
+    Ke = max(20, args.steps // 20)
+    pinned = torch.from_numpy(phi0).pin_memory()
+    host_phi0 = pinned.numpy()
+    fields_out = np.zeros((4, cfg["ny"], cfg["nx"]))
+    with lbm.Simulation(cfg, args.form, stream=stream.cuda_stream) as sim:
+        lbm.lbm_init(sim.ctx, 0, host_phi0)
+        sim.step(5)
+        sim.sync()
+        t0 = time.perf_counter()
+        lbm.lbm_init(sim.ctx, 0, host_phi0)
+        for _ in range(Ke):
+            lbm.lbm_step(sim.ctx, 1)
+            lbm.lbm_diagnostics(sim.ctx, 0)
+        lbm.lbm_get_fields(sim.ctx, 0, 0xF, fields_out)
+        dt = time.perf_counter() - t0
+    d2h = 14 * 8 + 8 * 4 * cells / Ke
+    out["e2e"] = {"value": cells * Ke / dt / 1e6, "unit": "MLUPS",
+                  "h2d_bytes_per_step": 8 * cells / Ke, "d2h_bytes_per_step": d2h,
+                  "steps": Ke, "per_step": "lbm_step(1) + lbm_diagnostics (FP64 record to host)"}
+
+    # CPU oracle on the host cores (bounded sample: whole-grid steps for ~15 s)
+    mlups, threads, n, secs = oracle_rate(cfg)
+    out["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                           "sample": "%d full 1024x4096 steps (%.1f s), FP64, OpenMP over rows" % (n, secs)}
+    return out
+
+
+if __name__ == "__main__":
+    main()

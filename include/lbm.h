@@ -58,15 +58,21 @@ enum { LBM_FS_MU_GRADPHI = 0, LBM_FS_PHI_GRADMU = 1 };
  * mu_A (phi >= 1/2) / mu_B (Sec. 4.3). */
 enum { LBM_VISC_INV_LINEAR = 0, LBM_VISC_STEP = 1 };
 
-/* Storage and arithmetic form of a context.
- *  LBM_F64      populations and auxiliary fields in FP64, FP64 arithmetic.
- *  LBM_F32      populations and auxiliary fields in FP32, FP32 arithmetic.
- *  LBM_F32_G16  FP32 arithmetic; h in FP32; g in FP16, scaled by a power of
- *               two chosen per instance (g is stored shifted: g_0 - rho_0).
- *  LBM_F32_H16  FP32 arithmetic; g as in LBM_F32_G16; h_1..h_8 in FP16 and h_0
- *               in FP32, with h_0 stored as phi* - sum of the rounded h_1..h_8 so
- *               that rounding cannot create or destroy phi.                          */
-enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_G16 = 2, LBM_F32_H16 = 3 };
+/* Storage and arithmetic form of a context (bytes moved per lattice update in
+ * brackets: every population read and written once, plus phi*u and p).
+ *  LBM_F64      populations and auxiliary fields in FP64, FP64 arithmetic [336].
+ *  LBM_F32      populations and auxiliary fields in FP32, FP32 arithmetic [168].
+ *  LBM_F32_G16  FP32 arithmetic; h_1..h_8 FP32; g in FP16, scaled by a power of
+ *               two chosen per instance (g_0 stored as g_0 - rho_0); conservative
+ *               h_0 (below) [140].
+ *  LBM_F32_H16  FP32 arithmetic; h_1..h_8 and g in FP16, scaled; conservative
+ *               h_0 [108].
+ *  LBM_F32_C    FP32 arithmetic and storage with conservative h_0 [176].
+ * Conservative h_0: h_0 is stored as a pair of floats (hi + lo) set after each
+ * collision to phi minus the stored h_1..h_8 with error-free FP32 operations,
+ * so that storage rounding cannot create or destroy phi (sum of phi conserved
+ * to ~1e-13 relative instead of drifting ~2^-24 per step in plain FP32). */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_G16 = 2, LBM_F32_H16 = 3, LBM_F32_C = 4 };
 
 /* Field selection bits for lbm_get_fields*: outputs are written field-major in
  * this bit order, each field nx*ny doubles. P is the Laplace-law pressure of
@@ -121,7 +127,7 @@ lbm_status lbm_validate_params(const lbm_params* params);
 /* Creates a context holding n_instances independent simulations (one parameter
  * block each, sizes may differ), all advanced together by lbm_step.
  * params:      host array of n_instances blocks, copied.
- * precision:   LBM_F64 / LBM_F32 / LBM_F32_G16 / LBM_F32_H16.
+ * precision:   LBM_F64 / LBM_F32 / LBM_F32_G16 / LBM_F32_H16 / LBM_F32_C.
  * cuda_stream: a cudaStream_t to queue work on, or NULL for a library stream.
  * out:         receives the context; *out is NULL on failure.
  * Errors: LBM_EINVAL (bad arguments; *out stays NULL and no CUDA call is made),

@@ -1,0 +1,779 @@
+// lbm_api.cu -- the C ABI of include/lbm.h: contexts, device memory, work
+// planning, kernel dispatch, field readback, diagnostics and checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbm::AuxArgs;
+using lbm::DevInst;
+using lbm::StepArgs;
+using lbm::WorkItem;
+
+namespace {
+
+constexpr int kForms = 5;
+
+template <typename Fn>
+cudaError_t by_form(int form, Fn&& fn) {
+    switch (form) {
+        case 0: return fn(std::integral_constant<int, 0>{});
+        case 1: return fn(std::integral_constant<int, 1>{});
+        case 2: return fn(std::integral_constant<int, 2>{});
+        case 3: return fn(std::integral_constant<int, 3>{});
+        case 4: return fn(std::integral_constant<int, 4>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// storage of each form (see the form table in lbm_device.cuh)
+size_t h_elem(int form) { return form == 0 ? 8 : (form == 3 ? 2 : 4); }
+size_t g_elem(int form) { return form == 0 ? 8 : ((form == 2 || form == 3) ? 2 : 4); }
+size_t a_elem(int form) { return form == 0 ? 8 : 4; }
+bool conservative(int form) { return form >= 2; }
+int h_planes(int form) { return conservative(form) ? 8 : 9; }
+
+// Largest power of two s with s * bound <= 2048: keeps FP16-stored values
+// (|v| * s) at least 30x below the FP16 maximum and far above its subnormals.
+double pow2_scale(double bound) {
+    if (!(bound > 0)) return 1.0;
+    return std::ldexp(1.0, (int)std::floor(std::log2(2048.0 / bound)));
+}
+
+bool finite_all(const lbm_params& p) {
+    const double v[] = {p.rho_A, p.rho_B, p.nu_A, p.nu_B, p.sigma, p.W, p.tau_h,
+                        p.mobility, p.force_x, p.force_y, p.gravity};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+const char* check_params(const lbm_params& p) {
+    if (p.nx < 3 || p.ny < 3) return "nx and ny must be >= 3";
+    if ((long long)p.nx * p.ny >= (1LL << 31)) return "nx*ny must be < 2^31";
+    if (p.bc_y != LBM_BC_PERIODIC && p.bc_y != LBM_BC_BOUNCEBACK) return "bc_y out of range";
+    if (p.variant != LBM_IM && p.variant != LBM_QIM) return "variant out of range";
+    if (p.pressure_scheme < LBM_P_MODIFIED_PRINTED || p.pressure_scheme > LBM_P_PREVIOUS)
+        return "pressure_scheme out of range";
+    if (p.surface_force != LBM_FS_MU_GRADPHI && p.surface_force != LBM_FS_PHI_GRADMU)
+        return "surface_force out of range";
+    if (p.viscosity_model != LBM_VISC_INV_LINEAR && p.viscosity_model != LBM_VISC_STEP)
+        return "viscosity_model out of range";
+    if (p.reserved != 0) return "reserved must be 0";
+    if (!finite_all(p)) return "parameters must be finite";
+    if (!(p.rho_A > 0 && p.rho_B > 0)) return "densities must be > 0";
+    if (!(p.nu_A > 0 && p.nu_B > 0)) return "viscosities must be > 0";
+    if (!(p.W > 0)) return "W must be > 0";
+    if (!(p.sigma >= 0)) return "sigma must be >= 0";
+    if (!(p.mobility >= 0)) return "mobility must be >= 0";
+    if (!(p.tau_h > 0.5)) return "tau_h must be > 1/2";
+    return nullptr;
+}
+
+// Host-side derivation of the per-instance constants (Eqs. 6-7, 17, Sec. 3.2.1).
+DevInst derive(const lbm_params& p, long long base, int form) {
+    DevInst d;
+    std::memset(&d, 0, sizeof(d));
+    d.base = base;
+    d.nx = p.nx;
+    d.ny = p.ny;
+    d.walls = p.bc_y == LBM_BC_BOUNCEBACK;
+    d.qim = p.variant == LBM_QIM;
+    d.pscheme = p.pressure_scheme;
+    d.sforce = p.surface_force;
+    d.visc = p.viscosity_model;
+    const double phiA = 1.0, phiB = 0.0;
+    d.rho_A = p.rho_A;
+    d.rho_B = p.rho_B;
+    d.drho = (p.rho_A - p.rho_B) / (phiA - phiB);
+    d.inv_nu_A = 1.0 / p.nu_A;
+    d.inv_nu_B = 1.0 / p.nu_B;
+    d.mu_A = p.rho_A * p.nu_A;
+    d.mu_B = p.rho_B * p.nu_B;
+    d.kappa = 1.5 * p.sigma * p.W;                 // from W = sqrt(8 kappa / beta), sigma = sqrt(2 kappa beta)/6
+    d.beta = 12.0 * p.sigma / p.W;
+    d.eta = p.mobility / ((1.0 / 3.0) * (p.tau_h - 0.5));   // Eq. 17
+    const double gamma = (p.rho_A - p.rho_B) / (phiA * p.rho_B - phiB * p.rho_A);
+    d.gammaM = gamma * p.mobility;
+    d.inv_tau_h = 1.0 / p.tau_h;
+    d.force_x = p.force_x;
+    d.force_y = p.force_y;
+    d.gravity = p.gravity;
+    // Storage scales of the FP16 forms: bounds of |h_i| (i != 0) and |g_i| from the
+    // equilibria (Eqs. 11, 33) with |mu| <~ beta and |u| <~ 0.1.
+    const double rho_max = std::max(p.rho_A, p.rho_B);
+    const double h_bound = (d.eta * d.beta + 0.35) / 9.0;
+    const double g_bound = rho_max * 0.05 + 3.0 * d.beta + 1e-3;
+    d.h_scale = form == 3 ? pow2_scale(h_bound) : 1.0;
+    d.g_scale = (form == 2 || form == 3) ? pow2_scale(g_bound) : 1.0;
+    return d;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    int n = 0, form = 0, device = 0;
+    std::vector<lbm_params> params;
+    std::vector<DevInst> inst;
+    std::vector<int64_t> time;
+    std::vector<char> ready;
+    long long S = 0, max_cells = 0;
+    DevInst* d_inst = nullptr;
+    void* h[2] = {nullptr, nullptr};
+    void* h0[2] = {nullptr, nullptr};     // conservative forms: h_0 as float2
+    void* g[2] = {nullptr, nullptr};
+    void* phiu = nullptr;
+    void* p[2] = {nullptr, nullptr};
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int tile_req = 0, rows_req = 0;
+    struct Launch { int tx, offset, count; };
+    std::vector<Launch> launches;
+    std::vector<WorkItem> work;
+    WorkItem* d_work = nullptr;
+    bool plan_dirty = true;
+    double* d_tmp = nullptr;       // 2 * max_cells
+    double* d_out = nullptr;       // field staging, grown on demand
+    size_t d_out_cells = 0;
+    double* d_partials = nullptr;
+    double* d_result = nullptr;
+    double* h_result = nullptr;    // pinned
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CK(ctx, call)                                          \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+StepArgs step_args(const lbm_ctx* c, int in) {
+    StepArgs a;
+    a.h_in = c->h[in];
+    a.h_out = c->h[1 - in];
+    a.h0_in = c->h0[in];
+    a.h0_out = c->h0[1 - in];
+    a.g_in = c->g[in];
+    a.g_out = c->g[1 - in];
+    a.phiu = c->phiu;
+    a.p_in = c->p[in];
+    a.p_out = c->p[1 - in];
+    a.S = c->S;
+    a.inst = c->d_inst;
+    a.work = nullptr;
+    return a;
+}
+
+AuxArgs aux_args(const lbm_ctx* c, int instance) {
+    AuxArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.h = c->h[c->cur];
+    a.h0 = c->h0[c->cur];
+    a.g = c->g[c->cur];
+    a.phiu = c->phiu;
+    a.p_prev = c->p[c->cur];
+    a.S = c->S;
+    a.inst = c->d_inst;
+    a.instance = instance;
+    a.tmp_phi = c->d_tmp;
+    a.tmp_mu = c->d_tmp + c->max_cells;
+    a.partials = c->d_partials;
+    a.result = c->d_result;
+    return a;
+}
+
+int default_tile(int nx) {
+    if (nx >= 128) return 128;
+    if (nx > 32) return 64;
+    return 32;
+}
+
+// Work list: per instance, strips of tile_x columns, each split into runs of
+// rows. Neighbouring runs march in opposite directions (down, up, down, ...) so
+// that two blocks that share a run boundary read its halo rows at the same time
+// (both at their start or both at their end), from L2 rather than HBM.
+lbm_status plan(lbm_ctx* c) {
+    std::vector<std::vector<WorkItem>> by_class(5);
+    const int classes[5] = {32, 64, 128, 256, 0};
+    auto cls_index = [&](int tx) {
+        for (int k = 0; k < 4; ++k)
+            if (classes[k] == tx) return k;
+        return 4;
+    };
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    for (int k = 0; k < c->n; ++k) {
+        const lbm_params& p = c->params[k];
+        const int tx = c->tile_req ? c->tile_req : default_tile(p.nx);
+        const int strips = (p.nx + tx - 1) / tx;
+        int rows = c->rows_req;
+        if (rows <= 0) {
+            if (c->n == 1) {
+                // one domain: fill the GPU with resident blocks in a single wave
+                int occ = 0;
+                by_form(c->form, [&](auto F) {
+                    occ = lbm::step_occupancy_t<decltype(F)::value>(tx);
+                    return cudaSuccess;
+                });
+                const long long target = (long long)sms * std::max(occ, 1);
+                const long long chunks = std::max<long long>(1, (target + strips - 1) / strips);
+                rows = (int)std::max<long long>(8, (p.ny + chunks - 1) / chunks);
+            } else {
+                rows = 32;
+            }
+        }
+        rows = std::min(rows, p.ny);
+        const int nchunks = (p.ny + rows - 1) / rows;
+        auto& list = by_class[cls_index(tx)];
+        for (int s = 0; s < strips; ++s)
+            for (int ch = 0; ch < nchunks; ++ch) {
+                const int y0 = ch * rows, y1 = std::min(p.ny, y0 + rows);
+                WorkItem w;
+                w.inst = k;
+                w.x0 = s * tx;
+                w.nrows = y1 - y0;
+                w.dir = (ch % 2 == 0) ? -1 : 1;
+                w.ystart = w.dir < 0 ? y1 - 1 : y0;
+                w.pad = 0;
+                list.push_back(w);
+            }
+    }
+    c->work.clear();
+    c->launches.clear();
+    for (int k = 0; k < 4; ++k) {
+        if (by_class[k].empty()) continue;
+        c->launches.push_back({classes[k], (int)c->work.size(), (int)by_class[k].size()});
+        c->work.insert(c->work.end(), by_class[k].begin(), by_class[k].end());
+    }
+    if (c->d_work) cudaFree(c->d_work);
+    c->d_work = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_work, c->work.size() * sizeof(WorkItem)));
+    LBM_CK(c, cudaMemcpy(c->d_work, c->work.data(), c->work.size() * sizeof(WorkItem),
+                         cudaMemcpyHostToDevice));
+    c->plan_dirty = false;
+    return LBM_OK;
+}
+
+lbm_status check_instance(lbm_ctx* c, int instance) {
+    if (!c) return LBM_EINVAL;
+    if (instance < 0 || instance >= c->n) return fail(c, LBM_EINVAL, "instance out of range");
+    return LBM_OK;
+}
+
+lbm_status sticky(lbm_ctx* c) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "earlier asynchronous work");
+    return LBM_OK;
+}
+
+lbm_status ensure_out(lbm_ctx* c, size_t cells) {
+    if (c->d_out_cells >= cells) return LBM_OK;
+    if (c->d_out) cudaFree(c->d_out);
+    c->d_out = nullptr;
+    c->d_out_cells = 0;
+    LBM_CK(c, cudaMalloc(&c->d_out, cells * sizeof(double)));
+    c->d_out_cells = cells;
+    return LBM_OK;
+}
+
+void release(lbm_ctx* c) {
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->h[b]);
+        cudaFree(c->h0[b]);
+        cudaFree(c->g[b]);
+        cudaFree(c->p[b]);
+    }
+    cudaFree(c->phiu);
+    cudaFree(c->d_inst);
+    cudaFree(c->d_work);
+    cudaFree(c->d_tmp);
+    cudaFree(c->d_out);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_result);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+int popcount7(unsigned m) {
+    int k = 0;
+    for (int b = 0; b < 7; ++b) k += (m >> b) & 1u;
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_validate_params(const lbm_params* params) {
+    if (!params) return LBM_EINVAL;
+    return check_params(*params) ? LBM_EINVAL : LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, void* cuda_stream,
+                      lbm_ctx** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (!params || n_instances <= 0) return LBM_EINVAL;
+    if (precision < 0 || precision >= kForms) return LBM_EINVAL;
+    for (int k = 0; k < n_instances; ++k)
+        if (check_params(params[k])) return LBM_EINVAL;
+
+    lbm_ctx* c = new lbm_ctx();
+    c->n = n_instances;
+    c->form = precision;
+    c->params.assign(params, params + n_instances);
+    c->time.assign(n_instances, 0);
+    c->ready.assign(n_instances, 0);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        lbm_status st = cuda_fail(c, e, "cudaGetDevice");
+        delete c;
+        return st;
+    }
+    // Instance placement: each instance starts on a 64-cell boundary.
+    long long base = 0;
+    for (int k = 0; k < n_instances; ++k) {
+        c->inst.push_back(derive(params[k], base, precision));
+        const long long cells = (long long)params[k].nx * params[k].ny;
+        c->max_cells = std::max(c->max_cells, cells);
+        base += (cells + 63) / 64 * 64;
+    }
+    c->S = base;
+    auto cleanup = [&](lbm_status st) {
+        release(c);
+        delete c;
+        return st;
+    };
+    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+    const size_t S = (size_t)c->S;
+    for (int b = 0; b < 2; ++b) {
+        if ((e = alloc(&c->h[b], h_planes(precision) * S * h_elem(precision))) != cudaSuccess ||
+            (e = alloc(&c->g[b], 9 * S * g_elem(precision))) != cudaSuccess ||
+            (e = alloc(&c->p[b], S * a_elem(precision))) != cudaSuccess)
+            return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+        if (conservative(precision) && (e = alloc(&c->h0[b], S * 2 * sizeof(float))) != cudaSuccess)
+            return cleanup(LBM_ENOMEM);
+    }
+    if ((e = alloc(&c->phiu, 2 * S * a_elem(precision))) != cudaSuccess ||
+        (e = alloc((void**)&c->d_inst, n_instances * sizeof(DevInst))) != cudaSuccess ||
+        (e = alloc((void**)&c->d_tmp, 2 * (size_t)c->max_cells * sizeof(double))) != cudaSuccess ||
+        (e = alloc((void**)&c->d_partials, lbm::kDiagBlocks * lbm::kDiagQuantities * sizeof(double))) !=
+            cudaSuccess ||
+        (e = alloc((void**)&c->d_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess)
+        return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+    if ((e = cudaMallocHost((void**)&c->h_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess)
+        return cleanup(LBM_ENOMEM);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cleanup(LBM_ECUDA);
+        c->own_stream = true;
+    }
+    if ((e = cudaMemcpy(c->d_inst, c->inst.data(), n_instances * sizeof(DevInst),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cleanup(LBM_ECUDA);
+    e = by_form(precision, [](auto F) { return lbm::prepare_step_t<decltype(F)::value>(); });
+    if (e != cudaSuccess) return cleanup(LBM_ECUDA);
+    if (plan(c) != LBM_OK) return cleanup(LBM_ECUDA);
+    *out = c;
+    return LBM_OK;
+}
+
+static lbm_status init_common(lbm_ctx* c, int instance, const double* phi0_dev) {
+    const lbm_params& p = c->params[instance];
+    const int ncells = p.nx * p.ny;
+    StepArgs a = step_args(c, 1 - c->cur);   // writes into the current buffers
+    cudaError_t e = by_form(c->form, [&](auto F) {
+        return lbm::launch_init_t<decltype(F)::value>(a, phi0_dev, instance, ncells, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    c->time[instance] = 0;
+    c->ready[instance] = 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* c, int instance, const double* phi0_host) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!phi0_host) return fail(c, LBM_EINVAL, "phi0 is NULL");
+    LBM_CK(c, cudaSetDevice(c->device));
+    const lbm_params& p = c->params[instance];
+    const size_t bytes = (size_t)p.nx * p.ny * sizeof(double);
+    LBM_CK(c, cudaMemcpyAsync(c->d_tmp, phi0_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    st = init_common(c, instance, c->d_tmp);
+    if (st != LBM_OK) return st;
+    // phi0_host is caller-owned: finish reading it before returning
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_device(lbm_ctx* c, int instance, const double* phi0_device) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!phi0_device) return fail(c, LBM_EINVAL, "phi0 is NULL");
+    LBM_CK(c, cudaSetDevice(c->device));
+    return init_common(c, instance, phi0_device);
+}
+
+lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
+    for (int k = 0; k < c->n; ++k)
+        if (!c->ready[k]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    lbm_status st = sticky(c);
+    if (st != LBM_OK) return st;
+    if (c->plan_dirty && (st = plan(c)) != LBM_OK) return st;
+    for (int t = 0; t < nsteps; ++t) {
+        StepArgs a = step_args(c, c->cur);
+        for (const auto& L : c->launches) {
+            a.work = c->d_work + L.offset;
+            cudaError_t e = by_form(c->form, [&](auto F) {
+                return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+        }
+        c->cur ^= 1;
+    }
+    for (int k = 0; k < c->n; ++k) c->time[k] += nsteps;
+    return LBM_OK;
+}
+
+static lbm_status fields_to_device(lbm_ctx* c, int instance, unsigned mask, double* dev_out) {
+    const lbm_params& p = c->params[instance];
+    AuxArgs a = aux_args(c, instance);
+    a.out = dev_out;
+    a.mask = mask;
+    cudaError_t e = by_form(c->form, [&](auto F) {
+        return lbm::launch_fields_t<decltype(F)::value>(a, p.nx * p.ny, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "fields kernels");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_ctx* c, int instance, unsigned mask, double* host_out) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!host_out || mask == 0 || mask >= 128u) return fail(c, LBM_EINVAL, "bad mask or output");
+    if (!c->ready[instance]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    if ((st = sticky(c)) != LBM_OK) return st;
+    const lbm_params& p = c->params[instance];
+    const size_t cells = (size_t)p.nx * p.ny * popcount7(mask);
+    if ((st = ensure_out(c, cells)) != LBM_OK) return st;
+    if ((st = fields_to_device(c, instance, mask, c->d_out)) != LBM_OK) return st;
+    LBM_CK(c, cudaMemcpyAsync(host_out, c->d_out, cells * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields_device(lbm_ctx* c, int instance, unsigned mask, double* dev_out) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!dev_out || mask == 0 || mask >= 128u) return fail(c, LBM_EINVAL, "bad mask or output");
+    if (!c->ready[instance]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    if ((st = sticky(c)) != LBM_OK) return st;
+    return fields_to_device(c, instance, mask, dev_out);
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* c, int instance, lbm_diag* out) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!out) return fail(c, LBM_EINVAL, "out is NULL");
+    if (!c->ready[instance]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    if ((st = sticky(c)) != LBM_OK) return st;
+    const lbm_params& p = c->params[instance];
+    AuxArgs a = aux_args(c, instance);
+    cudaError_t e = by_form(c->form, [&](auto F) {
+        return lbm::launch_diag_t<decltype(F)::value>(a, p.nx * p.ny, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernels");
+    LBM_CK(c, cudaMemcpyAsync(c->h_result, c->d_result, lbm::kDiagQuantities * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    const double* r = c->h_result;
+    std::memset(out, 0, sizeof(*out));
+    out->sum_phi = r[0];
+    out->sum_rho = r[1];
+    out->kinetic_energy = r[2];
+    out->max_u = r[3];
+    out->mass_A = r[0];
+    out->mass_B = r[13];
+    out->centroid_A_x = r[4] / r[0];
+    out->centroid_A_y = r[5] / r[0];
+    out->centroid_B_x = r[6] / r[13];
+    out->centroid_B_y = r[7] / r[13];
+    out->P_bulk_A = r[9] > 0 ? r[8] / r[9] : 0.0;
+    out->n_bulk_A = r[9];
+    out->P_bulk_B = r[11] > 0 ? r[10] / r[11] : 0.0;
+    out->n_bulk_B = r[11];
+    out->nonfinite = r[12] > 0 ? 1 : 0;
+    out->time = c->time[instance];
+    if (out->nonfinite) return fail(c, LBM_ENONFINITE, "non-finite population");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, int instance, double* host_h, double* host_g) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!c->ready[instance]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    if ((st = sticky(c)) != LBM_OK) return st;
+    const lbm_params& p = c->params[instance];
+    const size_t n = (size_t)p.nx * p.ny;
+    if ((st = ensure_out(c, 18 * n)) != LBM_OK) return st;
+    AuxArgs a = aux_args(c, instance);
+    cudaError_t e = by_form(c->form, [&](auto F) {
+        return lbm::launch_populations_t<decltype(F)::value>(a, (int)n, c->d_out, c->d_out + 9 * n,
+                                                             c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "populations kernel");
+    if (host_h)
+        LBM_CK(c, cudaMemcpyAsync(host_h, c->d_out, 9 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->stream));
+    if (host_g)
+        LBM_CK(c, cudaMemcpyAsync(host_g, c->d_out + 9 * n, 9 * n * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+// ---- checkpoints --------------------------------------------------------
+namespace {
+const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+struct Segment { void* dev; size_t elem; int planes; };
+
+std::vector<Segment> segments(lbm_ctx* c) {
+    std::vector<Segment> s;
+    s.push_back({c->h[c->cur], h_elem(c->form), h_planes(c->form)});
+    if (conservative(c->form)) s.push_back({c->h0[c->cur], 8, 1});
+    s.push_back({c->g[c->cur], g_elem(c->form), 9});
+    s.push_back({c->phiu, a_elem(c->form), 2});
+    s.push_back({c->p[c->cur], a_elem(c->form), 1});
+    return s;
+}
+
+bool little_endian() {
+    const uint32_t one = 1;
+    unsigned char b;
+    std::memcpy(&b, &one, 1);
+    return b == 1;
+}
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    if (!little_endian()) return fail(c, LBM_EIO, "checkpoints need a little-endian host");
+    LBM_CK(c, cudaSetDevice(c->device));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(c, LBM_EIO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+    const int32_t hdr[4] = {1, c->form, c->n, 0};
+    ok = ok && std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    ok = ok && std::fwrite(c->params.data(), sizeof(lbm_params), c->n, f) == (size_t)c->n;
+    ok = ok && std::fwrite(c->time.data(), sizeof(int64_t), c->n, f) == (size_t)c->n;
+    std::vector<unsigned char> buf;
+    for (const Segment& s : segments(c)) {
+        const size_t bytes = (size_t)s.planes * c->S * s.elem;
+        buf.resize(bytes);
+        cudaError_t e = cudaMemcpy(buf.data(), s.dev, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return cuda_fail(c, e, "checkpoint read-back");
+        }
+        ok = ok && std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LBM_OK : fail(c, LBM_EIO, std::string("write failed: ") + path);
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    if (!little_endian()) return fail(c, LBM_EIO, "checkpoints need a little-endian host");
+    LBM_CK(c, cudaSetDevice(c->device));
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, LBM_EIO, std::string("cannot open ") + path);
+    char magic[8];
+    int32_t hdr[4];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
+    ok = ok && std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 1;
+    if (!ok) {
+        std::fclose(f);
+        return fail(c, LBM_EIO, "not a checkpoint file");
+    }
+    if (hdr[1] != c->form || hdr[2] != c->n) {
+        std::fclose(f);
+        return fail(c, LBM_EINVAL, "checkpoint precision or instance count differs");
+    }
+    std::vector<lbm_params> ps(c->n);
+    std::vector<int64_t> ts(c->n);
+    ok = std::fread(ps.data(), sizeof(lbm_params), c->n, f) == (size_t)c->n &&
+         std::fread(ts.data(), sizeof(int64_t), c->n, f) == (size_t)c->n;
+    if (!ok || std::memcmp(ps.data(), c->params.data(), sizeof(lbm_params) * c->n) != 0) {
+        std::fclose(f);
+        return fail(c, ok ? LBM_EINVAL : LBM_EIO, "checkpoint parameters differ");
+    }
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    std::vector<unsigned char> buf;
+    for (const Segment& s : segments(c)) {
+        const size_t bytes = (size_t)s.planes * c->S * s.elem;
+        buf.resize(bytes);
+        if (std::fread(buf.data(), 1, bytes, f) != bytes) {
+            std::fclose(f);
+            return fail(c, LBM_EIO, "checkpoint truncated");
+        }
+        cudaError_t e = cudaMemcpy(s.dev, buf.data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return cuda_fail(c, e, "checkpoint upload");
+        }
+    }
+    std::fclose(f);
+    c->time = ts;
+    c->ready.assign(c->n, 1);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_ctx* c, int tile_x, int rows) {
+    if (!c) return LBM_EINVAL;
+    if (!(tile_x == 0 || tile_x == 32 || tile_x == 64 || tile_x == 128 || tile_x == 256))
+        return fail(c, LBM_EINVAL, "tile_x must be 0, 32, 64, 128 or 256");
+    if (rows < 0) return fail(c, LBM_EINVAL, "rows must be >= 0");
+    c->tile_req = tile_x;
+    c->rows_req = rows;
+    c->plan_dirty = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx* c, int* best_tile_x, int* best_rows) {
+    if (!c) return LBM_EINVAL;
+    for (int k = 0; k < c->n; ++k)
+        if (!c->ready[k]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    // Save the state (current buffers) so the trial steps leave no trace.
+    std::vector<Segment> segs = segments(c);
+    std::vector<void*> saved;
+    for (const Segment& s : segs) {
+        void* b = nullptr;
+        const size_t bytes = (size_t)s.planes * c->S * s.elem;
+        cudaError_t e = cudaMalloc(&b, bytes);
+        if (e != cudaSuccess) {
+            for (void* q : saved) cudaFree(q);
+            return cuda_fail(c, e, "autotune backup");
+        }
+        cudaMemcpyAsync(b, s.dev, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        saved.push_back(b);
+    }
+    const int cur0 = c->cur;
+    const std::vector<int64_t> time0 = c->time;
+    const int tiles[3] = {64, 128, 256};
+    const int rows_c[5] = {0, 8, 16, 32, 64};
+    float best = 1e30f;
+    int bt = c->tile_req, br = c->rows_req;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    lbm_status st = LBM_OK;
+    for (int tx : tiles) {
+        bool fits = false;
+        for (const auto& p : c->params) fits = fits || p.nx >= tx / 2;
+        if (!fits) continue;
+        for (int r : rows_c) {
+            c->tile_req = tx;
+            c->rows_req = r;
+            c->plan_dirty = true;
+            if ((st = lbm_step(c, 2)) != LBM_OK) break;   // warm-up
+            cudaEventRecord(e0, c->stream);
+            if ((st = lbm_step(c, 6)) != LBM_OK) break;
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = tx;
+                br = r;
+            }
+        }
+        if (st != LBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->cur = cur0;
+    segs = segments(c);
+    for (size_t k = 0; k < segs.size(); ++k) {
+        cudaMemcpyAsync(segs[k].dev, saved[k], (size_t)segs[k].planes * c->S * segs[k].elem,
+                        cudaMemcpyDeviceToDevice, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    for (void* q : saved) cudaFree(q);
+    c->time = time0;
+    if (st != LBM_OK) return st;
+    c->tile_req = bt;
+    c->rows_req = br;
+    c->plan_dirty = true;
+    if (best_tile_x) *best_tile_x = bt;
+    if (best_rows) *best_rows = br;
+    return sticky(c);
+}
+
+int lbm_launches_per_step(const lbm_ctx* c) {
+    if (!c) return 0;
+    if (!c->plan_dirty) return (int)c->launches.size();
+    int classes = 0;
+    bool seen[5] = {false, false, false, false, false};
+    for (const auto& p : c->params) {
+        const int tx = c->tile_req ? c->tile_req : default_tile(p.nx);
+        const int k = tx == 32 ? 0 : tx == 64 ? 1 : tx == 128 ? 2 : 3;
+        if (!seen[k]) { seen[k] = true; ++classes; }
+    }
+    return classes;
+}
+
+int64_t lbm_time(const lbm_ctx* c, int instance) {
+    if (!c || instance < 0 || instance >= c->n) return -1;
+    return c->time[instance];
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    LBM_CK(c, cudaSetDevice(c->device));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return sticky(c);
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,787 @@
+// lbm_device.cuh -- device code of the phase-field lattice Boltzmann step
+// (arXiv:1902.08933, Sec. 3), shared by the per-precision translation units.
+//
+// Data layout (structure of arrays, one plane per population direction):
+//   pop[i * S + base + y * nx + x],  S = plane stride (all instances), base = the
+//   instance's first cell. The state between steps is the set of post-streaming
+//   populations h_i(x, t), g_i(x, t) (as in Eqs. 10 and 24, left-hand side), the
+//   product phi*u of the previous step (for Eq. 14) and the pressure p of the
+//   previous step (for grad p, reading Q2). g_0 is stored shifted by rho_0, i.e.
+//   the kernel works with rho_0 = 0: rho_0 enters only g_0 and cancels from every
+//   output (Eq. 33, App. B).
+//
+// Fused step kernel (one launch per time step): a thread block owns a strip of
+// TX columns and marches over a run of rows. Per output row Y it
+//   A. loads the populations h of the lead row Y + 2d (aligned loads) and forms
+//      phi = sum_i h_i (Eq. 18) over the strip plus a 2-column halo, keeping
+//      h in shared memory for the collision two rows later; loads p of row Y + d;
+//   B. forms mu (Eq. 8, Laplacian of Eq. 30b) of row Y + d from the phi ring;
+//   C. collides row Y: stencils of phi, mu, p (Eq. 30), forces, velocity
+//      (Eq. 27a), pressure (Eq. 28/29), g^eq (Eq. 33), G_i (Eq. 34), h^eq
+//      (Eq. 11), R_i (Eq. 14), BGK updates (Eqs. 24, 10), and pushes the new
+//      populations to their neighbours (periodic or halfway bounce-back).
+// Every population is read from HBM once per step (halo columns aside) and
+// written once; phi and mu never leave shared memory.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// D2Q9 lattice (Sec. 2.2): order (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+// (-1,-1),(1,-1); weights 4/9, 1/9 (axes), 1/36 (diagonals); c_s^2 = 1/3.
+__host__ __device__ constexpr int cx_of(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_of(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+template <typename R>
+__host__ __device__ constexpr R w_of(int i) {
+    return i == 0 ? R(4) / R(9) : (i <= 4 ? R(1) / R(9) : R(1) / R(36));
+}
+
+// ---------------------------------------------------------------------------
+// Storage forms (enum order of include/lbm.h):
+//   0 LBM_F64      everything FP64.
+//   1 LBM_F32      everything FP32.
+//   2 LBM_F32_G16  h_1..8 FP32, g FP16 (scaled), aux FP32, h_0 conservative.
+//   3 LBM_F32_H16  h_1..8 FP16 (scaled), g FP16 (scaled), aux FP32, h_0 conservative.
+//   4 LBM_F32_C    h_1..8 FP32, g FP32, aux FP32, h_0 conservative.
+// "Conservative h_0": h_0 is kept as an unevaluated sum of two floats (hi + lo)
+// in a plane of its own and, after each collision, set to phi minus the stored
+// (rounded) h_1..h_8, with error-free FP32 transformations. The stored
+// populations of a cell then sum to phi to about 2^-48, so the storage rounding
+// cannot create or destroy phi: the global sum of phi is conserved although the
+// arithmetic is FP32 (plain FP32 drifts by ~2^-24 per step where phi ~ 1 sits in
+// h_0 and rounds the same way every step).
+template <int FORM> struct Form;
+template <> struct Form<0> {
+    using R = double; using HT = double; using GT = double; using AT = double;
+    static constexpr bool h16 = false, g16 = false, cons = false;
+};
+template <> struct Form<1> {
+    using R = float; using HT = float; using GT = float; using AT = float;
+    static constexpr bool h16 = false, g16 = false, cons = false;
+};
+template <> struct Form<2> {
+    using R = float; using HT = float; using GT = __half; using AT = float;
+    static constexpr bool h16 = false, g16 = true, cons = true;
+};
+template <> struct Form<3> {
+    using R = float; using HT = __half; using GT = __half; using AT = float;
+    static constexpr bool h16 = true, g16 = true, cons = true;
+};
+template <> struct Form<4> {
+    using R = float; using HT = float; using GT = float; using AT = float;
+    static constexpr bool h16 = false, g16 = false, cons = true;
+};
+
+template <typename T, typename R> __device__ __forceinline__ R ldr(const T* p);
+template <> __device__ __forceinline__ double ldr<double, double>(const double* p) { return *p; }
+template <> __device__ __forceinline__ float ldr<float, float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ldr<__half, float>(const __half* p) {
+    return __half2float(*p);
+}
+template <typename T, typename R> __device__ __forceinline__ void str(T* p, R v);
+template <> __device__ __forceinline__ void str<double, double>(double* p, double v) { *p = v; }
+template <> __device__ __forceinline__ void str<float, float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void str<__half, float>(__half* p, float v) {
+    *p = __float2half_rn(v);
+}
+
+// Error-free transformations (Knuth's TwoSum, Dekker's Fast2Sum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Population access through the storage form. For conservative forms plane 0 of
+// h is a float2 plane (hi, lo) of its own and planes 1..8 sit at (i - 1) * S.
+template <class F>
+struct PopIO {
+    using R = typename F::R;
+    using HT = typename F::HT;
+    using GT = typename F::GT;
+    const HT* hin; HT* hout; const float2* h0in; float2* h0out;
+    const GT* gin; GT* gout;
+    long long S;
+    R hs, ihs, gs, igs;    // storage scales and their inverses
+
+    __device__ __forceinline__ long long hoff(int i) const {
+        return (long long)(F::cons ? i - 1 : i) * S;
+    }
+    // h_i for i >= 1 (and i = 0 for non-conservative forms)
+    __device__ __forceinline__ R load_h(int i, long long c) const {
+        if constexpr (F::h16) return ldr<HT, R>(hin + hoff(i) + c) * ihs;
+        else return ldr<HT, R>(hin + hoff(i) + c);
+    }
+    __device__ __forceinline__ float2 load_h0(long long c) const { return h0in[c]; }
+    // the value of h_i (i >= 1) as it will be read back after storage
+    __device__ __forceinline__ R round_h(R v) const {
+        if constexpr (F::h16) return __half2float(__float2half_rn(v * hs)) * ihs;
+        else return v;
+    }
+    __device__ __forceinline__ void store_h(int i, long long c, R v) const {
+        if constexpr (F::h16) str<HT, R>(hout + hoff(i) + c, v * hs);
+        else str<HT, R>(hout + hoff(i) + c, v);
+    }
+    __device__ __forceinline__ void store_h0(long long c, float2 v) const { h0out[c] = v; }
+    __device__ __forceinline__ R load_g(int i, long long c) const {
+        if constexpr (F::g16) return ldr<GT, R>(gin + (long long)i * S + c) * igs;
+        else return ldr<GT, R>(gin + (long long)i * S + c);
+    }
+    __device__ __forceinline__ void store_g(int i, long long c, R v) const {
+        if constexpr (F::g16) str<GT, R>(gout + (long long)i * S + c, v * gs);
+        else str<GT, R>(gout + (long long)i * S + c, v);
+    }
+    // phi = sum_i h_i (Eq. 18) of cell c; for conservative forms also the low
+    // part of phi (phi ~ hi + lo). Summation order: h_0 + h_1 + ... + h_8.
+    __device__ __forceinline__ R phi_of(long long c, R hv[9], R& phi_lo) const {
+        if constexpr (F::cons) {
+            R s8 = R(0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) { hv[i] = load_h(i, c); s8 += hv[i]; }
+            const float2 h0 = load_h0(c);
+            float s, e, hi, lo;
+            two_sum(h0.x, s8, s, e);
+            fast_two_sum(s, e + h0.y, hi, lo);
+            hv[0] = hi - s8;        // h_0 as seen by the arithmetic (not stored)
+            phi_lo = lo;
+            return hi;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) hv[i] = load_h(i, c);
+            R phi = hv[0];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) phi += hv[i];
+            phi_lo = R(0);
+            return phi;
+        }
+    }
+    // h_0 after the collision for conservative forms: (phi_hi + phi_lo) - sum of the
+    // stored h_1..8, as a normalised float pair.
+    __device__ __forceinline__ float2 conservative_h0(float phi_hi, float phi_lo, float rest) const {
+        float s, e, hi, lo;
+        two_sum(phi_hi, -rest, s, e);
+        fast_two_sum(s, e + phi_lo, hi, lo);
+        return make_float2(hi, lo);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Per-instance constants in the arithmetic type.
+template <typename R>
+struct Consts {
+    int nx, ny, walls, qim, pscheme, sforce, visc;
+    long long base;
+    R rho_A, rho_B, drho, inv_nu_A, inv_nu_B, mu_A, mu_B, beta, kappa, eta, gammaM;
+    R inv_tau_h, src_h;   // 1/tau_h and 1 - 1/(2 tau_h)
+    R force_x, force_y, gravity;
+    R hs, ihs, gs, igs;
+
+    __device__ __forceinline__ void load(const DevInst& P) {
+        nx = P.nx; ny = P.ny; walls = P.walls; qim = P.qim; pscheme = P.pscheme;
+        sforce = P.sforce; visc = P.visc; base = P.base;
+        rho_A = R(P.rho_A); rho_B = R(P.rho_B); drho = R(P.drho);
+        inv_nu_A = R(P.inv_nu_A); inv_nu_B = R(P.inv_nu_B); mu_A = R(P.mu_A); mu_B = R(P.mu_B);
+        beta = R(P.beta); kappa = R(P.kappa); eta = R(P.eta); gammaM = R(P.gammaM);
+        inv_tau_h = R(P.inv_tau_h); src_h = R(1) - R(0.5) * R(P.inv_tau_h);
+        force_x = R(P.force_x); force_y = R(P.force_y); gravity = R(P.gravity);
+        hs = R(P.h_scale); ihs = R(1.0 / P.h_scale); gs = R(P.g_scale); igs = R(1.0 / P.g_scale);
+    }
+};
+
+// Chemical potential, Eq. 8.
+template <typename R>
+__device__ __forceinline__ R chem_pot(const Consts<R>& C, R phi, R lap_phi) {
+    return R(4) * C.beta * phi * (phi - R(1)) * (phi - R(0.5)) - C.kappa * lap_phi;
+}
+
+// 3x3 neighbourhood z[dy+1][dx+1] of a field around a cell.
+template <typename R>
+struct Nbr {
+    R z[3][3];
+    // Isotropic gradient, Eq. 30a: sum_{i!=0} w_i c_i z(x + c_i) / c_s^2.
+    __device__ __forceinline__ void grad(R& gx, R& gy) const {
+        const R w1 = R(3) / R(9), w2 = R(3) / R(36);   // w_i / c_s^2
+        gx = w1 * (z[1][2] - z[1][0]) + w2 * ((z[2][2] - z[2][0]) + (z[0][2] - z[0][0]));
+        gy = w1 * (z[2][1] - z[0][1]) + w2 * ((z[2][2] - z[0][2]) + (z[2][0] - z[0][0]));
+    }
+    // Isotropic Laplacian, Eq. 30b: sum_{i!=0} 2 w_i (z(x + c_i) - z(x)) / c_s^2.
+    __device__ __forceinline__ R lap() const {
+        const R c = z[1][1];
+        const R a = (z[1][2] - c) + (z[2][1] - c) + (z[1][0] - c) + (z[0][1] - c);
+        const R d = (z[2][2] - c) + (z[2][0] - c) + (z[0][0] - c) + (z[0][2] - c);
+        return (R(6) / R(9)) * a + (R(6) / R(36)) * d;
+    }
+};
+
+// Macroscopic stage of one cell (steps 1-6 of the time step): inputs are the
+// post-streaming g, phi, mu and the stencils of phi, mu and p_prev.
+template <typename R>
+struct Macro {
+    R rho, ux, uy, Fx, Fy, Ftx, Fty, S, S1, tgm /* tau_g - 1/2 */, inv_tau_g, p;
+};
+
+template <typename R>
+__device__ __forceinline__ Macro<R> macroscopic(const Consts<R>& C, const R g[9], R phi, R mu,
+                                                R gphix, R gphiy, R gmux, R gmuy, R lapmu,
+                                                R gpx, R gpy) {
+    Macro<R> m;
+    m.rho = C.rho_B + phi * C.drho;                     // Eq. 3aa (phi_B = 0)
+    const R drx = C.drho * gphix, dry = C.drho * gphiy; // grad rho
+    m.S1 = C.qim ? -C.gammaM * lapmu : R(0);            // Sec. 3.2.1
+    R Fsx, Fsy;                                         // surface tension
+    if (C.sforce == 0) { Fsx = mu * gphix; Fsy = mu * gphiy; }
+    else { Fsx = -phi * gmux; Fsy = -phi * gmuy; }
+    m.Fx = Fsx + C.force_x;
+    m.Fy = Fsy + C.force_y - (m.rho - C.rho_A) * C.gravity;   // buoyancy, Sec. 4.4
+    const R jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const R jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    const R inv_rho = R(1) / m.rho;
+    m.ux = (jx + R(0.5) * m.Fx) * inv_rho;              // Eq. 27a
+    m.uy = (jy + R(0.5) * m.Fy) * inv_rho;
+    m.S = m.ux * drx + m.uy * dry + m.rho * m.S1;       // S = u.grad(rho) + rho S1
+    R nu;                                               // viscosity, Sec. 3.2.2 / 4.3
+    if (C.visc == 0) nu = R(1) / (phi * (C.inv_nu_A - C.inv_nu_B) + C.inv_nu_B);
+    else nu = (phi >= R(0.5) ? C.mu_A : C.mu_B) * inv_rho;
+    m.tgm = R(3) * nu;                                  // tau_g - 1/2 = nu / c_s^2
+    m.inv_tau_g = R(1) / (m.tgm + R(0.5));
+    m.Ftx = m.Fx - gpx + drx * (R(1) / R(3));           // F~ = F - grad(p - rho c_s^2)
+    m.Fty = m.Fy - gpy + dry * (R(1) / R(3));
+    const R w0 = w_of<R>(0);
+    R G0 = R(0);
+    if (C.pscheme == 0) {         // simplified G_0 printed after Eq. 34
+        G0 = w0 * (R(0.5) * m.rho * m.S1 - R(3) * (m.ux * (m.Fx - gpx) + m.uy * (m.Fy - gpy)));
+    } else if (C.pscheme == 1) {  // Eq. 34 at i = 0
+        G0 = w0 * (m.S - R(3) * (m.ux * m.Ftx + m.uy * m.Fty) - m.rho * m.S1);
+    }
+    const R sum_g = (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+    const R uu = m.ux * m.ux + m.uy * m.uy;
+    const R s0 = -w0 * R(1.5) * uu;                     // s_0(u)
+    // Eq. 28 (Eq. 29 for the previous scheme): c_s^2 / (1 - w0) = 3/5
+    m.p = R(0.6) * (sum_g + R(0.5) * m.S + m.rho * s0 + m.tgm * G0);
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel.
+template <int FORM, int TX>
+struct StepSmem {
+    using R = typename Form<FORM>::R;
+    static constexpr int PW = TX + 4;   // phi ring row: strip + 2-column halo each side
+    static constexpr int MW = TX + 2;   // mu / p ring row: strip + 1-column halo
+    static constexpr size_t elems = 5 * PW + 3 * MW + 4 * MW + 4 * 9 * TX;
+    static constexpr size_t bytes = elems * sizeof(R);
+};
+
+__device__ __forceinline__ int ring5(int y) { return (y + 40) % 5; }
+__device__ __forceinline__ int ring4(int y) { return (y + 40) & 3; }
+__device__ __forceinline__ int ring3(int y) { return (y + 42) % 3; }
+
+template <int FORM, int TX>
+__global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
+    using F = Form<FORM>;
+    using R = typename F::R;
+    using AT = typename F::AT;
+    using SM = StepSmem<FORM, TX>;
+    constexpr int PW = SM::PW, MW = SM::MW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* phiR = reinterpret_cast<R*>(smem_raw);   // [5][PW]
+    R* muR = phiR + 5 * PW;                      // [3][MW]
+    R* pR = muR + 3 * MW;                        // [4][MW]
+    R* hR = pR + 4 * MW;                         // [4][9][TX]
+
+    const WorkItem wk = a.work[blockIdx.x];
+    Consts<R> C;
+    C.load(a.inst[wk.inst]);
+    const int nx = C.nx, ny = C.ny, walls = C.walls;
+    const int x0 = wk.x0, d = wk.dir;
+    const int w = min(TX, nx - x0);
+    const int tid = threadIdx.x;
+    const long long S = a.S, base = C.base;
+
+    PopIO<F> io;
+    io.hin = static_cast<const typename F::HT*>(a.h_in);
+    io.hout = static_cast<typename F::HT*>(a.h_out);
+    io.h0in = static_cast<const float2*>(a.h0_in);
+    io.h0out = static_cast<float2*>(a.h0_out);
+    io.gin = static_cast<const typename F::GT*>(a.g_in);
+    io.gout = static_cast<typename F::GT*>(a.g_out);
+    io.S = S; io.hs = C.hs; io.ihs = C.ihs; io.gs = C.gs; io.igs = C.igs;
+    const AT* p_in = static_cast<const AT*>(a.p_in);
+    AT* p_out = static_cast<AT*>(a.p_out);
+    AT* phiu = static_cast<AT*>(a.phiu);
+
+    auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+    auto rowg = [ny, walls](int y) { return walls ? y : (y < 0 ? y + ny : (y >= ny ? y - ny : y)); };
+    auto ghost = [ny, walls](int y) { return walls && (y < 0 || y >= ny); };
+    auto mirror = [ny](int y) { return y < 0 ? -1 - y : 2 * ny - 1 - y; };
+
+    // A. phi of row L over columns x0-2 .. x0+w+1; h of the strip kept for the collision.
+    auto lead_row = [&](int L) {
+        R* prow = phiR + ring5(L) * PW;
+        if (ghost(L)) {   // mirror ghost row next to a wall (reading Q7)
+            const R* src = phiR + ring5(mirror(L)) * PW;
+            for (int s = tid; s < w + 4; s += TX) prow[s] = src[s];
+            return;
+        }
+        const long long row = base + (long long)rowg(L) * nx;
+        R* hrow = hR + ring4(L) * 9 * TX;
+        for (int s = tid; s < w + 4; s += TX) {
+            const long long c = row + wrapx(x0 - 2 + s);
+            R hv[9], phi_lo;
+            const R phi = io.phi_of(c, hv, phi_lo);          // Eq. 18
+            prow[s] = phi;
+            if (s >= 2 && s < w + 2) {
+                // conservative forms keep the low part of phi where h_0 would go
+                if constexpr (F::cons) hv[0] = phi_lo;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hrow[i * TX + (s - 2)] = hv[i];
+            }
+        }
+    };
+    // p of the previous step, row M, columns x0-1 .. x0+w (mirror ghost at walls).
+    auto p_row = [&](int M) {
+        const int gy = ghost(M) ? mirror(M) : rowg(M);
+        const AT* src = p_in + base + (long long)gy * nx;
+        R* dst = pR + ring4(M) * MW;
+        for (int s = tid; s < w + 2; s += TX) dst[s] = R(src[wrapx(x0 - 1 + s)]);
+    };
+    // B. mu of row M (Eq. 8 with the Laplacian of Eq. 30b), columns x0-1 .. x0+w.
+    auto mu_row = [&](int M) {
+        R* mrow = muR + ring3(M) * MW;
+        if (ghost(M)) {
+            const R* src = muR + ring3(mirror(M)) * MW;
+            for (int s = tid; s < w + 2; s += TX) mrow[s] = src[s];
+            return;
+        }
+        const R* r0 = phiR + ring5(M - 1) * PW;
+        const R* r1 = phiR + ring5(M) * PW;
+        const R* r2 = phiR + ring5(M + 1) * PW;
+        for (int s = tid; s < w + 2; s += TX) {
+            Nbr<R> n;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                n.z[0][dx] = r0[s + dx];
+                n.z[1][dx] = r1[s + dx];
+                n.z[2][dx] = r2[s + dx];
+            }
+            mrow[s] = chem_pot(C, n.z[1][1], n.lap());
+        }
+    };
+    // C. collision and push-streaming of row Y.
+    auto collide_row = [&](int Y) {
+        if (tid >= w) return;
+        const int X = x0 + tid;
+        const long long c = base + (long long)rowg(Y) * nx + X;
+        Nbr<R> nphi, nmu, np;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const R* pr = phiR + ring5(Y + dy - 1) * PW + tid + 1;
+            const R* mr = muR + ring3(Y + dy - 1) * MW + tid;
+            const R* qr = pR + ring4(Y + dy - 1) * MW + tid;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                nphi.z[dy][dx] = pr[dx];
+                nmu.z[dy][dx] = mr[dx];
+                np.z[dy][dx] = qr[dx];
+            }
+        }
+        const R phi = nphi.z[1][1], mu = nmu.z[1][1];
+        R gphix, gphiy, gmux, gmuy, gpx, gpy;
+        nphi.grad(gphix, gphiy);
+        nmu.grad(gmux, gmuy);
+        np.grad(gpx, gpy);
+        const R lapmu = nmu.lap();
+        R g[9], h[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = io.load_g(i, c);
+        const R* hrow = hR + ring4(Y) * 9 * TX + tid;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i] = hrow[i * TX];
+        const R pux = R(phiu[c]), puy = R(phiu[S + c]);
+
+        const Macro<R> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
+
+        // Collision of g (Eq. 24) with g^eq (Eq. 33, rho_0 = 0) and G_i (Eq. 34).
+        const R uu = m.ux * m.ux + m.uy * m.uy;
+        const R uFt = m.ux * m.Ftx + m.uy * m.Fty;
+        const R gsrc = R(1) - R(0.5) * m.inv_tau_g;
+        const R phiux = phi * m.ux, phiuy = phi * m.uy;
+        const R ddx = phiux - pux, ddy = phiuy - puy;     // d_t(phi u), first-order backward
+        const R etamu = C.eta * mu;
+        R hpost[9], gpost[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R wi = w_of<R>(i);
+            const R ex = R(cx_of(i)), ey = R(cy_of(i));
+            const R cu = ex * m.ux + ey * m.uy;
+            const R si = wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+            const R geq = (i == 0) ? (wi - R(1)) * R(3) * m.p + m.rho * si
+                                   : R(3) * wi * m.p + m.rho * si;
+            const R cF = ex * m.Fx + ey * m.Fy;
+            const R cFt = ex * m.Ftx + ey * m.Fty;
+            const R c2 = ex * ex + ey * ey;
+            const R Gi = wi * (m.S + R(3) * cF + R(4.5) * (R(2) * cu * cFt - (R(2) / R(3)) * uFt) +
+                               R(1.5) * (c2 - R(2) / R(3)) * m.rho * m.S1);
+            gpost[i] = g[i] - (g[i] - geq) * m.inv_tau_g + gsrc * Gi;
+            // Collision of h (Eq. 10) with h^eq (Eq. 11) and R_i (Eq. 14).
+            const R heq = (i == 0) ? phi + (wi - R(1)) * etamu
+                                   : wi * etamu + R(3) * wi * (ex * phiux + ey * phiuy);
+            const R Ri = C.src_h * R(3) * wi * (ex * ddx + ey * ddy);
+            hpost[i] = h[i] - (h[i] - heq) * C.inv_tau_h + Ri;
+        }
+        float2 h0c = make_float2(0.f, 0.f);
+        if constexpr (F::cons) {
+            // h_0 absorbs the storage rounding of h_1..h_8: the stored populations
+            // of this cell still sum to phi (collision conserves phi: sum h^eq = phi,
+            // sum R_i = 0), so rounding cannot change sum(phi).
+            R rest = R(0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                hpost[i] = io.round_h(hpost[i]);
+                rest += hpost[i];
+            }
+            h0c = io.conservative_h0(phi, h[0] /* low part of phi */, rest);
+        }
+        // Push-streaming: population i moves to x + c_i; into a wall it comes back
+        // reversed at x (halfway bounce-back, Sec. 4.3).
+        const int gyY = rowg(Y);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int yt = Y + cy_of(i);
+            long long dst;
+            int k = i;
+            if (walls && (yt < 0 || yt >= ny)) {
+                dst = c;
+                k = opp_of(i);
+            } else {
+                dst = base + (long long)(cy_of(i) == 0 ? gyY : rowg(yt)) * nx + wrapx(X + cx_of(i));
+            }
+            if constexpr (F::cons) {
+                if (i == 0) io.store_h0(dst, h0c);
+                else io.store_h(k, dst, hpost[i]);
+            } else {
+                io.store_h(k, dst, hpost[i]);
+            }
+            io.store_g(k, dst, gpost[i]);
+        }
+        phiu[c] = AT(phiux);
+        phiu[S + c] = AT(phiuy);
+        p_out[c] = AT(m.p);
+    };
+
+    const int Y0 = wk.ystart;
+    // Prologue: phi rows Y0-2d .. Y0+d, mu rows Y0-d .. Y0, p rows Y0-d .. Y0.
+    // Rows inside the domain first: a ghost row (beyond a wall, on either side
+    // of Y0) copies its mirror row, which must exist by then.
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 1; k >= -2; --k)
+            if (ghost(Y0 + k * d) == (pass == 1)) lead_row(Y0 + k * d);
+    p_row(Y0 - d);
+    p_row(Y0);
+    __syncthreads();
+    mu_row(Y0);
+    mu_row(Y0 - d);
+    __syncthreads();
+    for (int k = 0; k < wk.nrows; ++k) {
+        const int Y = Y0 + k * d;
+        lead_row(Y + 2 * d);
+        p_row(Y + d);
+        __syncthreads();
+        mu_row(Y + d);
+        __syncthreads();
+        collide_row(Y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (reading Q6): h = h^eq(phi0, mu0, u = 0), g = g^eq(p = 0, u = 0)
+// (all zero with rho_0 = 0), phi*u of the previous step 0, p 0.
+template <int FORM>
+__global__ void init_kernel(const StepArgs a, const double* __restrict__ phi0, int instance) {
+    using F = Form<FORM>;
+    using R = typename F::R;
+    using AT = typename F::AT;
+    Consts<R> C;
+    C.load(a.inst[instance]);
+    PopIO<F> io;
+    io.hout = static_cast<typename F::HT*>(a.h_out);
+    io.h0out = static_cast<float2*>(a.h0_out);
+    io.gout = static_cast<typename F::GT*>(a.g_out);
+    io.S = a.S; io.hs = C.hs; io.ihs = C.ihs; io.gs = C.gs; io.igs = C.igs;
+    AT* phiu = static_cast<AT*>(a.phiu);
+    AT* p0 = static_cast<AT*>(a.p_out);
+    AT* p1 = static_cast<AT*>(const_cast<void*>(a.p_in));
+    const int n = C.nx * C.ny;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n; cell += gridDim.x * blockDim.x) {
+        const int x = cell % C.nx, y = cell / C.nx;
+        Nbr<R> nb;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int yy = y + dy, xx = x + dx;
+                xx = xx < 0 ? xx + C.nx : (xx >= C.nx ? xx - C.nx : xx);
+                if (C.walls) yy = yy < 0 ? -1 - yy : (yy >= C.ny ? 2 * C.ny - 1 - yy : yy);
+                else yy = yy < 0 ? yy + C.ny : (yy >= C.ny ? yy - C.ny : yy);
+                nb.z[dy + 1][dx + 1] = R(phi0[yy * C.nx + xx]);
+            }
+        const R phi = nb.z[1][1];
+        const R mu = chem_pot(C, phi, nb.lap());
+        const R etamu = C.eta * mu;
+        const long long c = C.base + cell;
+        R hv[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hv[i] = (i == 0) ? phi + (w_of<R>(0) - R(1)) * etamu : w_of<R>(i) * etamu;
+        if constexpr (F::cons) {
+            // h_0 = phi_0 - sum of the stored h_1..8, exactly as a float pair
+            double rest = 0.0;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) { hv[i] = io.round_h(hv[i]); rest += double(hv[i]); }
+            const double h0 = phi0[cell] - rest;
+            const float hi = float(h0);
+            io.store_h0(c, make_float2(hi, float(h0 - double(hi))));
+        } else {
+            io.store_h(0, c, hv[0]);
+        }
+#pragma unroll
+        for (int i = 1; i < 9; ++i) io.store_h(i, c, hv[i]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) io.store_g(i, c, R(0));
+        phiu[c] = AT(0);
+        phiu[a.S + c] = AT(0);
+        p0[c] = AT(0);
+        p1[c] = AT(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic fields and diagnostics of one instance, in three passes over
+// global memory (phi, then mu, then everything else) -- off the hot loop.
+template <int FORM>
+__global__ void phi_pass(const AuxArgs a) {
+    using F = Form<FORM>;
+    using R = typename F::R;
+    Consts<R> C;
+    C.load(a.inst[a.instance]);
+    PopIO<F> io;
+    io.hin = static_cast<const typename F::HT*>(a.h);
+    io.h0in = static_cast<const float2*>(a.h0);
+    io.S = a.S; io.hs = C.hs; io.ihs = C.ihs;
+    const int n = C.nx * C.ny;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n; cell += gridDim.x * blockDim.x) {
+        const long long c = C.base + cell;
+        R hv[9], lo;
+        const R phi = io.phi_of(c, hv, lo);
+        a.tmp_phi[cell] = double(phi) + double(lo);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void gather(const double* f, int nx, int ny, int walls, int x, int y,
+                                       Nbr<R>& nb) {
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int yy = y + dy, xx = x + dx;
+            xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+            if (walls) yy = yy < 0 ? -1 - yy : (yy >= ny ? 2 * ny - 1 - yy : yy);
+            else yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+            nb.z[dy + 1][dx + 1] = R(f[yy * nx + xx]);
+        }
+}
+
+template <int FORM>
+__global__ void mu_pass(const AuxArgs a) {
+    using R = typename Form<FORM>::R;
+    Consts<R> C;
+    C.load(a.inst[a.instance]);
+    const int n = C.nx * C.ny;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n; cell += gridDim.x * blockDim.x) {
+        Nbr<R> nb;
+        gather(a.tmp_phi, C.nx, C.ny, C.walls, cell % C.nx, cell / C.nx, nb);
+        a.tmp_mu[cell] = double(chem_pot(C, nb.z[1][1], nb.lap()));
+    }
+}
+
+// Everything one cell's macroscopic stage produces, plus the Laplace-law P of Sec. 4.2.
+template <int FORM>
+__device__ __forceinline__ void cell_fields(const AuxArgs& a, const Consts<typename Form<FORM>::R>& C,
+                                            int cell, typename Form<FORM>::R out[7], bool& finite) {
+    using F = Form<FORM>;
+    using R = typename F::R;
+    using AT = typename F::AT;
+    PopIO<F> io;
+    io.hin = static_cast<const typename F::HT*>(a.h);
+    io.h0in = static_cast<const float2*>(a.h0);
+    io.gin = static_cast<const typename F::GT*>(a.g);
+    io.S = a.S; io.hs = C.hs; io.ihs = C.ihs; io.gs = C.gs; io.igs = C.igs;
+    const int x = cell % C.nx, y = cell / C.nx;
+    const long long c = C.base + cell;
+    Nbr<R> nphi, nmu;
+    gather(a.tmp_phi, C.nx, C.ny, C.walls, x, y, nphi);
+    gather(a.tmp_mu, C.nx, C.ny, C.walls, x, y, nmu);
+    Nbr<R> np;
+    const AT* pp = static_cast<const AT*>(a.p_prev) + C.base;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int yy = y + dy, xx = x + dx;
+            xx = xx < 0 ? xx + C.nx : (xx >= C.nx ? xx - C.nx : xx);
+            if (C.walls) yy = yy < 0 ? -1 - yy : (yy >= C.ny ? 2 * C.ny - 1 - yy : yy);
+            else yy = yy < 0 ? yy + C.ny : (yy >= C.ny ? yy - C.ny : yy);
+            np.z[dy + 1][dx + 1] = R(pp[yy * C.nx + xx]);
+        }
+    R g[9], hv[9], lo;
+    io.phi_of(c, hv, lo);
+    finite = isfinite(lo);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        g[i] = io.load_g(i, c);
+        finite = finite && isfinite(g[i]) && isfinite(hv[i]);
+    }
+    R gphix, gphiy, gmux, gmuy, gpx, gpy;
+    nphi.grad(gphix, gphiy);
+    nmu.grad(gmux, gmuy);
+    np.grad(gpx, gpy);
+    const R phi = nphi.z[1][1], mu = nmu.z[1][1];
+    const Macro<R> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, nmu.lap(), gpx, gpy);
+    // P = p_0 - kappa phi lap(phi) + kappa |grad phi|^2 / 2 + p, p_0 = phi psi' - psi (Sec. 4.2)
+    const R psi = C.beta * phi * phi * (phi - R(1)) * (phi - R(1));
+    const R dpsi = R(2) * C.beta * phi * (phi - R(1)) * (R(2) * phi - R(1));
+    const R Plap = (phi * dpsi - psi) - C.kappa * phi * nphi.lap() +
+                   R(0.5) * C.kappa * (gphix * gphix + gphiy * gphiy) + m.p;
+    out[0] = phi; out[1] = m.ux; out[2] = m.uy; out[3] = m.p; out[4] = m.rho; out[5] = mu;
+    out[6] = Plap;
+}
+
+template <int FORM>
+__global__ void fields_pass(const AuxArgs a) {
+    using R = typename Form<FORM>::R;
+    Consts<R> C;
+    C.load(a.inst[a.instance]);
+    const int n = C.nx * C.ny;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n; cell += gridDim.x * blockDim.x) {
+        R v[7];
+        bool fin;
+        cell_fields<FORM>(a, C, cell, v, fin);
+        int k = 0;
+        for (int b = 0; b < 7; ++b)
+            if (a.mask & (1u << b)) a.out[(long long)(k++) * n + cell] = double(v[b]);
+    }
+}
+
+// Diagnostics: per-block FP64 partial sums written to a.partials (scratch,
+// kDiagBlocks x kDiagQuantities), then one block adds the partials in a fixed
+// order, so the result does not depend on timing.
+//   0 sum phi, 1 sum rho, 2 kinetic energy, 3 max |u|, 4 sum phi x, 5 sum phi y,
+//   6 sum (1-phi) x, 7 sum (1-phi) y, 8 sum P (bulk A), 9 n bulk A,
+//   10 sum P (bulk B), 11 n bulk B, 12 non-finite count, 13 sum (1 - phi)
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256) diag_pass(const AuxArgs a) {
+    using R = typename Form<FORM>::R;
+    Consts<R> C;
+    C.load(a.inst[a.instance]);
+    const int n = C.nx * C.ny;
+    double acc[kDiagQuantities];
+#pragma unroll
+    for (int q = 0; q < kDiagQuantities; ++q) acc[q] = 0.0;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n; cell += gridDim.x * blockDim.x) {
+        R v[7];
+        bool fin;
+        cell_fields<FORM>(a, C, cell, v, fin);
+        const double phi = double(v[0]), ux = double(v[1]), uy = double(v[2]);
+        const double rho = double(v[4]), P = double(v[6]);
+        const double x = double(cell % C.nx), y = double(cell / C.nx);
+        const double uu = ux * ux + uy * uy;
+        acc[0] += phi;
+        acc[1] += rho;
+        acc[2] += 0.5 * rho * uu;
+        acc[3] = fmax(acc[3], sqrt(uu));
+        acc[4] += phi * x;
+        acc[5] += phi * y;
+        acc[6] += (1.0 - phi) * x;
+        acc[7] += (1.0 - phi) * y;
+        if (phi > 1.0 - 1e-3) { acc[8] += P; acc[9] += 1.0; }
+        if (phi < 1e-3) { acc[10] += P; acc[11] += 1.0; }
+        if (!fin) acc[12] += 1.0;
+        acc[13] += 1.0 - phi;
+    }
+    __shared__ double red[kDiagQuantities][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kDiagQuantities; ++q) {
+        const double v = (q == 3) ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiagQuantities) {
+        const int q = threadIdx.x;
+        double v = red[q][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = (q == 3) ? fmax(v, red[q][k]) : v + red[q][k];
+        a.partials[blockIdx.x * kDiagQuantities + q] = v;
+    }
+}
+
+static __global__ void diag_final(const double* __restrict__ partials, int nblocks, double* __restrict__ result) {
+    const int q = threadIdx.x;
+    if (q >= kDiagQuantities) return;
+    double v = partials[q];
+    for (int b = 1; b < nblocks; ++b) {
+        const double x = partials[b * kDiagQuantities + q];
+        v = (q == 3) ? fmax(v, x) : v + x;
+    }
+    result[q] = v;
+}
+
+template <int FORM>
+__global__ void populations_pass(const AuxArgs a, double* out_h, double* out_g) {
+    using F = Form<FORM>;
+    using R = typename F::R;
+    Consts<R> C;
+    C.load(a.inst[a.instance]);
+    PopIO<F> io;
+    io.hin = static_cast<const typename F::HT*>(a.h);
+    io.h0in = static_cast<const float2*>(a.h0);
+    io.gin = static_cast<const typename F::GT*>(a.g);
+    io.S = a.S; io.hs = C.hs; io.ihs = C.ihs; io.gs = C.gs; io.igs = C.igs;
+    const int n = C.nx * C.ny;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n; cell += gridDim.x * blockDim.x) {
+        const long long c = C.base + cell;
+        for (int i = 0; i < 9; ++i) {
+            if (out_h) {
+                double v;
+                if (F::cons && i == 0) {
+                    const float2 h0 = io.load_h0(c);
+                    v = double(h0.x) + double(h0.y);
+                } else {
+                    v = double(io.load_h(i, c));
+                }
+                out_h[(long long)i * n + cell] = v;
+            }
+            if (out_g) out_g[(long long)i * n + cell] = double(io.load_g(i, c));
+        }
+    }
+}
+
+}  // namespace lbm

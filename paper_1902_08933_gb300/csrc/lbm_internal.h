@@ -1,0 +1,78 @@
+// lbm_internal.h -- types shared by the host API and the kernel translation units.
+// Not part of the public ABI (include/lbm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Per-instance constants, derived on the host from lbm_params (Eqs. 6-7, 17,
+// gamma of Sec. 3.2.1), read once per thread block.
+struct DevInst {
+    long long base;          // first cell of the instance inside every SoA plane
+    int nx, ny;
+    int walls;               // 1: halfway bounce-back walls in y
+    int qim;                 // 1: S1 = -gamma M lap(mu)
+    int pscheme;             // LBM_P_*
+    int sforce;              // LBM_FS_*
+    int visc;                // LBM_VISC_*
+    int pad;
+    double rho_A, rho_B, drho;       // drho = (rho_A - rho_B) / (phi_A - phi_B)
+    double inv_nu_A, inv_nu_B;       // inverse-linear viscosity
+    double mu_A, mu_B;               // dynamic viscosities rho nu (step model)
+    double beta, kappa, eta;
+    double gammaM;                   // gamma * M_phi
+    double inv_tau_h;
+    double force_x, force_y, gravity;
+    double h_scale, g_scale;         // storage scales of reduced-precision forms (powers of 2)
+};
+
+// One thread block's work: a strip of columns [x0, x0 + TX) (clipped to nx) of
+// one instance, marching over nrows rows from ystart in direction dir (+1/-1).
+struct WorkItem {
+    int inst, x0, ystart, nrows, dir, pad;
+};
+
+// Device buffers of one step (ping-pong: *_in is time t, *_out time t + 1).
+struct StepArgs {
+    const void* h_in;  void* h_out;     // 9 planes (h_1..h_8 only for conservative forms)
+    const void* h0_in; void* h0_out;    // conservative forms: h_0 as float2 (hi, lo), else null
+    const void* g_in;  void* g_out;     // 9 planes
+    void* phiu;                         // 2 planes, updated in place
+    const void* p_in;  void* p_out;     // 1 plane each
+    long long S;                        // plane stride in cells
+    const DevInst* inst;
+    const WorkItem* work;
+};
+
+// Buffers of the macroscopic / diagnostic kernels.
+struct AuxArgs {
+    const void* h; const void* h0; const void* g; const void* phiu; const void* p_prev;
+    long long S;
+    const DevInst* inst;
+    int instance;
+    double* tmp_phi;      // nx*ny scratch
+    double* tmp_mu;       // nx*ny scratch
+    double* out;          // field outputs (fields kernel)
+    unsigned mask;
+    double* partials;     // diagnostics: per-block partial sums
+    double* result;       // diagnostics: final record
+};
+
+constexpr int kDiagQuantities = 14;   // quantities of diag_pass (lbm_device.cuh)
+constexpr int kDiagBlocks = 304;      // 2 x 152 SMs
+
+// Launchers, instantiated once per storage form in lbm_form<N>.cu.
+template <int FORM> cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s);
+template <int FORM> cudaError_t prepare_step_t();          // opt-in shared memory sizes
+template <int FORM> size_t step_smem_t(int tile_x);
+template <int FORM> int step_occupancy_t(int tile_x);      // resident blocks per SM
+template <int FORM> cudaError_t launch_init_t(const StepArgs& a, const double* phi0, int instance,
+                                              int ncells, cudaStream_t s);
+template <int FORM> cudaError_t launch_fields_t(const AuxArgs& a, int ncells, cudaStream_t s);
+template <int FORM> cudaError_t launch_diag_t(const AuxArgs& a, int ncells, cudaStream_t s);
+template <int FORM> cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h,
+                                                     double* out_g, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,278 @@
+"""ctypes binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every computation runs in liblbm.so's CUDA kernels; this module converts
+Python arguments to the C types and status codes to exceptions. If the library
+is missing the first call raises: there is no CPU fallback.
+
+Functions carry the C names (``lbm_create``, ``lbm_init``, ``lbm_step``,
+``lbm_get_fields``, ...). ``Simulation`` is a small convenience wrapper over
+them for the tests and the benchmark.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+# enums of include/lbm.h
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
+LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
+LBM_IM, LBM_QIM = 0, 1
+LBM_P_MODIFIED_PRINTED, LBM_P_MODIFIED_LITERAL, LBM_P_PREVIOUS = 0, 1, 2
+LBM_FS_MU_GRADPHI, LBM_FS_PHI_GRADMU = 0, 1
+LBM_VISC_INV_LINEAR, LBM_VISC_STEP = 0, 1
+LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C = 0, 1, 2, 3, 4
+FIELDS = ("phi", "ux", "uy", "p", "rho", "mu", "P")
+FIELD_BITS = {name: 1 << k for k, name in enumerate(FIELDS)}
+FORMS = {"f64": LBM_F64, "f32": LBM_F32, "f32_g16": LBM_F32_G16, "f32_h16": LBM_F32_H16,
+         "f32_c": LBM_F32_C}
+# bytes moved per lattice update (every population read and written once, plus phi*u, p)
+BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176}
+
+_STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
+           5: "LBM_ETIMEOUT", 6: "LBM_ESTATE", 7: "LBM_EIO"}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("pressure_scheme", ctypes.c_int32),
+                ("surface_force", ctypes.c_int32), ("viscosity_model", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)] + [
+        (n, ctypes.c_double) for n in ("rho_A", "rho_B", "nu_A", "nu_B", "sigma", "W", "tau_h",
+                                       "mobility", "force_x", "force_y", "gravity")]
+
+
+class lbm_diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "sum_phi", "sum_rho", "kinetic_energy", "max_u", "centroid_A_x", "centroid_A_y",
+        "centroid_B_x", "centroid_B_y", "mass_A", "mass_B", "P_bulk_A", "P_bulk_B",
+        "n_bulk_A", "n_bulk_B")] + [("nonfinite", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                                     ("time", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+
+# (name, restype, argtypes) of every entry point declared in include/lbm.h
+SIGNATURES = [
+    ("lbm_validate_params", ctypes.c_int, [ctypes.POINTER(lbm_params)]),
+    ("lbm_create", ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int, ctypes.c_int, _VP,
+                                  ctypes.POINTER(_VP)]),
+    ("lbm_init", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
+    ("lbm_init_device", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_get_fields", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _DP]),
+    ("lbm_get_fields_device", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _VP]),
+    ("lbm_diagnostics", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_diag)]),
+    ("lbm_get_populations", ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
+    ("lbm_save", ctypes.c_int, [_VP, ctypes.c_char_p]),
+    ("lbm_load", ctypes.c_int, [_VP, ctypes.c_char_p]),
+    ("lbm_set_launch", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("lbm_autotune", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_launches_per_step", ctypes.c_int, [_VP]),
+    ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
+    ("lbm_sync", ctypes.c_int, [_VP]),
+    ("lbm_last_error", ctypes.c_char_p, [_VP]),
+    ("lbm_destroy", None, [_VP]),
+]
+
+
+def library():
+    """Load liblbm.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("liblbm.so not found at %s; build it with "
+                                   "`python -m paper_1902_08933_gb300.build`" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st, ctx=None):
+    if st != LBM_OK:
+        msg = library().lbm_last_error(ctx).decode() if ctx else ""
+        raise LbmError(st, msg)
+
+
+def make_params(cfg: dict) -> lbm_params:
+    """lbm_params from a workload dictionary (keys of workloads.PARAM_KEYS)."""
+    p = lbm_params()
+    p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
+    p.bc_y = int(cfg.get("walls_y", 0))
+    p.variant = int(cfg.get("qim", 1))
+    p.pressure_scheme = int(cfg.get("pressure", 0))
+    p.surface_force = int(cfg.get("surface_force", 0))
+    p.viscosity_model = int(cfg.get("viscosity", 0))
+    p.reserved = 0
+    for k, src in (("rho_A", "rho_A"), ("rho_B", "rho_B"), ("nu_A", "nu_A"), ("nu_B", "nu_B"),
+                   ("sigma", "sigma"), ("W", "W"), ("tau_h", "tau_h"), ("mobility", "M"),
+                   ("force_x", "force_x"), ("force_y", "force_y"), ("gravity", "gravity")):
+        setattr(p, k, float(cfg.get(src, 0.0)))
+    return p
+
+
+# ---- thin wrappers with the C names ---------------------------------------------
+def lbm_validate_params(p: lbm_params) -> int:
+    return library().lbm_validate_params(ctypes.byref(p))
+
+
+def lbm_create(params, precision=LBM_F64, stream=None):
+    arr = (lbm_params * len(params))(*params)
+    out = _VP()
+    st = library().lbm_create(arr, len(params), int(precision), _VP(stream or 0), ctypes.byref(out))
+    _check(st)
+    return out.value
+
+
+def lbm_init(ctx, instance, phi0: np.ndarray):
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    _check(library().lbm_init(ctx, instance, phi0.ctypes.data_as(_DP)), ctx)
+
+
+def lbm_init_device(ctx, instance, dev_ptr: int):
+    _check(library().lbm_init_device(ctx, instance, _VP(dev_ptr)), ctx)
+
+
+def lbm_step(ctx, nsteps: int):
+    _check(library().lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_get_fields(ctx, instance, mask: int, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(library().lbm_get_fields(ctx, instance, mask, out.ctypes.data_as(_DP)), ctx)
+
+
+def lbm_get_fields_device(ctx, instance, mask: int, dev_ptr: int):
+    _check(library().lbm_get_fields_device(ctx, instance, mask, _VP(dev_ptr)), ctx)
+
+
+def lbm_diagnostics(ctx, instance) -> dict:
+    d = lbm_diag()
+    st = library().lbm_diagnostics(ctx, instance, ctypes.byref(d))
+    out = {k: getattr(d, k) for k, _ in lbm_diag._fields_ if k != "reserved"}
+    if st not in (LBM_OK, LBM_ENONFINITE):
+        _check(st, ctx)
+    out["status"] = st
+    return out
+
+
+def lbm_get_populations(ctx, instance, nx, ny):
+    h = np.zeros((9, ny, nx))
+    g = np.zeros((9, ny, nx))
+    _check(library().lbm_get_populations(ctx, instance, h.ctypes.data_as(_DP), g.ctypes.data_as(_DP)), ctx)
+    return h, g
+
+
+def lbm_save(ctx, path: str):
+    _check(library().lbm_save(ctx, path.encode()), ctx)
+
+
+def lbm_load(ctx, path: str):
+    _check(library().lbm_load(ctx, path.encode()), ctx)
+
+
+def lbm_set_launch(ctx, tile_x: int, rows: int):
+    _check(library().lbm_set_launch(ctx, int(tile_x), int(rows)), ctx)
+
+
+def lbm_autotune(ctx):
+    t, r = ctypes.c_int(), ctypes.c_int()
+    _check(library().lbm_autotune(ctx, ctypes.byref(t), ctypes.byref(r)), ctx)
+    return t.value, r.value
+
+
+def lbm_launches_per_step(ctx) -> int:
+    return library().lbm_launches_per_step(ctx)
+
+
+def lbm_time(ctx, instance) -> int:
+    return library().lbm_time(ctx, instance)
+
+
+def lbm_sync(ctx):
+    _check(library().lbm_sync(ctx), ctx)
+
+
+def lbm_last_error(ctx) -> str:
+    return library().lbm_last_error(ctx).decode()
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        library().lbm_destroy(ctx)
+
+
+class Simulation:
+    """One context over one or more workload dictionaries."""
+
+    def __init__(self, cfgs, precision="f64", stream=None, phi0=None):
+        if isinstance(cfgs, dict):
+            cfgs = [cfgs]
+        self.cfgs = list(cfgs)
+        self.precision = FORMS[precision] if isinstance(precision, str) else int(precision)
+        self.ctx = lbm_create([make_params(c) for c in self.cfgs], self.precision, stream)
+        if phi0 is not None:
+            for k, f in enumerate(phi0):
+                lbm_init(self.ctx, k, f)
+
+    def init(self, k, phi0):
+        lbm_init(self.ctx, k, phi0)
+
+    def step(self, n):
+        lbm_step(self.ctx, n)
+
+    def fields(self, k=0, names=FIELDS) -> dict:
+        c = self.cfgs[k]
+        mask = 0
+        for n in names:
+            mask |= FIELD_BITS[n]
+        order = [n for n in FIELDS if mask & FIELD_BITS[n]]
+        out = np.zeros((len(order), int(c["ny"]), int(c["nx"])))
+        lbm_get_fields(self.ctx, k, mask, out)
+        return {n: out[i] for i, n in enumerate(order)}
+
+    def diagnostics(self, k=0) -> dict:
+        return lbm_diagnostics(self.ctx, k)
+
+    def populations(self, k=0):
+        c = self.cfgs[k]
+        return lbm_get_populations(self.ctx, k, int(c["nx"]), int(c["ny"]))
+
+    def sync(self):
+        lbm_sync(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -69,7 +69,7 @@ def initial_phi(cfg: dict) -> np.ndarray:
         phi = np.full((ny, nx), float(spec["value"]))
     else:
         raise ValueError("unknown init kind %r" % kind)
-    return np.ascontiguousarray(np.broadcast_to(phi, (ny, nx)), dtype=np.float64)
+    return np.array(np.broadcast_to(phi, (ny, nx)), dtype=np.float64, order="C")
 
 
 def _nu_from_tau(tau: float) -> float:
@@ -123,18 +123,28 @@ def layered_poiseuille(nx: int = 8, ny: int = 256, rho_ratio: float = 1.0,
                 name="layered_%dx%d_r%g_m%g" % (nx, ny, rho_ratio, mu_ratio))
 
 
+def stable_mobility(M: float, rho_A: float, rho_B: float) -> float:
+    """Mobility capped at 0.2 / gamma, gamma = (rho_A - rho_B) / rho_B: the explicit
+    QIM mass source S1 = -gamma M lap(mu) made light-bubble runs diverge (already
+    in the FP64 oracle) for gamma M >~ 0.5 (reading Q10)."""
+    gamma = abs(rho_A - rho_B) / rho_B
+    return M if gamma == 0 else min(M, 0.2 / gamma)
+
+
 def rising_bubble(nx: int = 1024, ny: int = 4096, R: float = 128.0, cy: float = 512.0,
                   rho_ratio: float = 10.0, Eo: float = 10.0, Re: float = 35.0,
-                  U_g: float = 0.02, W: float = 5.0, qim: int = 1, M: float = 0.1,
+                  U_g: float = 0.01, W: float = 5.0, qim: int = 1, M: float = 0.1,
                   tau_h: float = 1.0) -> dict:
     """Light bubble (phase B) in heavy ambient A, walls at top and bottom,
     periodic sides. D = 2R, U_g = sqrt(g D): g = U_g^2 / D,
-    sigma = g (rho_A - rho_B) D^2 / Eo, nu = U_g D / Re in both phases (reading Q19)."""
+    sigma = g (rho_A - rho_B) D^2 / Eo, nu = U_g D / Re in both phases (reading Q19);
+    M capped by stable_mobility."""
     D = 2.0 * R
     g = U_g * U_g / D
     rho_A, rho_B = rho_ratio, 1.0
     sigma = g * (rho_A - rho_B) * D * D / Eo
     nu = U_g * D / Re
+    M = stable_mobility(M, rho_A, rho_B)
     return dict(nx=nx, ny=ny, walls_y=1, qim=qim, pressure=0, surface_force=0,
                 viscosity=0, rho_A=rho_A, rho_B=rho_B, nu_A=nu, nu_B=nu, sigma=sigma,
                 W=W, tau_h=tau_h, M=M, force_x=0.0, force_y=0.0, gravity=g,
@@ -146,7 +156,8 @@ def batched_mixed(n_instances: int = 512, seed: int = 4242) -> list:
     """Independent static droplets and rising bubbles on square grids drawn from
     {32, 64, 128, 256}, R = N/4, W = 4, density ratio from {2, 10, 100},
     sigma uniform in [0.001, 0.02], tau_g = tau_h = 0.8; droplets periodic with
-    M = 0.02, bubbles walled in y with M = 0.1 and gravity from Eo = 10."""
+    M = 0.02, bubbles walled in y with M = 0.1 and gravity from Eo = 10; M capped
+    by stable_mobility."""
     u = uniform01(seed, 4 * n_instances).reshape(n_instances, 4)
     sizes = (32, 64, 128, 256)
     ratios = (2.0, 10.0, 100.0)
@@ -158,16 +169,17 @@ def batched_mixed(n_instances: int = 512, seed: int = 4242) -> list:
         ratio = ratios[min(2, int(u[k, 2] * 3))]
         sigma = 0.001 + 0.019 * u[k, 3]
         R = N / 4.0
+        M_cap = stable_mobility(1.0, ratio, 1.0)
         cfg = dict(nx=N, ny=N, qim=1, pressure=0, viscosity=0, rho_A=ratio, rho_B=1.0,
                    nu_A=nu, nu_B=nu, sigma=sigma, W=4.0, tau_h=0.8, force_x=0.0, force_y=0.0)
         if bubble:
             D = 2.0 * R
-            cfg.update(walls_y=1, surface_force=0, M=0.1,
+            cfg.update(walls_y=1, surface_force=0, M=min(0.1, M_cap),
                        gravity=10.0 * sigma / ((ratio - 1.0) * D * D),
                        init=dict(kind="bubble", cx=N / 2.0, cy=0.3 * N, R=R),
                        name="batch%03d_bubble_%d_r%g" % (k, N, ratio))
         else:
-            cfg.update(walls_y=0, surface_force=1, M=0.02, gravity=0.0,
+            cfg.update(walls_y=0, surface_force=1, M=min(0.02, M_cap), gravity=0.0,
                        init=dict(kind="droplet", cx=N / 2.0, cy=N / 2.0, R=R),
                        name="batch%03d_droplet_%d_r%g" % (k, N, ratio))
         out.append(cfg)

@@ -1,0 +1,280 @@
+"""GPU (C-ABI) versus the FP64 CPU oracle, element by element on seeded inputs.
+
+Error metric (field-max normalised): max |gpu - oracle| / max |oracle| per field.
+FP64 bar: 1e-10 after the stated steps (tiny grids: 1e-12).
+The velocity is compared as a vector: max |u_gpu - u_ref| / max |u_ref|.
+FP32 bar for phi after n steps: tol32_phi(n) = 4 * 9 * 2^-24 * sqrt(n). Each of the
+nine stored h_i (|h_i| <= 1) rounds by at most 2^-24 per step, so phi = sum h_i
+picks up at most 9 * 2^-24 per step; independent roundings accumulate like a
+random walk (sqrt(n)); 4 is the margin for the largest cell. u and p: the QIM
+source S1 = -gamma M lap(mu), mu containing kappa lap(phi), is a fourth
+difference of phi, so FP32 rounding of phi (~2^-24) is amplified by ~12^2 / k^4
+relative to the field where the field is small; stated bar 2e-2 of the field
+maximum for FP32 storage and 0.1 for FP16 storage (measured values are written
+to the parity report).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_1902_08933_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_08933_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def tol32_phi(n):
+    return 4 * 9 * 2.0 ** -24 * np.sqrt(n)
+
+
+def rel(a, b):
+    den = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / (den if den > 0 else 1.0)
+
+
+def oracle_fields(orc, cfg, phi0, steps, **over):
+    P = orc.params(cfg, **over)
+    st = orc.init(P, phi0)
+    if steps:
+        orc.step(P, st, steps)
+    return orc.fields(P, st), st
+
+
+def compare(sim, k, ref, st, tol, fields=("phi", "ux", "uy", "p", "rho", "mu", "P"), pops=True,
+            report=None, tag=""):
+    got = sim.fields(k)
+    errs = {f: rel(got[f], ref[f]) for f in fields}
+    if pops:
+        h, g = sim.populations(k)
+        errs["h"] = rel(h, st["h"])
+        errs["g"] = rel(g, st["g"])
+    if report is not None:
+        report(**{tag + f: e for f, e in errs.items()})
+    bad = {f: e for f, e in errs.items() if not e <= tol}
+    assert not bad, "errors above %g: %s" % (tol, bad)
+    return errs
+
+
+def noisy(cfg, seed, amp=0.02):
+    phi = wl.initial_phi(cfg)
+    return phi + amp * (wl.uniform01(seed, phi.size).reshape(phi.shape) - 0.5)
+
+
+FLAG_SETS = list(itertools.product([0, 1], [0, 1], [0, 1, 2], [0, 1], [0, 1]))
+
+
+@pytest.mark.parametrize("walls,qim,pressure,sforce,visc", FLAG_SETS)
+def test_tiny_grids_all_flags_fp64(L, orc, walls, qim, pressure, sforce, visc):
+    cfgs = []
+    for k, (nx, ny) in enumerate([(3, 3), (5, 4), (8, 8), (37, 23)]):
+        c = wl.rising_bubble(nx=nx, ny=ny, R=max(1.0, min(nx, ny) / 4), cy=ny / 2, W=3.0, Re=5.0)
+        c.update(walls_y=walls, qim=qim, pressure=pressure, surface_force=sforce, viscosity=visc,
+                 nu_A=0.05, nu_B=0.15, force_x=1e-5, sigma=0.01)
+        cfgs.append(c)
+    phis = [noisy(c, 100 + k) for k, c in enumerate(cfgs)]
+    with L.Simulation(cfgs, "f64", phi0=phis) as sim:
+        sim.step(10)
+        for k, c in enumerate(cfgs):
+            ref, st = oracle_fields(orc, c, phis[k], 10)
+            compare(sim, k, ref, st, 1e-12)
+
+
+@pytest.mark.parametrize("tile_x,rows", [(32, 1), (32, 3), (64, 5), (128, 8), (256, 2), (128, 0)])
+def test_launch_shapes_ragged_fp64(L, orc, tile_x, rows):
+    # several strips and row runs with ragged tails, both march directions, walls and periodic
+    cfgs = [wl.rising_bubble(nx=150, ny=41, R=9, cy=14, W=4.0, Re=5.0),
+            wl.static_droplet(n=70, R=17)]
+    phis = [noisy(c, 7 + k) for k, c in enumerate(cfgs)]
+    with L.Simulation(cfgs, "f64", phi0=phis) as sim:
+        L.lbm_set_launch(sim.ctx, tile_x, rows)
+        sim.step(12)
+        for k, c in enumerate(cfgs):
+            ref, st = oracle_fields(orc, c, phis[k], 12)
+            compare(sim, k, ref, st, 1e-12)
+
+
+def test_initial_state_matches_oracle(L, orc):
+    cfg = wl.static_droplet(n=48, R=11)
+    phi0 = noisy(cfg, 5)
+    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+        ref, st = oracle_fields(orc, cfg, phi0, 0)
+        compare(sim, 0, ref, st, 1e-14)
+
+
+def test_static_droplet_fp64_2000_steps(L, orc, report):
+    cfg = wl.static_droplet()                       # 64 x 64, R = 16, ratio 10
+    phi0 = wl.initial_phi(cfg)
+    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+        sim.step(2000)
+        ref, st = oracle_fields(orc, cfg, phi0, 2000)
+        compare(sim, 0, ref, st, 1e-10, report=report, tag="f64_")
+        d = sim.diagnostics()
+        od = orc.diagnostics(orc.params(cfg), st)
+        assert abs(d["sum_phi"] - phi0.sum()) / phi0.sum() < 1e-13
+        dp, odp = d["P_bulk_A"] - d["P_bulk_B"], od["P_bulk_A"] - od["P_bulk_B"]
+        assert abs(dp - odp) <= 1e-10 * abs(odp)
+        assert d["n_bulk_A"] == od["n_bulk_A"] and d["n_bulk_B"] == od["n_bulk_B"]
+
+
+def rel_u(got, ref):
+    du = np.hypot(got["ux"] - ref["ux"], got["uy"] - ref["uy"])
+    den = np.max(np.hypot(ref["ux"], ref["uy"]))
+    return np.max(du) / (den if den > 0 else 1.0)
+
+
+def check_reduced(sim, ref, n, report, tag, phi_tol=None, up_tol=2e-2):
+    got = sim.fields()
+    errs = {"phi": rel(got["phi"], ref["phi"]), "u": rel_u(got, ref), "p": rel(got["p"], ref["p"])}
+    report(**{tag + f: e for f, e in errs.items()})
+    assert errs["phi"] < (tol32_phi(n) if phi_tol is None else phi_tol), errs
+    for f in ("u", "p"):
+        assert errs[f] < up_tol, (f, errs)
+    return errs
+
+
+@pytest.mark.parametrize("qim", [0, 1])
+def test_spinodal_512_fp64_and_fp32(L, orc, qim, report):
+    cfg = wl.spinodal(qim=qim)
+    phi0 = wl.initial_phi(cfg)
+    steps = 300
+    ref, st = oracle_fields(orc, cfg, phi0, steps)
+    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+        sim.step(steps)
+        compare(sim, 0, ref, st, 1e-10, report=report, tag="f64_")
+    with L.Simulation(cfg, "f32", phi0=[phi0]) as sim:
+        sim.step(steps)
+        check_reduced(sim, ref, steps, report, "f32_")
+
+
+def test_layered_poiseuille_fp32_vs_oracle(L, orc, report):
+    cfg = wl.layered_poiseuille(rho_ratio=10.0, mu_ratio=10.0, viscosity=1)
+    phi0 = wl.initial_phi(cfg)
+    ref, st = oracle_fields(orc, cfg, phi0, 3000)
+    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+        sim.step(3000)
+        compare(sim, 0, ref, st, 1e-10, report=report, tag="f64_")
+    with L.Simulation(cfg, "f32", phi0=[phi0]) as sim:
+        sim.step(3000)
+        check_reduced(sim, ref, 3000, report, "f32_")
+
+
+def test_bubble_1024x4096_first_steps(L, orc, report):
+    # full-size configuration, in the launch shape the benchmark times
+    cfg = wl.rising_bubble()
+    phi0 = wl.initial_phi(cfg)
+    n = 20
+    ref, st = oracle_fields(orc, cfg, phi0, n)
+    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+        sim.step(n)
+        compare(sim, 0, ref, st, 1e-10, pops=False, report=report, tag="f64_")
+    for form in ("f32", "f32_c", "f32_g16", "f32_h16"):
+        with L.Simulation(cfg, form, phi0=[phi0]) as sim:
+            sim.step(n)
+            check_reduced(sim, ref, n, report, form + "_",
+                          phi_tol=tol32_phi(n) if form in ("f32", "f32_c", "f32_g16") else 1e-3,
+                          up_tol=2e-2 if form in ("f32", "f32_c") else 0.1)
+
+
+def test_batched_instances_match_oracle(L, orc):
+    cfgs = wl.batched_mixed(24, seed=4242)
+    phis = [wl.initial_phi(c) for c in cfgs]
+    with L.Simulation(cfgs, "f64", phi0=phis) as sim:
+        sim.step(40)
+        for k in range(0, 24, 3):
+            ref, st = oracle_fields(orc, cfgs[k], phis[k], 40)
+            compare(sim, k, ref, st, 1e-11, pops=False)
+
+
+def test_phi_conserved_all_forms(L, report):
+    # FP64 and the conservative FP32 forms (h_0 absorbs storage rounding): round-off
+    # only. Plain FP32: at most 2^-24 per step of systematic drift where phi ~ 1.
+    cfg = wl.rising_bubble(nx=256, ny=512, R=32, cy=128, W=4.0, Re=20.0)
+    phi0 = wl.initial_phi(cfg)
+    n = 500
+    bounds = {"f64": 1e-13, "f32": n * 2.0 ** -24, "f32_c": 1e-9, "f32_g16": 1e-9,
+              "f32_h16": 1e-9}
+    for form, tol in bounds.items():
+        with L.Simulation(cfg, form, phi0=[phi0]) as sim:
+            sim.step(n)
+            d = sim.diagnostics()
+            assert d["status"] == L.LBM_OK
+            drift = abs(d["sum_phi"] - phi0.sum()) / phi0.sum()
+            report(**{form + "_mass_drift": drift})
+            assert drift < tol, (form, drift)
+
+
+def test_checkpoint_resume_is_bitwise(L, tmp_path):
+    cfg = wl.static_droplet(n=40, R=9)
+    phi0 = wl.initial_phi(cfg)
+    path = str(tmp_path / "ck.bin")
+    with L.Simulation(cfg, "f32", phi0=[phi0]) as a:
+        a.step(7)
+        L.lbm_save(a.ctx, path)
+        a.step(9)
+        fa = a.fields()
+    with L.Simulation(cfg, "f32") as b:
+        L.lbm_load(b.ctx, path)
+        assert L.lbm_time(b.ctx, 0) == 7
+        b.step(9)
+        fb = b.fields()
+    for f in fa:
+        assert np.array_equal(fa[f], fb[f]), f
+
+
+def test_step_before_init_is_state_error(L):
+    with L.Simulation(wl.static_droplet(n=16), "f64") as sim:
+        with pytest.raises(L.LbmError) as e:
+            sim.step(1)
+        assert e.value.status == L.LBM_ESTATE
+
+
+def test_nonfinite_is_reported(L):
+    cfg = wl.static_droplet(n=16)
+    phi0 = wl.initial_phi(cfg)
+    phi0[3, 4] = np.nan           # poisoned on the host
+    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+        d = sim.diagnostics()
+        assert d["status"] == L.LBM_ENONFINITE and d["nonfinite"] == 1
+
+
+def test_bubble_1024x4096_long_run_fp32(L, report):
+    # the benchmark's workload stays finite, conserves phi and rises
+    cfg = wl.rising_bubble()
+    phi0 = wl.initial_phi(cfg)
+    with L.Simulation(cfg, "f32", phi0=[phi0]) as sim:
+        d0 = sim.diagnostics()
+        sim.step(20000)
+        d = sim.diagnostics()
+    drift = abs(d["sum_phi"] - phi0.sum()) / phi0.sum()
+    report(mass_drift=drift, rise=d["centroid_B_y"] - d0["centroid_B_y"], max_u=d["max_u"])
+    assert d["status"] == L.LBM_OK
+    assert drift < 20000 * 2.0 ** -24
+    assert d["centroid_B_y"] > d0["centroid_B_y"] + 1.0
+
+
+def test_batched_512_all_finite(L, report):
+    # all 512 instances stay finite; the mixed-precision forms keep the mass drift
+    # at or below 1e-6 relative (plain FP32: 2^-24 per step)
+    cfgs = wl.batched_mixed(512)
+    phis = [wl.initial_phi(c) for c in cfgs]
+    n = 2000
+    for form, tol in (("f32", n * 2.0 ** -24), ("f32_g16", 1e-6), ("f32_h16", 1e-6)):
+        with L.Simulation(cfgs, form, phi0=phis) as sim:
+            sim.step(n)
+            worst = 0.0
+            for k in range(len(cfgs)):
+                d = sim.diagnostics(k)
+                assert d["status"] == L.LBM_OK, (form, k, cfgs[k]["name"])
+                worst = max(worst, abs(d["sum_phi"] - phis[k].sum()) / phis[k].sum())
+            report(**{form + "_worst_mass_drift": worst})
+            assert worst < tol, (form, worst)
