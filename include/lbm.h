@@ -83,7 +83,8 @@ enum {
 };
 
 /* Parameters of one simulation instance (Sec. 3; values per experiment in Sec. 4).
- * Validation (lbm_create, lbm_validate_params): nx >= 3, ny >= 3, nx*ny < 2^31,
+ * Validation (lbm_create, lbm_validate_params): nx >= 3, ny >= 3, nx*ny < 2^31
+ * (lbm_create: all instances together, each padded to a multiple of 64 cells, < 2^31),
  * rho_A, rho_B, nu_A, nu_B, W > 0, sigma >= 0, mobility >= 0, tau_h > 1/2,
  * every enum in range; all values finite. */
 typedef struct lbm_params {

@@ -87,6 +87,9 @@ DevInst derive(const lbm_params& p, long long base, int form) {
     d.pscheme = p.pressure_scheme;
     d.sforce = p.surface_force;
     d.visc = p.viscosity_model;
+    d.uniform_nu = (p.viscosity_model == LBM_VISC_INV_LINEAR && p.nu_A == p.nu_B) ? 1 : 0;
+    d.tgm0 = 3.0 * p.nu_A;                         // nu = c_s^2 (tau_g - 1/2)
+    d.inv_tau_g0 = 1.0 / (d.tgm0 + 0.5);
     const double phiA = 1.0, phiB = 0.0;
     d.rho_A = p.rho_A;
     d.rho_B = p.rho_B;
@@ -335,6 +338,13 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     for (int k = 0; k < n_instances; ++k)
         if (check_params(params[k])) return LBM_EINVAL;
 
+    // Instance placement: each instance starts on a 64-cell boundary; the kernels
+    // index cells with 32-bit integers, so the padded total must stay below 2^31.
+    long long total = 0;
+    for (int k = 0; k < n_instances; ++k)
+        total += ((long long)params[k].nx * params[k].ny + 63) / 64 * 64;
+    if (total >= (1LL << 31)) return LBM_EINVAL;
+
     lbm_ctx* c = new lbm_ctx();
     c->n = n_instances;
     c->form = precision;
@@ -347,7 +357,6 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
         delete c;
         return st;
     }
-    // Instance placement: each instance starts on a 64-cell boundary.
     long long base = 0;
     for (int k = 0; k < n_instances; ++k) {
         c->inst.push_back(derive(params[k], base, precision));

@@ -183,10 +183,16 @@ struct PopIO {
 
 // ---------------------------------------------------------------------------
 // Per-instance constants in the arithmetic type.
+// Reciprocal: FP32 uses the hardware approximation (max 2 ulp, __fdividef); FP64
+// keeps the IEEE division so that the FP64 form tracks the oracle to round-off.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
 template <typename R>
 struct Consts {
-    int nx, ny, walls, qim, pscheme, sforce, visc;
+    int nx, ny, walls, qim, pscheme, sforce, visc, uniform_nu;
     long long base;
+    R tgm0, inv_tau_g0;   // tau_g - 1/2 and 1/tau_g when nu_A = nu_B (inverse-linear model)
     R rho_A, rho_B, drho, inv_nu_A, inv_nu_B, mu_A, mu_B, beta, kappa, eta, gammaM;
     R inv_tau_h, src_h;   // 1/tau_h and 1 - 1/(2 tau_h)
     R force_x, force_y, gravity;
@@ -194,7 +200,8 @@ struct Consts {
 
     __device__ __forceinline__ void load(const DevInst& P) {
         nx = P.nx; ny = P.ny; walls = P.walls; qim = P.qim; pscheme = P.pscheme;
-        sforce = P.sforce; visc = P.visc; base = P.base;
+        sforce = P.sforce; visc = P.visc; base = P.base; uniform_nu = P.uniform_nu;
+        tgm0 = R(P.tgm0); inv_tau_g0 = R(P.inv_tau_g0);
         rho_A = R(P.rho_A); rho_B = R(P.rho_B); drho = R(P.drho);
         inv_nu_A = R(P.inv_nu_A); inv_nu_B = R(P.inv_nu_B); mu_A = R(P.mu_A); mu_B = R(P.mu_B);
         beta = R(P.beta); kappa = R(P.kappa); eta = R(P.eta); gammaM = R(P.gammaM);
@@ -251,15 +258,20 @@ __device__ __forceinline__ Macro<R> macroscopic(const Consts<R>& C, const R g[9]
     m.Fy = Fsy + C.force_y - (m.rho - C.rho_A) * C.gravity;   // buoyancy, Sec. 4.4
     const R jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
     const R jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    const R inv_rho = R(1) / m.rho;
+    const R inv_rho = rcp(m.rho);
     m.ux = (jx + R(0.5) * m.Fx) * inv_rho;              // Eq. 27a
     m.uy = (jy + R(0.5) * m.Fy) * inv_rho;
     m.S = m.ux * drx + m.uy * dry + m.rho * m.S1;       // S = u.grad(rho) + rho S1
-    R nu;                                               // viscosity, Sec. 3.2.2 / 4.3
-    if (C.visc == 0) nu = R(1) / (phi * (C.inv_nu_A - C.inv_nu_B) + C.inv_nu_B);
-    else nu = (phi >= R(0.5) ? C.mu_A : C.mu_B) * inv_rho;
-    m.tgm = R(3) * nu;                                  // tau_g - 1/2 = nu / c_s^2
-    m.inv_tau_g = R(1) / (m.tgm + R(0.5));
+    if (C.uniform_nu) {                                 // nu_A = nu_B: constant tau_g
+        m.tgm = C.tgm0;
+        m.inv_tau_g = C.inv_tau_g0;
+    } else {                                            // viscosity, Sec. 3.2.2 / 4.3
+        R nu;
+        if (C.visc == 0) nu = rcp(phi * (C.inv_nu_A - C.inv_nu_B) + C.inv_nu_B);
+        else nu = (phi >= R(0.5) ? C.mu_A : C.mu_B) * inv_rho;
+        m.tgm = R(3) * nu;                              // tau_g - 1/2 = nu / c_s^2
+        m.inv_tau_g = rcp(m.tgm + R(0.5));
+    }
     m.Ftx = m.Fx - gpx + drx * (R(1) / R(3));           // F~ = F - grad(p - rho c_s^2)
     m.Fty = m.Fy - gpy + dry * (R(1) / R(3));
     const R w0 = w_of<R>(0);
@@ -278,31 +290,94 @@ __device__ __forceinline__ Macro<R> macroscopic(const Consts<R>& C, const R g[9]
 }
 
 // ---------------------------------------------------------------------------
-// The fused step kernel.
+// Collision of one cell: g by Eq. 24 with g^eq of Eq. 33 (rho_0 = 0) and G_i of
+// Eq. 34; h by Eq. 10 with h^eq of Eq. 11 and R_i of Eq. 14. Opposite directions
+// i and j (c_j = -c_i) share the even parts of s_i, G_i and h^eq and differ in
+// the sign of the odd parts, so each pair is formed once:
+//   s_i   = w (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+//   G_i   = w [S + 3 c.F + 4.5 (2 (c.u)(c.F~) - (2/3) u.F~) + 1.5 (|c|^2 - 2/3) rho S1]
+//   h^eq_i = w (eta mu + 3 c.(phi u)),  R_i = (1 - 1/(2 tau_h)) 3 w c.d_t(phi u).
+template <typename R>
+__device__ __forceinline__ void collide_cell(const Consts<R>& C, const Macro<R>& m, R phi, R mu,
+                                             R ddx, R ddy, const R g[9], const R h[9],
+                                             R gpost[9], R hpost[9]) {
+    const R uu = m.ux * m.ux + m.uy * m.uy;
+    const R uFt = m.ux * m.Ftx + m.uy * m.Fty;
+    const R om = m.inv_tau_g, om1 = R(1) - om, gsrc = R(1) - R(0.5) * om;
+    const R omh = C.inv_tau_h, omh1 = R(1) - omh;
+    const R p3 = R(3) * m.p;
+    const R rS1 = m.rho * m.S1;
+    const R etamu = C.eta * mu;
+    const R phiux = phi * m.ux, phiuy = phi * m.uy;
+    // rest direction (c = 0): G_0 = w0 (S - 3 u.F~ - rho S1), R_0 = 0
+    {
+        const R w0 = w_of<R>(0);
+        const R geq = (w0 - R(1)) * p3 + m.rho * (-w0 * R(1.5) * uu);
+        const R G = w0 * (m.S - R(3) * uFt - rS1);
+        gpost[0] = om1 * g[0] + (om * geq + gsrc * G);
+        const R heq = phi + (w0 - R(1)) * etamu;
+        hpost[0] = omh1 * h[0] + omh * heq;
+    }
+#pragma unroll
+    for (int i = 1; i <= 6; ++i) {
+        if (i == 3 || i == 4) continue;          // pairs (1,3) (2,4) (5,7) (6,8)
+        const int j = opp_of(i);
+        const R w = w_of<R>(i);
+        const R ex = R(cx_of(i)), ey = R(cy_of(i));
+        const R c2 = ex * ex + ey * ey;
+        const R cu = ex * m.ux + ey * m.uy;
+        const R cF = ex * m.Fx + ey * m.Fy;
+        const R cFt = ex * m.Ftx + ey * m.Fty;
+        const R geq_e = w * (p3 + m.rho * (R(4.5) * cu * cu - R(1.5) * uu));
+        const R geq_o = w * m.rho * R(3) * cu;
+        const R G_e = w * (m.S + R(9) * cu * cFt - R(3) * uFt + R(1.5) * (c2 - R(2) / R(3)) * rS1);
+        const R G_o = w * R(3) * cF;
+        gpost[i] = om1 * g[i] + (om * (geq_e + geq_o) + gsrc * (G_e + G_o));
+        gpost[j] = om1 * g[j] + (om * (geq_e - geq_o) + gsrc * (G_e - G_o));
+        const R heq_e = w * etamu;
+        const R heq_o = R(3) * w * (ex * phiux + ey * phiuy);
+        const R R_o = C.src_h * R(3) * w * (ex * ddx + ey * ddy);
+        hpost[i] = omh1 * h[i] + (omh * (heq_e + heq_o) + R_o);
+        hpost[j] = omh1 * h[j] + (omh * (heq_e - heq_o) - R_o);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel. Rings in shared memory (slots by row number, powers of
+// two so a slot is one AND):
+//   phi   [8][TX+4]  rows Y-2 .. Y+2 (and the lead row being written)
+//   mu    [4][TX+2]  rows Y-1 .. Y+1
+//   p     [4][TX+2]  rows Y-1 .. Y+1 of the previous step's pressure
+//   h     [4][9][TX] post-streaming h of rows Y .. Y+2d, kept for the collision
 template <int FORM, int TX>
 struct StepSmem {
     using R = typename Form<FORM>::R;
     static constexpr int PW = TX + 4;   // phi ring row: strip + 2-column halo each side
     static constexpr int MW = TX + 2;   // mu / p ring row: strip + 1-column halo
-    static constexpr size_t elems = 5 * PW + 3 * MW + 4 * MW + 4 * 9 * TX;
+    static constexpr size_t elems = 8 * PW + 4 * MW + 4 * MW + 4 * 9 * TX;
     static constexpr size_t bytes = elems * sizeof(R);
 };
 
-__device__ __forceinline__ int ring5(int y) { return (y + 40) % 5; }
-__device__ __forceinline__ int ring4(int y) { return (y + 40) & 3; }
-__device__ __forceinline__ int ring3(int y) { return (y + 42) % 3; }
+// Resident blocks per SM the register budget is sized for: FP32 forms 1024/TX
+// blocks (64 registers a thread), FP64 384/TX (170 registers; FP64 is bound by
+// its arithmetic on GB300, and its shared-memory rings allow few blocks anyway).
+template <int FORM, int TX>
+struct StepOcc {
+    static constexpr int value = (sizeof(typename Form<FORM>::R) == 8 ? 384 : 1024) / TX > 0
+                                     ? (sizeof(typename Form<FORM>::R) == 8 ? 384 : 1024) / TX : 1;
+};
 
 template <int FORM, int TX>
-__global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(const StepArgs a) {
     using F = Form<FORM>;
     using R = typename F::R;
     using AT = typename F::AT;
     using SM = StepSmem<FORM, TX>;
     constexpr int PW = SM::PW, MW = SM::MW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* phiR = reinterpret_cast<R*>(smem_raw);   // [5][PW]
-    R* muR = phiR + 5 * PW;                      // [3][MW]
-    R* pR = muR + 3 * MW;                        // [4][MW]
+    R* phiR = reinterpret_cast<R*>(smem_raw);   // [8][PW]
+    R* muR = phiR + 8 * PW;                      // [4][MW]
+    R* pR = muR + 4 * MW;                        // [4][MW]
     R* hR = pR + 4 * MW;                         // [4][9][TX]
 
     const WorkItem wk = a.work[blockIdx.x];
@@ -312,7 +387,8 @@ __global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
     const int x0 = wk.x0, d = wk.dir;
     const int w = min(TX, nx - x0);
     const int tid = threadIdx.x;
-    const long long S = a.S, base = C.base;
+    const int base = (int)C.base;       // cell indices fit in 32 bits (checked on the host)
+    const long long S = a.S;
 
     PopIO<F> io;
     io.hin = static_cast<const typename F::HT*>(a.h_in);
@@ -330,49 +406,62 @@ __global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
     auto rowg = [ny, walls](int y) { return walls ? y : (y < 0 ? y + ny : (y >= ny ? y - ny : y)); };
     auto ghost = [ny, walls](int y) { return walls && (y < 0 || y >= ny); };
     auto mirror = [ny](int y) { return y < 0 ? -1 - y : 2 * ny - 1 - y; };
+    auto rowoff = [&](int y) { return base + rowg(y) * nx; };
+
+    // Per-thread columns, fixed for the whole march.
+    const bool lead0 = tid < w + 4, lead1 = tid + TX < w + 4;      // phi / h columns x0-2+s
+    const int lc0 = lead0 ? wrapx(x0 - 2 + tid) : 0;
+    const int lc1 = lead1 ? wrapx(x0 - 2 + tid + TX) : 0;
+    const bool mid0 = tid < w + 2, mid1 = tid + TX < w + 2;       // mu / p columns x0-1+s
+    const int pc0 = mid0 ? wrapx(x0 - 1 + tid) : 0;
+    const int pc1 = mid1 ? wrapx(x0 - 1 + tid + TX) : 0;
+    const bool act = tid < w;                                     // collision column X
+    const int X = x0 + tid;
+    const int colm = act ? wrapx(X - 1) : 0, colp = act ? wrapx(X + 1) : 0;
 
     // A. phi of row L over columns x0-2 .. x0+w+1; h of the strip kept for the collision.
     auto lead_row = [&](int L) {
-        R* prow = phiR + ring5(L) * PW;
+        R* prow = phiR + ((L + 64) & 7) * PW;
         if (ghost(L)) {   // mirror ghost row next to a wall (reading Q7)
-            const R* src = phiR + ring5(mirror(L)) * PW;
-            for (int s = tid; s < w + 4; s += TX) prow[s] = src[s];
+            const R* src = phiR + ((mirror(L) + 64) & 7) * PW;
+            if (lead0) prow[tid] = src[tid];
+            if (lead1) prow[tid + TX] = src[tid + TX];
             return;
         }
-        const long long row = base + (long long)rowg(L) * nx;
-        R* hrow = hR + ring4(L) * 9 * TX;
-        for (int s = tid; s < w + 4; s += TX) {
-            const long long c = row + wrapx(x0 - 2 + s);
-            R hv[9], phi_lo;
-            const R phi = io.phi_of(c, hv, phi_lo);          // Eq. 18
-            prow[s] = phi;
+        const int ro = rowoff(L);
+        R* hrow = hR + ((L + 64) & 3) * 9 * TX;
+        auto column = [&](int s, int col) {
+            R hv[9], lo;
+            prow[s] = io.phi_of(ro + col, hv, lo);          // Eq. 18
             if (s >= 2 && s < w + 2) {
-                // conservative forms keep the low part of phi where h_0 would go
-                if constexpr (F::cons) hv[0] = phi_lo;
+                if constexpr (F::cons) hv[0] = lo;           // low part of phi in h_0's slot
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hrow[i * TX + (s - 2)] = hv[i];
             }
-        }
+        };
+        if (lead0) column(tid, lc0);
+        if (lead1) column(tid + TX, lc1);
     };
     // p of the previous step, row M, columns x0-1 .. x0+w (mirror ghost at walls).
     auto p_row = [&](int M) {
-        const int gy = ghost(M) ? mirror(M) : rowg(M);
-        const AT* src = p_in + base + (long long)gy * nx;
-        R* dst = pR + ring4(M) * MW;
-        for (int s = tid; s < w + 2; s += TX) dst[s] = R(src[wrapx(x0 - 1 + s)]);
+        const AT* src = p_in + base + (ghost(M) ? mirror(M) : rowg(M)) * nx;
+        R* dst = pR + ((M + 64) & 3) * MW;
+        if (mid0) dst[tid] = R(src[pc0]);
+        if (mid1) dst[tid + TX] = R(src[pc1]);
     };
     // B. mu of row M (Eq. 8 with the Laplacian of Eq. 30b), columns x0-1 .. x0+w.
     auto mu_row = [&](int M) {
-        R* mrow = muR + ring3(M) * MW;
+        R* mrow = muR + ((M + 64) & 3) * MW;
         if (ghost(M)) {
-            const R* src = muR + ring3(mirror(M)) * MW;
-            for (int s = tid; s < w + 2; s += TX) mrow[s] = src[s];
+            const R* src = muR + ((mirror(M) + 64) & 3) * MW;
+            if (mid0) mrow[tid] = src[tid];
+            if (mid1) mrow[tid + TX] = src[tid + TX];
             return;
         }
-        const R* r0 = phiR + ring5(M - 1) * PW;
-        const R* r1 = phiR + ring5(M) * PW;
-        const R* r2 = phiR + ring5(M + 1) * PW;
-        for (int s = tid; s < w + 2; s += TX) {
+        const R* r0 = phiR + ((M - 1 + 64) & 7) * PW;
+        const R* r1 = phiR + ((M + 64) & 7) * PW;
+        const R* r2 = phiR + ((M + 1 + 64) & 7) * PW;
+        auto column = [&](int s) {
             Nbr<R> n;
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
@@ -381,19 +470,21 @@ __global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
                 n.z[2][dx] = r2[s + dx];
             }
             mrow[s] = chem_pot(C, n.z[1][1], n.lap());
-        }
+        };
+        if (mid0) column(tid);
+        if (mid1) column(tid + TX);
     };
-    // C. collision and push-streaming of row Y.
-    auto collide_row = [&](int Y) {
-        if (tid >= w) return;
-        const int X = x0 + tid;
-        const long long c = base + (long long)rowg(Y) * nx + X;
+    // C. collision and push-streaming of row Y (g, phi u of the previous step loaded early).
+    auto collide_row = [&](int Y, const R (&g)[9], R pux, R puy) {
+        if (!act) return;
+        const int rY = rowoff(Y);
+        const int c = rY + X;
         Nbr<R> nphi, nmu, np;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const R* pr = phiR + ring5(Y + dy - 1) * PW + tid + 1;
-            const R* mr = muR + ring3(Y + dy - 1) * MW + tid;
-            const R* qr = pR + ring4(Y + dy - 1) * MW + tid;
+            const R* pr = phiR + ((Y + dy - 1 + 64) & 7) * PW + tid + 1;
+            const R* mr = muR + ((Y + dy - 1 + 64) & 3) * MW + tid;
+            const R* qr = pR + ((Y + dy - 1 + 64) & 3) * MW + tid;
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
                 nphi.z[dy][dx] = pr[dx];
@@ -407,44 +498,16 @@ __global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
         nmu.grad(gmux, gmuy);
         np.grad(gpx, gpy);
         const R lapmu = nmu.lap();
-        R g[9], h[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = io.load_g(i, c);
-        const R* hrow = hR + ring4(Y) * 9 * TX + tid;
+        R h[9];
+        const R* hrow = hR + ((Y + 64) & 3) * 9 * TX + tid;
 #pragma unroll
         for (int i = 0; i < 9; ++i) h[i] = hrow[i * TX];
-        const R pux = R(phiu[c]), puy = R(phiu[S + c]);
 
         const Macro<R> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
-
-        // Collision of g (Eq. 24) with g^eq (Eq. 33, rho_0 = 0) and G_i (Eq. 34).
-        const R uu = m.ux * m.ux + m.uy * m.uy;
-        const R uFt = m.ux * m.Ftx + m.uy * m.Fty;
-        const R gsrc = R(1) - R(0.5) * m.inv_tau_g;
         const R phiux = phi * m.ux, phiuy = phi * m.uy;
-        const R ddx = phiux - pux, ddy = phiuy - puy;     // d_t(phi u), first-order backward
-        const R etamu = C.eta * mu;
-        R hpost[9], gpost[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const R wi = w_of<R>(i);
-            const R ex = R(cx_of(i)), ey = R(cy_of(i));
-            const R cu = ex * m.ux + ey * m.uy;
-            const R si = wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-            const R geq = (i == 0) ? (wi - R(1)) * R(3) * m.p + m.rho * si
-                                   : R(3) * wi * m.p + m.rho * si;
-            const R cF = ex * m.Fx + ey * m.Fy;
-            const R cFt = ex * m.Ftx + ey * m.Fty;
-            const R c2 = ex * ex + ey * ey;
-            const R Gi = wi * (m.S + R(3) * cF + R(4.5) * (R(2) * cu * cFt - (R(2) / R(3)) * uFt) +
-                               R(1.5) * (c2 - R(2) / R(3)) * m.rho * m.S1);
-            gpost[i] = g[i] - (g[i] - geq) * m.inv_tau_g + gsrc * Gi;
-            // Collision of h (Eq. 10) with h^eq (Eq. 11) and R_i (Eq. 14).
-            const R heq = (i == 0) ? phi + (wi - R(1)) * etamu
-                                   : wi * etamu + R(3) * wi * (ex * phiux + ey * phiuy);
-            const R Ri = C.src_h * R(3) * wi * (ex * ddx + ey * ddy);
-            hpost[i] = h[i] - (h[i] - heq) * C.inv_tau_h + Ri;
-        }
+        R gpost[9], hpost[9];
+        collide_cell(C, m, phi, mu, phiux - pux, phiuy - puy, g, h, gpost, hpost);
+
         float2 h0c = make_float2(0.f, 0.f);
         if constexpr (F::cons) {
             // h_0 absorbs the storage rounding of h_1..h_8: the stored populations
@@ -459,18 +522,19 @@ __global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
             h0c = io.conservative_h0(phi, h[0] /* low part of phi */, rest);
         }
         // Push-streaming: population i moves to x + c_i; into a wall it comes back
-        // reversed at x (halfway bounce-back, Sec. 4.3).
-        const int gyY = rowg(Y);
+        // reversed at x (halfway bounce-back, Sec. 4.3). Wall rows are uniform per row.
+        const bool bot = walls && Y == 0, top = walls && Y == ny - 1;
+        const int rDn = bot ? 0 : rowoff(Y - 1);
+        const int rUp = top ? 0 : rowoff(Y + 1);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const int yt = Y + cy_of(i);
-            long long dst;
+            const int cyi = cy_of(i), cxi = cx_of(i);
+            const int col = cxi < 0 ? colm : (cxi > 0 ? colp : X);
+            int dst = (cyi == 0 ? rY : (cyi > 0 ? rUp : rDn)) + col;
             int k = i;
-            if (walls && (yt < 0 || yt >= ny)) {
+            if ((cyi > 0 && top) || (cyi < 0 && bot)) {
                 dst = c;
                 k = opp_of(i);
-            } else {
-                dst = base + (long long)(cy_of(i) == 0 ? gyY : rowg(yt)) * nx + wrapx(X + cx_of(i));
             }
             if constexpr (F::cons) {
                 if (i == 0) io.store_h0(dst, h0c);
@@ -500,12 +564,23 @@ __global__ void __launch_bounds__(TX) step_kernel(const StepArgs a) {
     __syncthreads();
     for (int k = 0; k < wk.nrows; ++k) {
         const int Y = Y0 + k * d;
+        // g and phi*u of the collision row, loaded before the barriers so the
+        // loads overlap phases A and B
+        R g[9];
+        R pux = R(0), puy = R(0);
+        if (act) {
+            const int c = rowoff(Y) + X;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = io.load_g(i, c);
+            pux = R(phiu[c]);
+            puy = R(phiu[S + c]);
+        }
         lead_row(Y + 2 * d);
         p_row(Y + d);
         __syncthreads();
         mu_row(Y + d);
         __syncthreads();
-        collide_row(Y);
+        collide_row(Y, g, pux, puy);
     }
 }
 

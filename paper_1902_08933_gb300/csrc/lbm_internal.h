@@ -17,7 +17,7 @@ struct DevInst {
     int pscheme;             // LBM_P_*
     int sforce;              // LBM_FS_*
     int visc;                // LBM_VISC_*
-    int pad;
+    int uniform_nu;          // 1: inverse-linear model with nu_A = nu_B (tau_g constant)
     double rho_A, rho_B, drho;       // drho = (rho_A - rho_B) / (phi_A - phi_B)
     double inv_nu_A, inv_nu_B;       // inverse-linear viscosity
     double mu_A, mu_B;               // dynamic viscosities rho nu (step model)
@@ -26,6 +26,7 @@ struct DevInst {
     double inv_tau_h;
     double force_x, force_y, gravity;
     double h_scale, g_scale;         // storage scales of reduced-precision forms (powers of 2)
+    double tgm0, inv_tau_g0;         // tau_g - 1/2 and 1/tau_g for uniform_nu
 };
 
 // One thread block's work: a strip of columns [x0, x0 + TX) (clipped to nx) of
