@@ -197,6 +197,31 @@ int lbm_launches_per_step(const lbm_ctx* ctx);
 /* Steps taken by an instance since its lbm_init. */
 int64_t lbm_time(const lbm_ctx* ctx, int instance);
 
+/* The FP64 diagnostics reduction for callers that cannot allocate device
+ * memory. The paper has no counterpart: this is a library service, not a step
+ * of the method. It is meant for code that runs where cudaMalloc is off limits,
+ * such as a host framework that owns all device memory through its own pool,
+ * or a loop that cannot afford the device synchronisation of cudaMalloc/cudaFree.
+ * fields_device: caller-owned device array of 5 * nx * ny doubles, field-major
+ *   phi, ux, uy, rho, P (exactly what lbm_get_fields_device writes for the mask
+ *   LBM_FIELD_PHI | LBM_FIELD_UX | LBM_FIELD_UY | LBM_FIELD_RHO | LBM_FIELD_PLAP).
+ * out_device: caller-owned device array of 14 doubles, receiving in this order
+ *   sum phi, sum rho, kinetic energy, max |u|, sum phi x, sum phi y,
+ *   sum (1-phi) x, sum (1-phi) y, sum P over phi > 1-1e-3, their cell count,
+ *   sum P over phi < 1e-3, their cell count, non-finite cells, sum (1-phi)
+ *   (the quantities behind lbm_diag).
+ * cuda_stream: the stream to queue the two kernels on (NULL: default stream).
+ * Allocates nothing: the per-block partial sums use a fixed array compiled
+ * into the library (229 KB, held by every GPU that loads it until exit), so
+ * nx * ny may be at most 16,777,216 cells; larger grids return LBM_EINVAL, as
+ * do NULL pointers or nx, ny < 1. The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture. All calls share the array, so
+ * calls that overlap on the GPU (several streams or devices' threads at once)
+ * race. Asynchronous; LBM_ECUDA if the set-up or a launch fails. */
+lbm_status lbm_reduce_fields_noalloc(const double* fields_device, int nx, int ny,
+                                     void* cuda_stream, double* out_device);
+
 /* Waits for all queued work. Returns LBM_ECUDA if it failed. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 

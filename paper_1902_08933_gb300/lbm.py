@@ -84,6 +84,7 @@ SIGNATURES = [
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_launches_per_step", ctypes.c_int, [_VP]),
     ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
+    ("lbm_reduce_fields_noalloc", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     ("lbm_sync", ctypes.c_int, [_VP]),
     ("lbm_last_error", ctypes.c_char_p, [_VP]),
     ("lbm_destroy", None, [_VP]),
@@ -206,6 +207,12 @@ def lbm_launches_per_step(ctx) -> int:
 
 def lbm_time(ctx, instance) -> int:
     return library().lbm_time(ctx, instance)
+
+
+def lbm_reduce_fields_noalloc(fields_dev_ptr: int, nx: int, ny: int, stream, out_dev_ptr: int) -> int:
+    """Returns the status code (allocation-free FP64 reduction of caller fields)."""
+    return library().lbm_reduce_fields_noalloc(_VP(fields_dev_ptr), int(nx), int(ny),
+                                               _VP(stream or 0), _VP(out_dev_ptr))
 
 
 def lbm_sync(ctx):
