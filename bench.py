@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32", choices=list(BYTES_PER_LUP))
+    ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs"],
+                    help="load path of the step kernel (lbm_set_pipeline)")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the side-by-side forms, e2e and CPU legs")
     return ap.parse_args()
@@ -255,7 +257,11 @@ def main():
 
     # ---- headline: K steps of the fused kernel, CUDA events on its stream
     sim = lbm.Simulation(cfg, args.form, stream=stream.cuda_stream, phi0=[phi0])
+    lbm.lbm_set_pipeline(sim.ctx, {"auto": lbm.LBM_PIPELINE_AUTO, "plain": lbm.LBM_PIPELINE_PLAIN,
+                                   "async": lbm.LBM_PIPELINE_ASYNC, "tma": lbm.LBM_PIPELINE_TMA,
+                                   "pairs": lbm.LBM_PIPELINE_PAIRS}[args.pipeline])
     launches = lbm.lbm_launches_per_step(sim.ctx)
+    variant = lbm.lbm_launch_info(sim.ctx, 0)["variant"]
     for _ in range(args.warmup):
         sim.step(1)
     sim.sync()
@@ -290,7 +296,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.form == "f64" else "f32", "data": "synthetic",
         "config": {"workload": "rising_bubble_1024x4096_rho10_qim", "nx": cfg["nx"], "ny": cfg["ny"],
-                   "form": args.form, "storage": {"f64": "f64", "f32": "f32",
+                   "form": args.form, "load_path": variant, "storage": {"f64": "f64", "f32": "f32",
                                                   "f32_g16": "h0 2xf32, h1-8 f32, g f16",
                                                   "f32_h16": "h0 2xf32, h1-8 f16, g f16",
                                                   "f32_c": "h0 2xf32, h1-8 f32, g f32"}[args.form],
@@ -343,6 +349,18 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
                                None if form == "f64" else
                                {k: rel_err(f[k], ref[k]) for k in ("phi", "ux", "uy", "p")})}
     out["forms"] = forms
+
+    # the three load paths of the FP32 step kernel on the headline workload
+    pipes = {}
+    for name, mode in (("plain", lbm.LBM_PIPELINE_PLAIN), ("async", lbm.LBM_PIPELINE_ASYNC),
+                       ("tma", lbm.LBM_PIPELINE_TMA), ("pairs", lbm.LBM_PIPELINE_PAIRS)):
+        with lbm.Simulation(cfg, "f32", stream=stream.cuda_stream, phi0=[phi0]) as sim:
+            lbm.lbm_set_pipeline(sim.ctx, mode)
+            ms = time_steps(lbm, sim, stream, K, 5)
+            gbs = BYTES_PER_LUP["f32"] * cells / (ms * 1e-3 / K) / 1e9
+            pipes[name] = {"MLUPS": cells * K / (ms * 1e-3) / 1e6, "frac_hbm": gbs / hbm_peak,
+                           "blocks": lbm.lbm_launch_info(sim.ctx, 0)["blocks"]}
+    out["f32_load_paths"] = pipes
 
     # batched: 512 independent droplets / bubbles of mixed size, one launch per size class
     cfgs = wl.batched_mixed(512)

@@ -186,12 +186,43 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
  * built-in choice. Takes effect at the next lbm_step. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
 
+/* How the step kernel brings a row's populations into shared memory. All
+ * variants compute the same arithmetic; they differ in the load path.
+ *  LBM_PIPELINE_PLAIN  every thread loads its own cells when it needs them.
+ *  LBM_PIPELINE_ASYNC  every thread copies its own cells of the next row with
+ *                      cp.async one row ahead (forms with FP32 h: LBM_F32,
+ *                      LBM_F32_C, LBM_F32_G16).
+ *  LBM_PIPELINE_TMA    one warp issues bulk copies (cp.async.bulk, the Tensor
+ *                      Memory Accelerator) of whole row segments one row ahead
+ *                      (FP32-arithmetic forms, classes whose instances all have
+ *                      nx % 8 == 0).
+ *  LBM_PIPELINE_PAIRS  every thread owns two adjacent cells and computes them in
+ *                      the packed FP32 instructions (FFMA2/FADD2/FMUL2) of
+ *                      sm_100+, with 8-byte pair loads and stores
+ *                      (FP32-arithmetic forms, instances with nx even, strips
+ *                      of at least 64 columns).
+ *  LBM_PIPELINE_AUTO   (default) PAIRS where available, else ASYNC, else TMA,
+ *                      else PLAIN.
+ * An instance that cannot use a variant falls back to PLAIN. Takes effect at
+ * the next lbm_step. LBM_EINVAL for an unknown mode. */
+enum {
+    LBM_PIPELINE_AUTO = 0, LBM_PIPELINE_PLAIN = 1, LBM_PIPELINE_ASYNC = 2, LBM_PIPELINE_TMA = 3,
+    LBM_PIPELINE_PAIRS = 4
+};
+lbm_status lbm_set_pipeline(lbm_ctx* ctx, int mode);
+
+/* Launch index (0 .. lbm_launches_per_step - 1) of one step: strip width,
+ * number of thread blocks, and the load path it uses (0 plain, 1 cp.async,
+ * 2 TMA, 3 pairs). Any output pointer may be NULL. LBM_EINVAL for an index out
+ * of range. */
+lbm_status lbm_launch_info(lbm_ctx* ctx, int index, int* tile_x, int* blocks, int* variant);
+
 /* Times the candidate launch shapes on the current state (the state is saved
  * and restored around the trials) and keeps the fastest. best_tile_x / best_rows
  * may be NULL. Synchronises. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int* best_tile_x, int* best_rows);
 
-/* Kernel launches queued by one lbm_step(1) (for accounting). */
+/* Kernel launches queued by one lbm_step(1) (for accounting); 0 on error. */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 
 /* Steps taken by an instance since its lbm_init. */
@@ -222,7 +253,10 @@ int64_t lbm_time(const lbm_ctx* ctx, int instance);
 lbm_status lbm_reduce_fields_noalloc(const double* fields_device, int nx, int ny,
                                      void* cuda_stream, double* out_device);
 
-/* Waits for all queued work. Returns LBM_ECUDA if it failed. */
+/* Waits for all queued work. Returns LBM_ECUDA if it failed, LBM_ETIMEOUT if a
+ * bounded device wait of the step kernel ran out (the state is then suspect;
+ * the status stays set for the life of the context). lbm_get_fields and
+ * lbm_diagnostics report the same status. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 /* Last error message of the context ("" if none); valid until the next call. */

@@ -136,7 +136,9 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int tile_req = 0, rows_req = 0;
-    struct Launch { int tx, offset, count; };
+    int pipeline = LBM_PIPELINE_AUTO;
+    int* d_status = nullptr;       // device status word written by bounded waits
+    struct Launch { int tx, offset, count, variant; };
     std::vector<Launch> launches;
     std::vector<WorkItem> work;
     WorkItem* d_work = nullptr;
@@ -181,6 +183,7 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.S = c->S;
     a.inst = c->d_inst;
     a.work = nullptr;
+    a.status = c->d_status;
     return a;
 }
 
@@ -208,23 +211,61 @@ int default_tile(int nx) {
     return 32;
 }
 
+int default_tile_pairs(int nx) {   // strip width of the paired kernel (2 columns a thread)
+    if (nx >= 256) return 256;
+    if (nx >= 128) return 128;
+    return 64;
+}
+
+// Load path and strip width of one instance under the context's pipeline mode.
+// The paired kernel needs nx even and strips of at least 64 columns; the TMA-fed
+// kernel 16-byte row segments (nx % 8 == 0, see lbm_step_tma.cuh); both exist for
+// the FP32-arithmetic forms, the cp.async kernel for FP32 storage of h and p.
+void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, bool f_tma,
+            int* tile, int* variant) {
+    const bool pairs_ok = f_pairs && p.nx % 2 == 0 && (c->tile_req == 0 || c->tile_req >= 64);
+    const bool tma_ok = f_tma && p.nx % 8 == 0 && p.nx >= 8;
+    int v = lbm::kPlain;
+    switch (c->pipeline) {
+        case LBM_PIPELINE_AUTO:
+            v = pairs_ok ? lbm::kPairs : (f_async ? lbm::kAsync : (tma_ok ? lbm::kTma : lbm::kPlain));
+            break;
+        case LBM_PIPELINE_PAIRS: v = pairs_ok ? lbm::kPairs : lbm::kPlain; break;
+        case LBM_PIPELINE_ASYNC: v = f_async ? lbm::kAsync : lbm::kPlain; break;
+        case LBM_PIPELINE_TMA: v = tma_ok ? lbm::kTma : lbm::kPlain; break;
+        default: v = lbm::kPlain; break;
+    }
+    *variant = v;
+    if (c->tile_req) *tile = c->tile_req;
+    else *tile = v == lbm::kPairs ? default_tile_pairs(p.nx) : default_tile(p.nx);
+}
+
 // Work list: per instance, strips of tile_x columns, each split into runs of
-// rows. Neighbouring runs march in opposite directions (down, up, down, ...) so
-// that two blocks that share a run boundary read its halo rows at the same time
-// (both at their start or both at their end), from L2 rather than HBM.
+// rows, grouped into one launch per (strip width, load path). Neighbouring runs
+// march in opposite directions (down, up, down, ...) so that two blocks that
+// share a run boundary read its halo rows at the same time (both at their start
+// or both at their end), from L2 rather than HBM.
 lbm_status plan(lbm_ctx* c) {
-    std::vector<std::vector<WorkItem>> by_class(5);
-    const int classes[5] = {32, 64, 128, 256, 0};
-    auto cls_index = [&](int tx) {
+    const int tiles[4] = {32, 64, 128, 256};
+    auto tile_index = [&](int tx) {
         for (int k = 0; k < 4; ++k)
-            if (classes[k] == tx) return k;
-        return 4;
+            if (tiles[k] == tx) return k;
+        return 0;
     };
+    std::vector<std::vector<WorkItem>> by_class(16);   // tile index * 4 + variant
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    bool f_pairs = false, f_async = false, f_tma = false;
+    by_form(c->form, [&](auto F) {
+        f_pairs = lbm::has_pairs_t<decltype(F)::value>();
+        f_async = lbm::has_async_t<decltype(F)::value>();
+        f_tma = lbm::has_tma_t<decltype(F)::value>();
+        return cudaSuccess;
+    });
     for (int k = 0; k < c->n; ++k) {
         const lbm_params& p = c->params[k];
-        const int tx = c->tile_req ? c->tile_req : default_tile(p.nx);
+        int tx = 0, variant = 0;
+        choose(c, p, f_pairs, f_async, f_tma, &tx, &variant);
         const int strips = (p.nx + tx - 1) / tx;
         int rows = c->rows_req;
         if (rows <= 0) {
@@ -232,7 +273,7 @@ lbm_status plan(lbm_ctx* c) {
                 // one domain: fill the GPU with resident blocks in a single wave
                 int occ = 0;
                 by_form(c->form, [&](auto F) {
-                    occ = lbm::step_occupancy_t<decltype(F)::value>(tx);
+                    occ = lbm::step_occupancy_t<decltype(F)::value>(tx, variant);
                     return cudaSuccess;
                 });
                 const long long target = (long long)sms * std::max(occ, 1);
@@ -244,7 +285,7 @@ lbm_status plan(lbm_ctx* c) {
         }
         rows = std::min(rows, p.ny);
         const int nchunks = (p.ny + rows - 1) / rows;
-        auto& list = by_class[cls_index(tx)];
+        auto& list = by_class[tile_index(tx) * 4 + variant];
         for (int s = 0; s < strips; ++s)
             for (int ch = 0; ch < nchunks; ++ch) {
                 const int y0 = ch * rows, y1 = std::min(p.ny, y0 + rows);
@@ -260,9 +301,9 @@ lbm_status plan(lbm_ctx* c) {
     }
     c->work.clear();
     c->launches.clear();
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 16; ++k) {
         if (by_class[k].empty()) continue;
-        c->launches.push_back({classes[k], (int)c->work.size(), (int)by_class[k].size()});
+        c->launches.push_back({tiles[k / 4], (int)c->work.size(), (int)by_class[k].size(), k % 4});
         c->work.insert(c->work.end(), by_class[k].begin(), by_class[k].end());
     }
     if (c->d_work) cudaFree(c->d_work);
@@ -283,6 +324,19 @@ lbm_status check_instance(lbm_ctx* c, int instance) {
 lbm_status sticky(lbm_ctx* c) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "earlier asynchronous work");
+    return LBM_OK;
+}
+
+// Reads the device status word (synchronises the stream). A bounded device wait
+// that ran out leaves LBM_ETIMEOUT there; it stays set (the state is suspect).
+lbm_status device_status(lbm_ctx* c) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read-back");
+    if (st == lbm::kStatusTimeout) return fail(c, LBM_ETIMEOUT, "a bounded device wait ran out in the step kernel");
+    if (st != 0) return fail(c, LBM_ECUDA, "device status word " + std::to_string(st) +
+                                                 " (100: a bulk copy was not 16-byte aligned and was skipped)");
     return LBM_OK;
 }
 
@@ -310,6 +364,7 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_out);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
+    cudaFree(c->d_status);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -385,8 +440,10 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
         (e = alloc((void**)&c->d_tmp, 2 * (size_t)c->max_cells * sizeof(double))) != cudaSuccess ||
         (e = alloc((void**)&c->d_partials, lbm::kDiagBlocks * lbm::kDiagQuantities * sizeof(double))) !=
             cudaSuccess ||
-        (e = alloc((void**)&c->d_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess)
+        (e = alloc((void**)&c->d_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess ||
+        (e = alloc((void**)&c->d_status, sizeof(int))) != cudaSuccess)
         return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+    if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(LBM_ECUDA);
     if ((e = cudaMallocHost((void**)&c->h_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess)
         return cleanup(LBM_ENOMEM);
     if (cuda_stream) {
@@ -456,7 +513,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         for (const auto& L : c->launches) {
             a.work = c->d_work + L.offset;
             cudaError_t e = by_form(c->form, [&](auto F) {
-                return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream);
+                return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream, L.variant);
             });
             if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
         }
@@ -492,7 +549,7 @@ lbm_status lbm_get_fields(lbm_ctx* c, int instance, unsigned mask, double* host_
     LBM_CK(c, cudaMemcpyAsync(host_out, c->d_out, cells * sizeof(double), cudaMemcpyDeviceToHost,
                               c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return device_status(c);
 }
 
 lbm_status lbm_get_fields_device(lbm_ctx* c, int instance, unsigned mask, double* dev_out) {
@@ -521,6 +578,7 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int instance, lbm_diag* out) {
     LBM_CK(c, cudaMemcpyAsync(c->h_result, c->d_result, lbm::kDiagQuantities * sizeof(double),
                               cudaMemcpyDeviceToHost, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
+    if ((st = device_status(c)) != LBM_OK) return st;
     const double* r = c->h_result;
     std::memset(out, 0, sizeof(*out));
     out->sum_phi = r[0];
@@ -752,15 +810,11 @@ lbm_status lbm_autotune(lbm_ctx* c, int* best_tile_x, int* best_rows) {
 
 int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
-    if (!c->plan_dirty) return (int)c->launches.size();
-    int classes = 0;
-    bool seen[5] = {false, false, false, false, false};
-    for (const auto& p : c->params) {
-        const int tx = c->tile_req ? c->tile_req : default_tile(p.nx);
-        const int k = tx == 32 ? 0 : tx == 64 ? 1 : tx == 128 ? 2 : 3;
-        if (!seen[k]) { seen[k] = true; ++classes; }
+    if (c->plan_dirty) {
+        lbm_ctx* m = const_cast<lbm_ctx*>(c);
+        if (cudaSetDevice(m->device) != cudaSuccess || plan(m) != LBM_OK) return 0;
     }
-    return classes;
+    return (int)c->launches.size();
 }
 
 int64_t lbm_time(const lbm_ctx* c, int instance) {
@@ -772,7 +826,32 @@ lbm_status lbm_sync(lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
     LBM_CK(c, cudaSetDevice(c->device));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
-    return sticky(c);
+    lbm_status st = sticky(c);
+    return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_set_pipeline(lbm_ctx* c, int mode) {
+    if (!c) return LBM_EINVAL;
+    if (mode < LBM_PIPELINE_AUTO || mode > LBM_PIPELINE_PAIRS)
+        return fail(c, LBM_EINVAL, "pipeline mode must be one of LBM_PIPELINE_*");
+    c->pipeline = mode;
+    c->plan_dirty = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_launch_info(lbm_ctx* c, int index, int* tile_x, int* blocks, int* variant) {
+    if (!c) return LBM_EINVAL;
+    if (c->plan_dirty) {
+        LBM_CK(c, cudaSetDevice(c->device));
+        lbm_status st = plan(c);
+        if (st != LBM_OK) return st;
+    }
+    if (index < 0 || index >= (int)c->launches.size()) return fail(c, LBM_EINVAL, "launch index out of range");
+    const auto& L = c->launches[index];
+    if (tile_x) *tile_x = L.tx;
+    if (blocks) *blocks = L.count;
+    if (variant) *variant = L.variant;
+    return LBM_OK;
 }
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }

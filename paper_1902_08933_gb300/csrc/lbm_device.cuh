@@ -211,81 +211,134 @@ struct Consts {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Value types of the cell arithmetic: double, float, or F2 -- two cells' FP32
+// values in the two lanes of a float2, computed with the packed FP32 instructions
+// of sm_100+ (FFMA2 / FADD2 / FMUL2), so one instruction serves two cells. The
+// cell functions below are written once for all three; constants come in the
+// scalar type S of the instance constants.
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(float2 w) : v(w) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+// a - b as a + (-1) b: the product is exact, so this rounds once, like a subtraction
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v));
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(float s, F2 b) { return F2(s) * b; }
+__device__ __forceinline__ F2 operator*(F2 a, float s) { return a * F2(s); }
+__device__ __forceinline__ F2 operator+(F2 a, float s) { return a + F2(s); }
+__device__ __forceinline__ F2 operator+(float s, F2 b) { return F2(s) + b; }
+__device__ __forceinline__ F2 operator-(F2 a, float s) { return a - F2(s); }
+__device__ __forceinline__ F2 operator-(float s, F2 b) { return F2(s) - b; }
+
+template <typename V> struct ScalarOf { using type = V; };
+template <> struct ScalarOf<F2> { using type = float; };
+
+// a * b + c (one FFMA2 for F2; the compiler contracts the scalar form)
+template <typename V>
+__device__ __forceinline__ V fmadd(V a, V b, V c) { return a * b + c; }
+__device__ __forceinline__ F2 fmadd(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 rcp(F2 x) { return F2(rcp(x.v.x), rcp(x.v.y)); }
+// step dynamic viscosity of Sec. 4.3: a where phi >= 1/2, else b
+template <typename V, typename S>
+__device__ __forceinline__ V step_pick(V phi, S a, S b) { return phi >= V(0.5) ? V(a) : V(b); }
+__device__ __forceinline__ F2 step_pick(F2 phi, float a, float b) {
+    return F2(phi.v.x >= 0.5f ? a : b, phi.v.y >= 0.5f ? a : b);
+}
+// c . (x, y) for a lattice direction c = (cx, cy) with components in {-1, 0, 1};
+// cx, cy are compile-time after unrolling, so this folds to one add or a copy.
+template <typename V>
+__device__ __forceinline__ V cdot(int cx, int cy, V x, V y) {
+    if (cx == 0) return cy > 0 ? y : -y;
+    if (cy == 0) return cx > 0 ? x : -x;
+    if (cx > 0) return cy > 0 ? x + y : x - y;
+    return cy > 0 ? y - x : -(x + y);
+}
+
 // Chemical potential, Eq. 8.
-template <typename R>
-__device__ __forceinline__ R chem_pot(const Consts<R>& C, R phi, R lap_phi) {
-    return R(4) * C.beta * phi * (phi - R(1)) * (phi - R(0.5)) - C.kappa * lap_phi;
+template <typename V, typename S>
+__device__ __forceinline__ V chem_pot(const Consts<S>& C, V phi, V lap_phi) {
+    return V(S(4) * C.beta) * phi * (phi - V(S(1))) * (phi - V(S(0.5))) - V(C.kappa) * lap_phi;
 }
 
 // 3x3 neighbourhood z[dy+1][dx+1] of a field around a cell.
-template <typename R>
+template <typename V>
 struct Nbr {
-    R z[3][3];
+    using S = typename ScalarOf<V>::type;
+    V z[3][3];
     // Isotropic gradient, Eq. 30a: sum_{i!=0} w_i c_i z(x + c_i) / c_s^2.
-    __device__ __forceinline__ void grad(R& gx, R& gy) const {
-        const R w1 = R(3) / R(9), w2 = R(3) / R(36);   // w_i / c_s^2
-        gx = w1 * (z[1][2] - z[1][0]) + w2 * ((z[2][2] - z[2][0]) + (z[0][2] - z[0][0]));
-        gy = w1 * (z[2][1] - z[0][1]) + w2 * ((z[2][2] - z[0][2]) + (z[2][0] - z[0][0]));
+    __device__ __forceinline__ void grad(V& gx, V& gy) const {
+        const V w1 = V(S(3) / S(9)), w2 = V(S(3) / S(36));   // w_i / c_s^2
+        gx = fmadd(w1, z[1][2] - z[1][0], w2 * ((z[2][2] - z[2][0]) + (z[0][2] - z[0][0])));
+        gy = fmadd(w1, z[2][1] - z[0][1], w2 * ((z[2][2] - z[0][2]) + (z[2][0] - z[0][0])));
     }
     // Isotropic Laplacian, Eq. 30b: sum_{i!=0} 2 w_i (z(x + c_i) - z(x)) / c_s^2.
-    __device__ __forceinline__ R lap() const {
-        const R c = z[1][1];
-        const R a = (z[1][2] - c) + (z[2][1] - c) + (z[1][0] - c) + (z[0][1] - c);
-        const R d = (z[2][2] - c) + (z[2][0] - c) + (z[0][0] - c) + (z[0][2] - c);
-        return (R(6) / R(9)) * a + (R(6) / R(36)) * d;
+    __device__ __forceinline__ V lap() const {
+        const V c = z[1][1];
+        const V a = (z[1][2] - c) + (z[2][1] - c) + (z[1][0] - c) + (z[0][1] - c);
+        const V d = (z[2][2] - c) + (z[2][0] - c) + (z[0][0] - c) + (z[0][2] - c);
+        return fmadd(V(S(6) / S(9)), a, V(S(6) / S(36)) * d);
     }
 };
 
 // Macroscopic stage of one cell (steps 1-6 of the time step): inputs are the
 // post-streaming g, phi, mu and the stencils of phi, mu and p_prev.
-template <typename R>
+template <typename V>
 struct Macro {
-    R rho, ux, uy, Fx, Fy, Ftx, Fty, S, S1, tgm /* tau_g - 1/2 */, inv_tau_g, p;
+    V rho, ux, uy, Fx, Fy, Ftx, Fty, S, S1, tgm /* tau_g - 1/2 */, inv_tau_g, p;
 };
 
-template <typename R>
-__device__ __forceinline__ Macro<R> macroscopic(const Consts<R>& C, const R g[9], R phi, R mu,
-                                                R gphix, R gphiy, R gmux, R gmuy, R lapmu,
-                                                R gpx, R gpy) {
-    Macro<R> m;
-    m.rho = C.rho_B + phi * C.drho;                     // Eq. 3aa (phi_B = 0)
-    const R drx = C.drho * gphix, dry = C.drho * gphiy; // grad rho
-    m.S1 = C.qim ? -C.gammaM * lapmu : R(0);            // Sec. 3.2.1
-    R Fsx, Fsy;                                         // surface tension
+template <typename V, typename S>
+__device__ __forceinline__ Macro<V> macroscopic(const Consts<S>& C, const V g[9], V phi, V mu,
+                                                V gphix, V gphiy, V gmux, V gmuy, V lapmu,
+                                                V gpx, V gpy) {
+    Macro<V> m;
+    m.rho = fmadd(phi, V(C.drho), V(C.rho_B));         // Eq. 3aa (phi_B = 0)
+    const V drx = V(C.drho) * gphix, dry = V(C.drho) * gphiy;   // grad rho
+    m.S1 = C.qim ? V(-C.gammaM) * lapmu : V(S(0));     // Sec. 3.2.1
+    V Fsx, Fsy;                                        // surface tension
     if (C.sforce == 0) { Fsx = mu * gphix; Fsy = mu * gphiy; }
-    else { Fsx = -phi * gmux; Fsy = -phi * gmuy; }
-    m.Fx = Fsx + C.force_x;
-    m.Fy = Fsy + C.force_y - (m.rho - C.rho_A) * C.gravity;   // buoyancy, Sec. 4.4
-    const R jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const R jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    const R inv_rho = rcp(m.rho);
-    m.ux = (jx + R(0.5) * m.Fx) * inv_rho;              // Eq. 27a
-    m.uy = (jy + R(0.5) * m.Fy) * inv_rho;
-    m.S = m.ux * drx + m.uy * dry + m.rho * m.S1;       // S = u.grad(rho) + rho S1
-    if (C.uniform_nu) {                                 // nu_A = nu_B: constant tau_g
-        m.tgm = C.tgm0;
-        m.inv_tau_g = C.inv_tau_g0;
-    } else {                                            // viscosity, Sec. 3.2.2 / 4.3
-        R nu;
-        if (C.visc == 0) nu = rcp(phi * (C.inv_nu_A - C.inv_nu_B) + C.inv_nu_B);
-        else nu = (phi >= R(0.5) ? C.mu_A : C.mu_B) * inv_rho;
-        m.tgm = R(3) * nu;                              // tau_g - 1/2 = nu / c_s^2
-        m.inv_tau_g = rcp(m.tgm + R(0.5));
+    else { Fsx = -(phi * gmux); Fsy = -(phi * gmuy); }
+    m.Fx = Fsx + V(C.force_x);
+    m.Fy = fmadd(m.rho - V(C.rho_A), V(-C.gravity), Fsy + V(C.force_y));   // buoyancy, Sec. 4.4
+    const V jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const V jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    const V inv_rho = rcp(m.rho);
+    m.ux = fmadd(V(S(0.5)), m.Fx, jx) * inv_rho;      // Eq. 27a
+    m.uy = fmadd(V(S(0.5)), m.Fy, jy) * inv_rho;
+    m.S = fmadd(m.ux, drx, fmadd(m.uy, dry, m.rho * m.S1));   // S = u.grad(rho) + rho S1
+    if (C.uniform_nu) {                                // nu_A = nu_B: constant tau_g
+        m.tgm = V(C.tgm0);
+        m.inv_tau_g = V(C.inv_tau_g0);
+    } else {                                           // viscosity, Sec. 3.2.2 / 4.3
+        V nu;
+        if (C.visc == 0) nu = rcp(fmadd(phi, V(C.inv_nu_A - C.inv_nu_B), V(C.inv_nu_B)));
+        else nu = step_pick(phi, C.mu_A, C.mu_B) * inv_rho;
+        m.tgm = V(S(3)) * nu;                          // tau_g - 1/2 = nu / c_s^2
+        m.inv_tau_g = rcp(m.tgm + V(S(0.5)));
     }
-    m.Ftx = m.Fx - gpx + drx * (R(1) / R(3));           // F~ = F - grad(p - rho c_s^2)
-    m.Fty = m.Fy - gpy + dry * (R(1) / R(3));
-    const R w0 = w_of<R>(0);
-    R G0 = R(0);
+    m.Ftx = fmadd(drx, V(S(1) / S(3)), m.Fx - gpx);   // F~ = F - grad(p - rho c_s^2)
+    m.Fty = fmadd(dry, V(S(1) / S(3)), m.Fy - gpy);
+    const S w0 = w_of<S>(0);
+    V G0 = V(S(0));
     if (C.pscheme == 0) {         // simplified G_0 printed after Eq. 34
-        G0 = w0 * (R(0.5) * m.rho * m.S1 - R(3) * (m.ux * (m.Fx - gpx) + m.uy * (m.Fy - gpy)));
+        const V uFp = fmadd(m.ux, m.Fx - gpx, m.uy * (m.Fy - gpy));
+        G0 = V(w0) * fmadd(V(S(0.5)) * m.rho, m.S1, V(S(-3)) * uFp);
     } else if (C.pscheme == 1) {  // Eq. 34 at i = 0
-        G0 = w0 * (m.S - R(3) * (m.ux * m.Ftx + m.uy * m.Fty) - m.rho * m.S1);
+        const V uFt = fmadd(m.ux, m.Ftx, m.uy * m.Fty);
+        G0 = V(w0) * (fmadd(V(S(-3)), uFt, m.S) - m.rho * m.S1);
     }
-    const R sum_g = (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
-    const R uu = m.ux * m.ux + m.uy * m.uy;
-    const R s0 = -w0 * R(1.5) * uu;                     // s_0(u)
-    // Eq. 28 (Eq. 29 for the previous scheme): c_s^2 / (1 - w0) = 3/5
-    m.p = R(0.6) * (sum_g + R(0.5) * m.S + m.rho * s0 + m.tgm * G0);
+    const V sum_g = (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+    const V uu = fmadd(m.ux, m.ux, m.uy * m.uy);
+    // Eq. 28 (Eq. 29 for the previous scheme): c_s^2 / (1 - w0) = 3/5, s_0 = -1.5 w0 u.u
+    m.p = V(S(0.6)) * fmadd(m.tgm, G0, fmadd(m.rho * V(S(-1.5) * w0), uu, fmadd(V(S(0.5)), m.S, sum_g)));
     return m;
 }
 
@@ -297,64 +350,112 @@ __device__ __forceinline__ Macro<R> macroscopic(const Consts<R>& C, const R g[9]
 //   s_i   = w (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
 //   G_i   = w [S + 3 c.F + 4.5 (2 (c.u)(c.F~) - (2/3) u.F~) + 1.5 (|c|^2 - 2/3) rho S1]
 //   h^eq_i = w (eta mu + 3 c.(phi u)),  R_i = (1 - 1/(2 tau_h)) 3 w c.d_t(phi u).
-template <typename R>
-__device__ __forceinline__ void collide_cell(const Consts<R>& C, const Macro<R>& m, R phi, R mu,
-                                             R ddx, R ddy, const R g[9], const R h[9],
-                                             R gpost[9], R hpost[9]) {
-    const R uu = m.ux * m.ux + m.uy * m.uy;
-    const R uFt = m.ux * m.Ftx + m.uy * m.Fty;
-    const R om = m.inv_tau_g, om1 = R(1) - om, gsrc = R(1) - R(0.5) * om;
-    const R omh = C.inv_tau_h, omh1 = R(1) - omh;
-    const R p3 = R(3) * m.p;
-    const R rS1 = m.rho * m.S1;
-    const R etamu = C.eta * mu;
-    const R phiux = phi * m.ux, phiuy = phi * m.uy;
+// The collision written once, handing each result to emit(i, g*_i, h*_i) as soon
+// as its pair of directions is formed (rest direction first), so callers that
+// store right away keep few values alive.
+template <typename V, typename S, typename Emit>
+__device__ __forceinline__ void collide_emit(const Consts<S>& C, const Macro<V>& m, V phi, V mu,
+                                             V ddx, V ddy, const V g[9], const V h[9], Emit&& emit) {
+    const V uu = fmadd(m.ux, m.ux, m.uy * m.uy);
+    const V uFt = fmadd(m.ux, m.Ftx, m.uy * m.Fty);
+    const V om = m.inv_tau_g, om1 = V(S(1)) - om;
+    const V gsrc = fmadd(V(S(-0.5)), om, V(S(1)));
+    const V omh = V(C.inv_tau_h), omh1 = V(S(1) - C.inv_tau_h);
+    const V p3 = V(S(3)) * m.p;
+    const V rS1 = m.rho * m.S1;
+    const V etamu = V(C.eta) * mu;
+    const V phiux = phi * m.ux, phiuy = phi * m.uy;
+    const V uu15 = V(S(-1.5)) * uu;
     // rest direction (c = 0): G_0 = w0 (S - 3 u.F~ - rho S1), R_0 = 0
     {
-        const R w0 = w_of<R>(0);
-        const R geq = (w0 - R(1)) * p3 + m.rho * (-w0 * R(1.5) * uu);
-        const R G = w0 * (m.S - R(3) * uFt - rS1);
-        gpost[0] = om1 * g[0] + (om * geq + gsrc * G);
-        const R heq = phi + (w0 - R(1)) * etamu;
-        hpost[0] = omh1 * h[0] + omh * heq;
+        const S w0 = w_of<S>(0);
+        const V geq = fmadd(V(w0 - S(1)), p3, m.rho * (V(w0) * uu15));
+        const V G = V(w0) * (fmadd(V(S(-3)), uFt, m.S) - rS1);
+        const V heq = fmadd(V(w0 - S(1)), etamu, phi);
+        emit(0, fmadd(om1, g[0], fmadd(om, geq, gsrc * G)), fmadd(omh1, h[0], omh * heq));
     }
 #pragma unroll
     for (int i = 1; i <= 6; ++i) {
         if (i == 3 || i == 4) continue;          // pairs (1,3) (2,4) (5,7) (6,8)
         const int j = opp_of(i);
-        const R w = w_of<R>(i);
-        const R ex = R(cx_of(i)), ey = R(cy_of(i));
-        const R c2 = ex * ex + ey * ey;
-        const R cu = ex * m.ux + ey * m.uy;
-        const R cF = ex * m.Fx + ey * m.Fy;
-        const R cFt = ex * m.Ftx + ey * m.Fty;
-        const R geq_e = w * (p3 + m.rho * (R(4.5) * cu * cu - R(1.5) * uu));
-        const R geq_o = w * m.rho * R(3) * cu;
-        const R G_e = w * (m.S + R(9) * cu * cFt - R(3) * uFt + R(1.5) * (c2 - R(2) / R(3)) * rS1);
-        const R G_o = w * R(3) * cF;
-        gpost[i] = om1 * g[i] + (om * (geq_e + geq_o) + gsrc * (G_e + G_o));
-        gpost[j] = om1 * g[j] + (om * (geq_e - geq_o) + gsrc * (G_e - G_o));
-        const R heq_e = w * etamu;
-        const R heq_o = R(3) * w * (ex * phiux + ey * phiuy);
-        const R R_o = C.src_h * R(3) * w * (ex * ddx + ey * ddy);
-        hpost[i] = omh1 * h[i] + (omh * (heq_e + heq_o) + R_o);
-        hpost[j] = omh1 * h[j] + (omh * (heq_e - heq_o) - R_o);
+        const int cx = cx_of(i), cy = cy_of(i);
+        const S w = w_of<S>(i);
+        const S c2 = S(cx * cx + cy * cy);
+        const V cu = cdot(cx, cy, m.ux, m.uy);
+        const V cF = cdot(cx, cy, m.Fx, m.Fy);
+        const V cFt = cdot(cx, cy, m.Ftx, m.Fty);
+        const V geq_e = V(w) * fmadd(m.rho, fmadd(V(S(4.5)) * cu, cu, uu15), p3);
+        const V geq_o = V(S(3) * w) * (m.rho * cu);
+        const V G_e = V(w) * fmadd(V(S(9)) * cu, cFt,
+                                   fmadd(V(S(-3)), uFt, fmadd(V(S(1.5) * (c2 - S(2) / S(3))), rS1, m.S)));
+        const V G_o = V(S(3) * w) * cF;
+        const V heq_e = V(w) * etamu;
+        const V heq_o = V(S(3) * w) * cdot(cx, cy, phiux, phiuy);
+        const V R_o = V(C.src_h * S(3) * w) * cdot(cx, cy, ddx, ddy);
+        emit(i, fmadd(om1, g[i], fmadd(om, geq_e + geq_o, gsrc * (G_e + G_o))),
+             fmadd(omh1, h[i], fmadd(omh, heq_e + heq_o, R_o)));
+        emit(j, fmadd(om1, g[j], fmadd(om, geq_e - geq_o, gsrc * (G_e - G_o))),
+             fmadd(omh1, h[j], fmadd(omh, heq_e - heq_o, -R_o)));
     }
 }
+
+template <typename V, typename S>
+__device__ __forceinline__ void collide_cell(const Consts<S>& C, const Macro<V>& m, V phi, V mu,
+                                             V ddx, V ddy, const V g[9], const V h[9],
+                                             V gpost[9], V hpost[9]) {
+    collide_emit(C, m, phi, mu, ddx, ddy, g, h, [&](int i, V gi, V hi) {
+        gpost[i] = gi;
+        hpost[i] = hi;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous copies global -> shared by each thread for itself (LDGSTS):
+// the data lands in shared memory without passing through registers, and
+// cp.async.wait_all makes this thread's copies visible to it.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // The fused step kernel. Rings in shared memory (slots by row number, powers of
 // two so a slot is one AND):
-//   phi   [8][TX+4]  rows Y-2 .. Y+2 (and the lead row being written)
-//   mu    [4][TX+2]  rows Y-1 .. Y+1
-//   p     [4][TX+2]  rows Y-1 .. Y+1 of the previous step's pressure
-//   h     [4][9][TX] post-streaming h of rows Y .. Y+2d, kept for the collision
+//   phi   [8][TX+4]      rows Y-2 .. Y+2 (and the lead row being written)
+//   mu    [4][TX+2]      rows Y-1 .. Y+1
+//   p     [4][TX+2]      rows Y-1 .. Y+1 of the previous step's pressure
+//   h     [4][P][TX+4]   post-streaming h of rows Y .. Y+3d over the strip and
+//                        its 2-column halo (P = 9 planes; conservative forms keep
+//                        h_0 as a float pair in the first two planes' room)
+// ASYNC (FP32 storage of h and p): each thread copies the h and p values of its
+// own columns of the next iteration's lead row (Y + 3d) and p row (Y + 2d) into
+// these rings with cp.async right after the first barrier of the iteration, so
+// the copies fly during the mu pass and the collision; the next phase A only
+// waits for its own copies. Otherwise phase A loads them synchronously.
 template <int FORM, int TX>
 struct StepSmem {
-    using R = typename Form<FORM>::R;
-    static constexpr int PW = TX + 4;   // phi ring row: strip + 2-column halo each side
+    using F = Form<FORM>;
+    using R = typename F::R;
+    static constexpr int PW = TX + 4;   // phi / h ring row: strip + 2-column halo each side
     static constexpr int MW = TX + 2;   // mu / p ring row: strip + 1-column halo
-    static constexpr size_t elems = 8 * PW + 4 * MW + 4 * MW + 4 * 9 * TX;
+    static constexpr int HPL = F::cons ? 10 : 9;   // R-sized planes of one h slot
+    static constexpr size_t elems = 8 * PW + 4 * MW + 4 * MW + 4 * HPL * PW;
     static constexpr size_t bytes = elems * sizeof(R);
 };
 
@@ -367,18 +468,23 @@ struct StepOcc {
                                      ? (sizeof(typename Form<FORM>::R) == 8 ? 384 : 1024) / TX : 1;
 };
 
-template <int FORM, int TX>
+// The asynchronous variant needs 4- or 8-byte elements for h and p (cp.async).
+template <int FORM>
+constexpr bool kAsyncOk = sizeof(typename Form<FORM>::R) == 4 && !Form<FORM>::h16;
+
+template <int FORM, int TX, bool ASYNC>
 __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(const StepArgs a) {
     using F = Form<FORM>;
     using R = typename F::R;
     using AT = typename F::AT;
     using SM = StepSmem<FORM, TX>;
-    constexpr int PW = SM::PW, MW = SM::MW;
+    static_assert(!ASYNC || kAsyncOk<FORM>, "asynchronous copies need 4-byte h and p");
+    constexpr int PW = SM::PW, MW = SM::MW, HPL = SM::HPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* phiR = reinterpret_cast<R*>(smem_raw);   // [8][PW]
     R* muR = phiR + 8 * PW;                      // [4][MW]
     R* pR = muR + 4 * MW;                        // [4][MW]
-    R* hR = pR + 4 * MW;                         // [4][9][TX]
+    R* hR = pR + 4 * MW;                         // [4][HPL][PW]
 
     const WorkItem wk = a.work[blockIdx.x];
     Consts<R> C;
@@ -407,6 +513,11 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
     auto ghost = [ny, walls](int y) { return walls && (y < 0 || y >= ny); };
     auto mirror = [ny](int y) { return y < 0 ? -1 - y : 2 * ny - 1 - y; };
     auto rowoff = [&](int y) { return base + rowg(y) * nx; };
+    // h slot of row y: plane i (i >= 1 for conservative forms) at hplane(y, i)[s],
+    // conservative h_0 pair at hpair(y)[s]
+    auto hslot = [&](int y) { return hR + ((y + 64) & 3) * HPL * PW; };
+    auto hplane = [&](int y, int i) { return hslot(y) + (F::cons ? i + 1 : i) * PW; };
+    auto hpair = [&](int y) { return reinterpret_cast<float2*>(hslot(y)); };
 
     // Per-thread columns, fixed for the whole march.
     const bool lead0 = tid < w + 4, lead1 = tid + TX < w + 4;      // phi / h columns x0-2+s
@@ -419,24 +530,48 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
     const int X = x0 + tid;
     const int colm = act ? wrapx(X - 1) : 0, colp = act ? wrapx(X + 1) : 0;
 
-    // A. phi of row L over columns x0-2 .. x0+w+1; h of the strip kept for the collision.
-    auto lead_row = [&](int L) {
+    // phi (and its low part) of column s from h values already in the slot of row L
+    auto phi_from_slot = [&](int L, int s) {
         R* prow = phiR + ((L + 64) & 7) * PW;
-        if (ghost(L)) {   // mirror ghost row next to a wall (reading Q7)
-            const R* src = phiR + ((mirror(L) + 64) & 7) * PW;
-            if (lead0) prow[tid] = src[tid];
-            if (lead1) prow[tid + TX] = src[tid + TX];
-            return;
+        if constexpr (F::cons) {
+            R s8 = R(0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) s8 += hplane(L, i)[s];
+            float2* pr = hpair(L);
+            const float2 h0 = pr[s];
+            float sm, e, hi, lo;
+            two_sum(h0.x, s8, sm, e);
+            fast_two_sum(sm, e + h0.y, hi, lo);
+            prow[s] = hi;
+            pr[s].y = lo;                      // low part of phi, read by the collision
+        } else {
+            R phi = hplane(L, 0)[s];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) phi += hplane(L, i)[s];
+            prow[s] = phi;
         }
+    };
+    auto ghost_row = [&](int L) {   // mirror ghost row next to a wall (reading Q7)
+        R* prow = phiR + ((L + 64) & 7) * PW;
+        const R* src = phiR + ((mirror(L) + 64) & 7) * PW;
+        if (lead0) prow[tid] = src[tid];
+        if (lead1) prow[tid + TX] = src[tid + TX];
+    };
+    // A (synchronous). phi of row L over columns x0-2 .. x0+w+1; h kept in the slot.
+    auto lead_row = [&](int L) {
+        if (ghost(L)) { ghost_row(L); return; }
         const int ro = rowoff(L);
-        R* hrow = hR + ((L + 64) & 3) * 9 * TX;
+        R* prow = phiR + ((L + 64) & 7) * PW;
         auto column = [&](int s, int col) {
             R hv[9], lo;
             prow[s] = io.phi_of(ro + col, hv, lo);          // Eq. 18
-            if (s >= 2 && s < w + 2) {
-                if constexpr (F::cons) hv[0] = lo;           // low part of phi in h_0's slot
+            if constexpr (F::cons) {
+                hpair(L)[s] = make_float2(hv[0], lo);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) hrow[i * TX + (s - 2)] = hv[i];
+                for (int i = 1; i < 9; ++i) hplane(L, i)[s] = hv[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) hplane(L, i)[s] = hv[i];
             }
         };
         if (lead0) column(tid, lc0);
@@ -448,6 +583,39 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
         R* dst = pR + ((M + 64) & 3) * MW;
         if (mid0) dst[tid] = R(src[pc0]);
         if (mid1) dst[tid + TX] = R(src[pc1]);
+    };
+    // Asynchronous copies of this thread's columns of lead row L and p row M.
+    auto prefetch = [&](int L, int M) {
+        if constexpr (ASYNC) {
+            if (!ghost(L)) {
+                const int ro = rowoff(L);
+                auto column = [&](int s, int col) {
+                    const int cc = ro + col;
+                    if constexpr (F::cons) {
+                        cp_async8(&hpair(L)[s], io.h0in + cc);
+#pragma unroll
+                        for (int i = 1; i < 9; ++i) cp_async4(&hplane(L, i)[s], io.hin + io.hoff(i) + cc);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) cp_async4(&hplane(L, i)[s], io.hin + io.hoff(i) + cc);
+                    }
+                };
+                if (lead0) column(tid, lc0);
+                if (lead1) column(tid + TX, lc1);
+            }
+            const AT* src = p_in + base + (ghost(M) ? mirror(M) : rowg(M)) * nx;
+            R* dst = pR + ((M + 64) & 3) * MW;
+            if (mid0) cp_async4(&dst[tid], src + pc0);
+            if (mid1) cp_async4(&dst[tid + TX], src + pc1);
+            cp_async_commit();
+        }
+    };
+    // A (asynchronous). phi of row L from the values this thread copied itself.
+    auto lead_row_async = [&](int L) {
+        cp_async_wait_all();
+        if (ghost(L)) { ghost_row(L); return; }
+        if (lead0) phi_from_slot(L, tid);
+        if (lead1) phi_from_slot(L, tid + TX);
     };
     // B. mu of row M (Eq. 8 with the Laplacian of Eq. 30b), columns x0-1 .. x0+w.
     auto mu_row = [&](int M) {
@@ -499,9 +667,14 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
         np.grad(gpx, gpy);
         const R lapmu = nmu.lap();
         R h[9];
-        const R* hrow = hR + ((Y + 64) & 3) * 9 * TX + tid;
+        if constexpr (F::cons) {
+            h[0] = hpair(Y)[tid + 2].y;        // low part of phi
 #pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = hrow[i * TX];
+            for (int i = 1; i < 9; ++i) h[i] = hplane(Y, i)[tid + 2];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = hplane(Y, i)[tid + 2];
+        }
 
         const Macro<R> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
         const R phiux = phi * m.ux, phiuy = phi * m.uy;
@@ -559,6 +732,8 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
     p_row(Y0 - d);
     p_row(Y0);
     __syncthreads();
+    // the slot of row Y0 - 2d (read only above) takes the first lead row
+    if constexpr (ASYNC) prefetch(Y0 + 2 * d, Y0 + d);
     mu_row(Y0);
     mu_row(Y0 - d);
     __syncthreads();
@@ -575,9 +750,18 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
             pux = R(phiu[c]);
             puy = R(phiu[S + c]);
         }
-        lead_row(Y + 2 * d);
-        p_row(Y + d);
+        if constexpr (ASYNC) {
+            lead_row_async(Y + 2 * d);
+        } else {
+            lead_row(Y + 2 * d);
+            p_row(Y + d);
+        }
         __syncthreads();
+        // Every thread is past the collision of row Y - d: the h slot of row Y - d
+        // and the p slot of row Y - 2d are free for the next iteration's rows.
+        if constexpr (ASYNC) {
+            if (k + 1 < wk.nrows) prefetch(Y + 3 * d, Y + 2 * d);
+        }
         mu_row(Y + d);
         __syncthreads();
         collide_row(Y, g, pux, puy);

@@ -45,7 +45,12 @@ struct StepArgs {
     long long S;                        // plane stride in cells
     const DevInst* inst;
     const WorkItem* work;
+    int* status;                        // device status word (0 = ok), see kStatusTimeout
 };
+
+// Value a kernel writes to the status word when a bounded device wait runs out
+// (equal to LBM_ETIMEOUT of include/lbm.h).
+constexpr int kStatusTimeout = 5;
 
 // Buffers of the macroscopic / diagnostic kernels.
 struct AuxArgs {
@@ -65,10 +70,18 @@ constexpr int kDiagQuantities = 14;   // quantities of diag_pass (lbm_device.cuh
 constexpr int kDiagBlocks = 304;      // 2 x 152 SMs
 
 // Launchers, instantiated once per storage form in lbm_form<N>.cu.
-template <int FORM> cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s);
+// Step kernel variants: synchronous loads; per-thread cp.async prefetch (FP32
+// storage of h and p); bulk copies by the TMA (FP32 arithmetic, 16-byte rows);
+// two cells per thread in packed FP32 (FP32 arithmetic, nx even, tile >= 64).
+enum StepVariant { kPlain = 0, kAsync = 1, kTma = 2, kPairs = 3 };
+template <int FORM> cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s,
+                                              int variant);
 template <int FORM> cudaError_t prepare_step_t();          // opt-in shared memory sizes
 template <int FORM> size_t step_smem_t(int tile_x);
-template <int FORM> int step_occupancy_t(int tile_x);      // resident blocks per SM
+template <int FORM> int step_occupancy_t(int tile_x, int variant);   // resident blocks per SM
+template <int FORM> bool has_tma_t();                      // the form has a TMA-fed kernel
+template <int FORM> bool has_async_t();                    // the form has the cp.async kernel
+template <int FORM> bool has_pairs_t();                    // the form has the paired kernel
 template <int FORM> cudaError_t launch_init_t(const StepArgs& a, const double* phi0, int instance,
                                               int ncells, cudaStream_t s);
 template <int FORM> cudaError_t launch_fields_t(const AuxArgs& a, int ncells, cudaStream_t s);

@@ -3,32 +3,91 @@
 #pragma once
 
 #include "lbm_device.cuh"
+#include "lbm_step_tma.cuh"
+#include "lbm_step_x2.cuh"
 
 namespace lbm {
 
+template <int FORM>
+constexpr bool kHasTma = sizeof(typename Form<FORM>::R) == 4;
+
+template <int FORM>
+bool has_tma_t() { return kHasTma<FORM>; }
+
+template <int FORM>
+bool has_async_t() { return kAsyncOk<FORM>; }
+
+template <int FORM>
+bool has_pairs_t() { return kHasTma<FORM>; }   // the FP32-arithmetic forms
+
+// paired kernel: tile_x columns per block, tile_x / 2 threads
 template <int FORM, int TX>
-static cudaError_t launch_step_tx(const StepArgs& a, int nwork, cudaStream_t s) {
-    const size_t smem = StepSmem<FORM, TX>::bytes;
-    step_kernel<FORM, TX><<<nwork, TX, smem, s>>>(a);
+static cudaError_t launch_pairs_tx(const StepArgs& a, int nwork, cudaStream_t s) {
+    step_kernel_x2<FORM, TX><<<nwork, TX, X2Smem<FORM, TX>::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+// variant: kPlain (synchronous loads), kAsync (per-thread cp.async prefetch),
+// kTma (bulk copies); the caller only asks for a variant the form has.
+template <int FORM, int TX>
+static cudaError_t launch_step_tx(const StepArgs& a, int nwork, cudaStream_t s, int variant) {
+    if constexpr (kHasTma<FORM>) {
+        if (variant == kTma) {
+            step_kernel_tma<FORM, TX><<<nwork, TX, TmaSmem<FORM, TX>::bytes, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (kAsyncOk<FORM>) {
+        if (variant == kAsync) {
+            step_kernel<FORM, TX, true><<<nwork, TX, StepSmem<FORM, TX>::bytes, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    step_kernel<FORM, TX, false><<<nwork, TX, StepSmem<FORM, TX>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int FORM>
-cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s) {
+cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s, int variant) {
     if (nwork <= 0) return cudaSuccess;
+    if constexpr (kHasTma<FORM>) {
+        if (variant == kPairs) {
+            switch (tile_x) {
+                case 64: return launch_pairs_tx<FORM, 32>(a, nwork, s);
+                case 128: return launch_pairs_tx<FORM, 64>(a, nwork, s);
+                case 256: return launch_pairs_tx<FORM, 128>(a, nwork, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     switch (tile_x) {
-        case 32: return launch_step_tx<FORM, 32>(a, nwork, s);
-        case 64: return launch_step_tx<FORM, 64>(a, nwork, s);
-        case 128: return launch_step_tx<FORM, 128>(a, nwork, s);
-        case 256: return launch_step_tx<FORM, 256>(a, nwork, s);
+        case 32: return launch_step_tx<FORM, 32>(a, nwork, s, variant);
+        case 64: return launch_step_tx<FORM, 64>(a, nwork, s, variant);
+        case 128: return launch_step_tx<FORM, 128>(a, nwork, s, variant);
+        case 256: return launch_step_tx<FORM, 256>(a, nwork, s, variant);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int FORM, int TX>
 static cudaError_t prep_tx() {
-    return cudaFuncSetAttribute(step_kernel<FORM, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)StepSmem<FORM, TX>::bytes);
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<FORM, TX, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)StepSmem<FORM, TX>::bytes);
+    if constexpr (kAsyncOk<FORM>) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel<FORM, TX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)StepSmem<FORM, TX>::bytes);
+    }
+    if constexpr (kHasTma<FORM>) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel_tma<FORM, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TmaSmem<FORM, TX>::bytes);
+        if (e == cudaSuccess && TX >= 32 && TX <= 128)
+            e = cudaFuncSetAttribute(step_kernel_x2<FORM, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)X2Smem<FORM, TX>::bytes);
+    }
+    return e;
 }
 
 template <int FORM>
@@ -51,18 +110,48 @@ size_t step_smem_t(int tile_x) {
     }
 }
 
-template <int FORM>
-int step_occupancy_t(int tile_x) {
+template <int FORM, int TX>
+static int occ_tx(int variant) {
     int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (tile_x) {
-        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<FORM, 32>, 32, StepSmem<FORM, 32>::bytes); break;
-        case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<FORM, 64>, 64, StepSmem<FORM, 64>::bytes); break;
-        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<FORM, 128>, 128, StepSmem<FORM, 128>::bytes); break;
-        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<FORM, 256>, 256, StepSmem<FORM, 256>::bytes); break;
-        default: break;
+    cudaError_t e;
+    if constexpr (kHasTma<FORM>) {
+        if (variant == kPairs) {
+            if constexpr (TX >= 64) {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_x2<FORM, TX / 2>, TX / 2,
+                                                                  X2Smem<FORM, TX / 2>::bytes);
+                return e == cudaSuccess ? n : 0;
+            }
+            return 0;
+        }
     }
+    if constexpr (kHasTma<FORM>) {
+        if (variant == kTma) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_tma<FORM, TX>, TX,
+                                                              TmaSmem<FORM, TX>::bytes);
+            return e == cudaSuccess ? n : 0;
+        }
+    }
+    if constexpr (kAsyncOk<FORM>) {
+        if (variant == kAsync) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<FORM, TX, true>, TX,
+                                                              StepSmem<FORM, TX>::bytes);
+            return e == cudaSuccess ? n : 0;
+        }
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<FORM, TX, false>, TX,
+                                                      StepSmem<FORM, TX>::bytes);
     return e == cudaSuccess ? n : 0;
+}
+
+template <int FORM>
+int step_occupancy_t(int tile_x, int variant) {
+    switch (tile_x) {
+        case 32: return occ_tx<FORM, 32>(variant);
+        case 64: return occ_tx<FORM, 64>(variant);
+        case 128: return occ_tx<FORM, 128>(variant);
+        case 256: return occ_tx<FORM, 256>(variant);
+        default: return 0;
+    }
 }
 
 static inline int grid_for(int ncells, int block) {
@@ -104,10 +193,13 @@ cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h, do
 }
 
 #define LBM_INSTANTIATE_FORM(F)                                                               \
-    template cudaError_t launch_step_t<F>(int, const StepArgs&, int, cudaStream_t);           \
+    template cudaError_t launch_step_t<F>(int, const StepArgs&, int, cudaStream_t, int);      \
     template cudaError_t prepare_step_t<F>();                                                 \
     template size_t step_smem_t<F>(int);                                                      \
-    template int step_occupancy_t<F>(int);                                                    \
+    template int step_occupancy_t<F>(int, int);                                               \
+    template bool has_tma_t<F>();                                                             \
+    template bool has_async_t<F>();                                                           \
+    template bool has_pairs_t<F>();                                                           \
     template cudaError_t launch_init_t<F>(const StepArgs&, const double*, int, int,           \
                                           cudaStream_t);                                      \
     template cudaError_t launch_fields_t<F>(const AuxArgs&, int, cudaStream_t);               \

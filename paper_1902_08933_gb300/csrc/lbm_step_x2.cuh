@@ -1,0 +1,376 @@
+// lbm_step_x2.cuh -- the fused step kernel with two cells per thread.
+//
+// Same row march and arithmetic as step_kernel (lbm_device.cuh) for the FP32
+// forms, but every thread owns two horizontally adjacent cells (X, X+1), X even,
+// and computes them together in the two lanes of the packed FP32 instructions of
+// sm_100+ (FFMA2 / FADD2 / FMUL2 through the F2 value type). A pair is one 8-byte
+// (FP32) or 4-byte (FP16) element in memory, so the loads of g, h, phi*u and p
+// and the stores that keep the pair together (directions with c_x = 0) are
+// vector accesses; the shared-memory stencils read three 8-byte words per row.
+// Per cell this halves the address arithmetic, the per-row bookkeeping and the
+// floating-point instruction count of the collision.
+//
+// Rings in shared memory, each row RW = 2 TX + 8 entries, column x at index
+// x - x0 + 4 (even columns on 8-byte boundaries; the outer two entries on each
+// side are padding that only ever feeds values nobody reads):
+//   phi [8][RW], mu [4][RW], p [4][RW] (FP32), and 4 slots of h in its storage
+//   type: [RW] (hi, lo) pairs of the conservative h_0, then the planes.
+// Loads of the lead row (h) and of the p row run ahead: each thread copies its
+// own column pairs of the next iteration's rows with cp.async right after the
+// first barrier of the iteration, and waits only for its own copies at the next
+// phase A (the same schedule as step_kernel<..., true>).
+// Requires nx even (a pair never straddles the periodic seam); the host checks.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ F2 ld_pair(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ F2 ld_pair(const __half* p) {
+    return F2(__half22float2(*reinterpret_cast<const __half2*>(p)));
+}
+__device__ __forceinline__ void st_pair(float* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+__device__ __forceinline__ void st_pair(__half* p, F2 v) {
+    *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
+}
+__device__ __forceinline__ void st_one(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_one(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ F2 lds_pair(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
+
+template <int FORM, int TX>
+struct X2Smem {
+    using F = Form<FORM>;
+    using HT = typename F::HT;
+    static constexpr int SW = 2 * TX;   // strip width in columns
+    static constexpr int RW = SW + 8;
+    static constexpr size_t H0B = F::cons ? (size_t)RW * sizeof(float2) : 0;   // h_0 pairs (hi, lo)
+    static constexpr size_t HPB = (size_t)RW * sizeof(HT);                      // one plane, storage type
+    static constexpr size_t SLOT = H0B + (F::cons ? 8 : 9) * HPB;
+    static constexpr size_t RINGS = (size_t)(8 * RW + 4 * RW + 4 * RW) * sizeof(float);
+    static constexpr size_t bytes = RINGS + 4 * SLOT;
+    static_assert(SLOT % 16 == 0 && RINGS % 16 == 0, "h slots must stay 16-byte aligned");
+};
+
+template <int FORM, int TX>
+struct X2Occ {   // register budget: 128 registers a thread
+    static constexpr int value = (512 / TX) > 0 ? 512 / TX : 1;
+};
+
+template <int FORM, int TX>
+__global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(const StepArgs a) {
+    using F = Form<FORM>;
+    using HT = typename F::HT;
+    using GT = typename F::GT;
+    using L = X2Smem<FORM, TX>;
+    static_assert(sizeof(typename F::R) == 4, "the paired kernel serves the FP32-arithmetic forms");
+    constexpr int SW = L::SW, RW = L::RW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* phiR = reinterpret_cast<float*>(smem_raw);   // [8][RW]
+    float* muR = phiR + 8 * RW;                          // [4][RW]
+    float* pR = muR + 4 * RW;                            // [4][RW]
+    unsigned char* hR = smem_raw + L::RINGS;             // [4] slots of L::SLOT bytes
+
+    const WorkItem wk = a.work[blockIdx.x];
+    Consts<float> C;
+    C.load(a.inst[wk.inst]);
+    const int nx = C.nx, ny = C.ny, walls = C.walls;
+    const int x0 = wk.x0, d = wk.dir;
+    const int w = min(SW, nx - x0);
+    const int tid = threadIdx.x;
+    const int base = (int)C.base;
+    const long long S = a.S;
+    const HT* hin = static_cast<const HT*>(a.h_in);
+    HT* hout = static_cast<HT*>(a.h_out);
+    const float2* h0in = static_cast<const float2*>(a.h0_in);
+    float2* h0out = static_cast<float2*>(a.h0_out);
+    const GT* gin = static_cast<const GT*>(a.g_in);
+    GT* gout = static_cast<GT*>(a.g_out);
+    const float* p_in = static_cast<const float*>(a.p_in);
+    float* p_out = static_cast<float*>(a.p_out);
+    float* phiu = static_cast<float*>(a.phiu);
+    const float hs = C.hs, ihs = C.ihs, gs = C.gs, igs = C.igs;
+
+    auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+    auto rowg = [ny, walls](int y) { return walls ? y : (y < 0 ? y + ny : (y >= ny ? y - ny : y)); };
+    auto ghost = [ny, walls](int y) { return walls && (y < 0 || y >= ny); };
+    auto mirror = [ny](int y) { return y < 0 ? -1 - y : 2 * ny - 1 - y; };
+    auto rowoff = [&](int y) { return base + rowg(y) * nx; };
+    auto prow = [&](int y) { return phiR + ((y + 64) & 7) * RW; };
+    auto mrow = [&](int y) { return muR + ((y + 64) & 3) * RW; };
+    auto qrow = [&](int y) { return pR + ((y + 64) & 3) * RW; };
+    auto hslot = [&](int y) { return hR + ((y + 64) & 3) * L::SLOT; };
+    // plane i (i >= 1 for conservative forms) of the h slot of row y, storage type
+    auto hplane = [&](int y, int i) {
+        return reinterpret_cast<HT*>(hslot(y) + L::H0B + (F::cons ? i - 1 : i) * L::HPB);
+    };
+    auto hpairs = [&](int y) { return reinterpret_cast<float2*>(hslot(y)); };   // conservative h_0
+    // stored pair -> arithmetic values
+    auto cvt_h = [&](F2 v) { return F::h16 ? v * ihs : v; };
+
+    // population i >= 1 (all i for non-conservative forms) of the cell pair at c
+    auto ld_h = [&](int i, int c) -> F2 {
+        const F2 v = ld_pair(hin + (long long)(F::cons ? i - 1 : i) * S + c);
+        return F::h16 ? v * ihs : v;
+    };
+    auto ld_g = [&](int i, int c) -> F2 {
+        const F2 v = ld_pair(gin + (long long)i * S + c);
+        return F::g16 ? v * igs : v;
+    };
+    auto st_h1 = [&](int k, int c, float v) {
+        st_one(hout + (long long)(F::cons ? k - 1 : k) * S + c, F::h16 ? v * hs : v);
+    };
+    auto st_h2 = [&](int k, int c, F2 v) {
+        st_pair(hout + (long long)(F::cons ? k - 1 : k) * S + c, F::h16 ? v * hs : v);
+    };
+    auto st_g1 = [&](int k, int c, float v) { st_one(gout + (long long)k * S + c, F::g16 ? v * gs : v); };
+    auto st_g2 = [&](int k, int c, F2 v) { st_pair(gout + (long long)k * S + c, F::g16 ? v * gs : v); };
+
+    // Column pairs of the lead / p rows: pair q covers x0-2+2q, x0-1+2q (ring index 2+2q).
+    const int nq = (w + 4) >> 1;
+    const bool q0 = tid < nq, q1 = tid + TX < nq;
+    const int qc0 = q0 ? wrapx(x0 - 2 + 2 * tid) : 0;
+    const int qc1 = q1 ? wrapx(x0 - 2 + 2 * (tid + TX)) : 0;
+    // The collision pair of this thread.
+    const bool act = 2 * tid < w;
+    const int X = x0 + 2 * tid;
+    const int jX = 2 * tid + 4;
+    const int colm = act ? wrapx(X - 1) : 0, colp = act ? wrapx(X + 2) : 0;
+
+    // phi of the pair at ring index j of row Lr from the raw values in its h slot
+    // (conservative forms: the low part of phi goes back into the h_0 pair slot)
+    auto phi_from_slot = [&](int Lr, int j) {
+        F2 phi;
+        if constexpr (F::cons) {
+            F2 s8 = F2(0.f);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) s8 = s8 + cvt_h(ld_pair(hplane(Lr, i) + j));
+            float4* h0p = reinterpret_cast<float4*>(&hpairs(Lr)[j]);
+            const float4 h0 = *h0p;                                     // (hi, lo) of both cells
+            float sa, ea, ha, la, sb, eb, hb, lb;
+            two_sum(h0.x, s8.v.x, sa, ea);
+            fast_two_sum(sa, ea + h0.y, ha, la);
+            two_sum(h0.z, s8.v.y, sb, eb);
+            fast_two_sum(sb, eb + h0.w, hb, lb);
+            phi = F2(ha, hb);
+            *h0p = make_float4(0.f, la, 0.f, lb);                       // low parts of phi
+        } else {
+            phi = cvt_h(ld_pair(hplane(Lr, 0) + j));
+#pragma unroll
+            for (int i = 1; i < 9; ++i) phi = phi + cvt_h(ld_pair(hplane(Lr, i) + j));   // Eq. 18
+        }
+        st_pair(prow(Lr) + j, phi);
+    };
+    // A (synchronous, prologue). Pair q of row Lr: copy the stored values into the
+    // slot, then phi.
+    auto lead_pair = [&](int Lr, int q, int col) {
+        const int c = rowoff(Lr) + col;
+        const int j = 2 + 2 * q;
+        if constexpr (F::cons)
+            *reinterpret_cast<float4*>(&hpairs(Lr)[j]) = *reinterpret_cast<const float4*>(h0in + c);
+#pragma unroll
+        for (int i = F::cons ? 1 : 0; i < 9; ++i) {
+            const HT* src = hin + (long long)(F::cons ? i - 1 : i) * S + c;
+            if constexpr (F::h16) *reinterpret_cast<__half2*>(hplane(Lr, i) + j) = *reinterpret_cast<const __half2*>(src);
+            else *reinterpret_cast<float2*>(hplane(Lr, i) + j) = *reinterpret_cast<const float2*>(src);
+        }
+        phi_from_slot(Lr, j);
+    };
+    auto ghost_row = [&](int Lr) {   // mirror ghost row next to a wall (reading Q7)
+        float* dst = prow(Lr);
+        const float* src = prow(mirror(Lr));
+        if (q0) st_pair(dst + 2 + 2 * tid, lds_pair(src + 2 + 2 * tid));
+        if (q1) st_pair(dst + 2 + 2 * (tid + TX), lds_pair(src + 2 + 2 * (tid + TX)));
+    };
+    auto lead_row = [&](int Lr) {
+        if (ghost(Lr)) { ghost_row(Lr); return; }
+        if (q0) lead_pair(Lr, tid, qc0);
+        if (q1) lead_pair(Lr, tid + TX, qc1);
+    };
+    // Asynchronous copies of this thread's column pairs of lead row Lr and p row M.
+    auto prefetch = [&](int Lr, int M) {
+        auto h_pair = [&](int q, int col) {
+            const int c = rowoff(Lr) + col;
+            const int j = 2 + 2 * q;
+            if constexpr (F::cons) cp_async16(&hpairs(Lr)[j], h0in + c);
+#pragma unroll
+            for (int i = F::cons ? 1 : 0; i < 9; ++i) {
+                const HT* src = hin + (long long)(F::cons ? i - 1 : i) * S + c;
+                if constexpr (F::h16) cp_async4(hplane(Lr, i) + j, src);
+                else cp_async8(hplane(Lr, i) + j, src);
+            }
+        };
+        if (!ghost(Lr)) {
+            if (q0) h_pair(tid, qc0);
+            if (q1) h_pair(tid + TX, qc1);
+        }
+        const float* src = p_in + base + (ghost(M) ? mirror(M) : rowg(M)) * nx;
+        float* dst = qrow(M);
+        if (q0) cp_async8(dst + 2 + 2 * tid, src + qc0);
+        if (q1) cp_async8(dst + 2 + 2 * (tid + TX), src + qc1);
+        cp_async_commit();
+    };
+    // A (asynchronous). phi of row Lr from the pairs this thread copied itself.
+    auto lead_row_async = [&](int Lr) {
+        cp_async_wait_all();
+        if (ghost(Lr)) { ghost_row(Lr); return; }
+        if (q0) phi_from_slot(Lr, 2 + 2 * tid);
+        if (q1) phi_from_slot(Lr, 2 + 2 * (tid + TX));
+    };
+    // p of the previous step, row M (mirror ghost at walls), same column pairs.
+    auto p_row = [&](int M) {
+        const float* src = p_in + base + (ghost(M) ? mirror(M) : rowg(M)) * nx;
+        float* dst = qrow(M);
+        if (q0) st_pair(dst + 2 + 2 * tid, ld_pair(src + qc0));
+        if (q1) st_pair(dst + 2 + 2 * (tid + TX), ld_pair(src + qc1));
+    };
+    // 3x3 neighbourhoods of the pair at ring index j (cells j, j+1) from three rows
+    auto nbr_pair = [&](const float* r0, const float* r1, const float* r2, int j, Nbr<F2>& n) {
+        const float* rows[3] = {r0, r1, r2};
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const float2 a2 = *reinterpret_cast<const float2*>(rows[dy] + j - 2);
+            const float2 b2 = *reinterpret_cast<const float2*>(rows[dy] + j);
+            const float2 c2 = *reinterpret_cast<const float2*>(rows[dy] + j + 2);
+            n.z[dy][0] = F2(a2.y, b2.x);
+            n.z[dy][1] = F2(b2);
+            n.z[dy][2] = F2(b2.y, c2.x);
+        }
+    };
+    // B. mu of row M (Eq. 8 with the Laplacian of Eq. 30b), same column pairs.
+    auto mu_row = [&](int M) {
+        float* dst = mrow(M);
+        if (ghost(M)) {
+            const float* src = mrow(mirror(M));
+            if (q0) st_pair(dst + 2 + 2 * tid, lds_pair(src + 2 + 2 * tid));
+            if (q1) st_pair(dst + 2 + 2 * (tid + TX), lds_pair(src + 2 + 2 * (tid + TX)));
+            return;
+        }
+        const float *r0 = prow(M - 1), *r1 = prow(M), *r2 = prow(M + 1);
+        auto column = [&](int q) {
+            const int j = 2 + 2 * q;
+            Nbr<F2> n;
+            nbr_pair(r0, r1, r2, j, n);
+            st_pair(dst + j, chem_pot(C, n.z[1][1], n.lap()));
+        };
+        if (q0) column(tid);
+        if (q1) column(tid + TX);
+    };
+    // C. collision and push-streaming of the pair in row Y.
+    auto collide_row = [&](int Y, const F2 (&g)[9], F2 pu_x, F2 pu_y) {
+        if (!act) return;
+        const int rY = rowoff(Y);
+        const int c = rY + X;
+        Nbr<F2> nphi, nmu, np;
+        nbr_pair(prow(Y - 1), prow(Y), prow(Y + 1), jX, nphi);
+        nbr_pair(mrow(Y - 1), mrow(Y), mrow(Y + 1), jX, nmu);
+        nbr_pair(qrow(Y - 1), qrow(Y), qrow(Y + 1), jX, np);
+        const F2 phi = nphi.z[1][1], mu = nmu.z[1][1];
+        F2 gphix, gphiy, gmux, gmuy, gpx, gpy;
+        nphi.grad(gphix, gphiy);
+        nmu.grad(gmux, gmuy);
+        np.grad(gpx, gpy);
+        const F2 lapmu = nmu.lap();
+        F2 h[9];
+        F2 lo = F2(0.f);
+        if constexpr (F::cons) {
+            const float4 l4 = *reinterpret_cast<const float4*>(&hpairs(Y)[jX]);
+            lo = F2(l4.y, l4.w);
+            h[0] = lo;
+        }
+#pragma unroll
+        for (int i = F::cons ? 1 : 0; i < 9; ++i) h[i] = cvt_h(ld_pair(hplane(Y, i) + jX));
+
+        const Macro<F2> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
+        const F2 phiux = phi * m.ux, phiuy = phi * m.uy;
+        // Push-streaming as each result is formed (halfway bounce-back into walls;
+        // wall rows uniform per row). Conservative forms: h_0 goes last, as phi
+        // minus the stored h_1..h_8 (per cell, as in step_kernel).
+        const bool bot = walls && Y == 0, top = walls && Y == ny - 1;
+        const int rDn = bot ? 0 : rowoff(Y - 1);
+        const int rUp = top ? 0 : rowoff(Y + 1);
+        float ra = 0.f, rb = 0.f;   // sums of the stored h_1..h_8 of the two cells
+        collide_emit(C, m, phi, mu, phiux - pu_x, phiuy - pu_y, g, h, [&](int i, F2 gi, F2 hi) {
+            if constexpr (F::cons) {
+                if (i == 0) {          // rest direction: g_0 now, h_0 after all h_1..h_8
+                    st_g2(0, c, gi);
+                    return;
+                }
+                if constexpr (F::h16)
+                    hi = F2(__half2float(__float2half_rn(hi.v.x * hs)) * ihs,
+                            __half2float(__float2half_rn(hi.v.y * hs)) * ihs);
+                ra += hi.v.x;
+                rb += hi.v.y;
+            }
+            const int cyi = cy_of(i), cxi = cx_of(i);
+            if ((cyi > 0 && top) || (cyi < 0 && bot)) {   // back into the own pair, reversed
+                const int k = opp_of(i);
+                st_h2(k, c, hi);
+                st_g2(k, c, gi);
+                return;
+            }
+            const int r = cyi == 0 ? rY : (cyi > 0 ? rUp : rDn);
+            if (cxi == 0) {
+                if (!F::cons || i != 0) st_h2(i, r + X, hi);
+                st_g2(i, r + X, gi);
+            } else {
+                const int da = r + (cxi > 0 ? X + 1 : colm);   // destination of cell X
+                const int db = r + (cxi > 0 ? colp : X);       // destination of cell X + 1
+                st_h1(i, da, hi.v.x);
+                st_h1(i, db, hi.v.y);
+                st_g1(i, da, gi.v.x);
+                st_g1(i, db, gi.v.y);
+            }
+        });
+        if constexpr (F::cons) {
+            float s_, e_, hi, l2;
+            float4 h0c;
+            two_sum(phi.v.x, -ra, s_, e_);
+            fast_two_sum(s_, e_ + lo.v.x, hi, l2);
+            h0c.x = hi; h0c.y = l2;
+            two_sum(phi.v.y, -rb, s_, e_);
+            fast_two_sum(s_, e_ + lo.v.y, hi, l2);
+            h0c.z = hi; h0c.w = l2;
+            *reinterpret_cast<float4*>(h0out + c) = h0c;
+        }
+        st_pair(phiu + c, phiux);
+        st_pair(phiu + S + c, phiuy);
+        st_pair(p_out + c, m.p);
+    };
+
+    const int Y0 = wk.ystart;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 1; k >= -2; --k)
+            if (ghost(Y0 + k * d) == (pass == 1)) lead_row(Y0 + k * d);
+    p_row(Y0 - d);
+    p_row(Y0);
+    __syncthreads();
+    // the slot of row Y0 - 2d (read only above) takes the first lead row
+    prefetch(Y0 + 2 * d, Y0 + d);
+    mu_row(Y0);
+    mu_row(Y0 - d);
+    __syncthreads();
+    for (int k = 0; k < wk.nrows; ++k) {
+        const int Y = Y0 + k * d;
+        // g and phi*u of the collision pair, loaded before the barriers
+        F2 g[9];
+        F2 pux = F2(0.f), puy = F2(0.f);
+        if (act) {
+            const int c = rowoff(Y) + X;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = ld_g(i, c);
+            pux = ld_pair(phiu + c);
+            puy = ld_pair(phiu + S + c);
+        }
+        lead_row_async(Y + 2 * d);
+        __syncthreads();
+        // every thread is past the collision of row Y - d: the h slot of row Y - d
+        // and the p slot of row Y - 2d are free for the next iteration's rows
+        if (k + 1 < wk.nrows) prefetch(Y + 3 * d, Y + 2 * d);
+        mu_row(Y + d);
+        __syncthreads();
+        collide_row(Y, g, pux, puy);
+    }
+}
+
+}  // namespace lbm

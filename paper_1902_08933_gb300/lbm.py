@@ -27,6 +27,8 @@ LBM_P_MODIFIED_PRINTED, LBM_P_MODIFIED_LITERAL, LBM_P_PREVIOUS = 0, 1, 2
 LBM_FS_MU_GRADPHI, LBM_FS_PHI_GRADMU = 0, 1
 LBM_VISC_INV_LINEAR, LBM_VISC_STEP = 0, 1
 LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C = 0, 1, 2, 3, 4
+LBM_PIPELINE_AUTO, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC, LBM_PIPELINE_TMA, LBM_PIPELINE_PAIRS = 0, 1, 2, 3, 4
+VARIANTS = {0: "plain", 1: "async", 2: "tma", 3: "pairs"}
 FIELDS = ("phi", "ux", "uy", "p", "rho", "mu", "P")
 FIELD_BITS = {name: 1 << k for k, name in enumerate(FIELDS)}
 FORMS = {"f64": LBM_F64, "f32": LBM_F32, "f32_g16": LBM_F32_G16, "f32_h16": LBM_F32_H16,
@@ -81,6 +83,9 @@ SIGNATURES = [
     ("lbm_save", ctypes.c_int, [_VP, ctypes.c_char_p]),
     ("lbm_load", ctypes.c_int, [_VP, ctypes.c_char_p]),
     ("lbm_set_launch", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("lbm_set_pipeline", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_launch_info", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_launches_per_step", ctypes.c_int, [_VP]),
     ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
@@ -193,6 +198,16 @@ def lbm_load(ctx, path: str):
 
 def lbm_set_launch(ctx, tile_x: int, rows: int):
     _check(library().lbm_set_launch(ctx, int(tile_x), int(rows)), ctx)
+
+
+def lbm_set_pipeline(ctx, mode: int):
+    _check(library().lbm_set_pipeline(ctx, int(mode)), ctx)
+
+
+def lbm_launch_info(ctx, index: int) -> dict:
+    t, b, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(library().lbm_launch_info(ctx, int(index), ctypes.byref(t), ctypes.byref(b), ctypes.byref(m)), ctx)
+    return {"tile_x": t.value, "blocks": b.value, "variant": VARIANTS.get(m.value, m.value)}
 
 
 def lbm_autotune(ctx):

@@ -278,3 +278,59 @@ def test_batched_512_all_finite(L, report):
                 worst = max(worst, abs(d["sum_phi"] - phis[k].sum()) / phis[k].sum())
             report(**{form + "_worst_mass_drift": worst})
             assert worst < tol, (form, worst)
+
+
+PIPES = {"plain": 1, "async": 2, "tma": 3, "pairs": 4}
+
+
+@pytest.mark.parametrize("form", ["f32", "f32_c", "f32_g16", "f32_h16"])
+@pytest.mark.parametrize("tile_x,rows", [(32, 1), (64, 5), (128, 0), (256, 3)])
+def test_load_paths_match(L, orc, form, tile_x, rows, report):
+    # The four load paths (plain loads, per-thread cp.async, TMA bulk copies, two
+    # cells per thread in packed FP32) feed the same arithmetic; ragged last strip (152 = 4 x 32 + 24), walls and
+    # periodic y, both march directions; each run is also checked against the oracle.
+    cfgs = [wl.rising_bubble(nx=152, ny=41, R=9, cy=14, W=4.0, Re=5.0),
+            wl.static_droplet(n=72, R=17)]
+    phis = [noisy(c, 7 + k) for k, c in enumerate(cfgs)]
+    n = 12
+    expect = {"plain": "plain", "async": "plain" if form == "f32_h16" else "async", "tma": "tma",
+              "pairs": "pairs" if tile_x >= 64 else "plain"}
+    got = {}
+    for name, mode in PIPES.items():
+        with L.Simulation(cfgs, form, phi0=phis) as sim:
+            L.lbm_set_launch(sim.ctx, tile_x, rows)
+            L.lbm_set_pipeline(sim.ctx, mode)
+            infos = [L.lbm_launch_info(sim.ctx, i) for i in range(L.lbm_launches_per_step(sim.ctx))]
+            assert all(i["variant"] == expect[name] for i in infos), (name, infos)
+            sim.step(n)
+            got[name] = [(sim.fields(k), sim.populations(k)) for k in range(len(cfgs))]
+    # plain, async and tma run the same compiled arithmetic: they agree to
+    # round-off; pairs (packed FP32, other contraction points) is held to the
+    # FP32 bars against the oracle, like every FP32 run
+    worst = 0.0
+    for k in range(len(cfgs)):
+        fp, (hp, gp) = got["plain"][k]
+        ref, _ = oracle_fields(orc, cfgs[k], phis[k], n)
+        for name in ("async", "tma"):
+            fa, (ha, ga) = got[name][k]
+            for f in ("phi", "ux", "uy", "p"):
+                worst = max(worst, rel(fa[f], fp[f]))
+            worst = max(worst, rel(ha, hp), rel(ga, gp))
+        for name in ("plain", "async", "tma", "pairs"):
+            fa = got[name][k][0]
+            assert rel(fa["phi"], ref["phi"]) < (tol32_phi(n) if form != "f32_h16" else 1e-3), (name, k)
+            up = 2e-2 if form in ("f32", "f32_c") else 0.1
+            assert rel_u(fa, ref) < up and rel(fa["p"], ref["p"]) < up, (name, k)
+    report(load_paths_vs_plain=worst)
+    assert worst < 1e-5
+
+
+def test_bubble_load_paths(L):
+    cfg = wl.rising_bubble()
+    for form, auto, tile in (("f32", "pairs", 256), ("f32_c", "pairs", 256), ("f32_g16", "pairs", 256),
+                             ("f32_h16", "pairs", 256), ("f64", "plain", 128)):
+        with L.Simulation(cfg, form) as sim:
+            info = L.lbm_launch_info(sim.ctx, 0)
+            assert info["variant"] == auto and info["tile_x"] == tile, (form, info)
+            L.lbm_set_pipeline(sim.ctx, L.LBM_PIPELINE_TMA)
+            assert L.lbm_launch_info(sim.ctx, 0)["variant"] == ("plain" if form == "f64" else "tma")
