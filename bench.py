@@ -7,10 +7,11 @@ timed on the host cores.
 
 Workload (headline): rising bubble, 1024 x 4096, bounce-back walls in y,
 periodic x, R = 128 at y = 512, density ratio 10, Eo = 10, Re = 35, W = 5,
-quasi-incompressible model, pressure of Eq. 28; FP32 storage and arithmetic.
-One step = one lattice time step of the whole grid (both population sets).
-The state (2 x 352 MB ping-pong in FP32) is larger than the 129 MB L2, so no
-L2 flush is needed between steps.
+quasi-incompressible model, pressure of Eq. 28; FP32 storage and arithmetic with
+h_0 kept as a two-float pair (form LBM_F32_C: the fastest FP32 form, and the one
+that conserves sum(phi) to round-off). One step = one lattice time step of the
+whole grid (both population sets). The state (2 x 369 MB ping-pong) is larger
+than the 129 MB L2, so no L2 flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="f32", choices=list(BYTES_PER_LUP))
+    ap.add_argument("--form", default="f32_c", choices=list(BYTES_PER_LUP))
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs"],
                     help="load path of the step kernel (lbm_set_pipeline)")
     ap.add_argument("--headline-only", action="store_true",
@@ -128,8 +129,10 @@ class ClockSampler:
 def traffic_record(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source
     has not changed since it was captured (else None)."""
-    src = os.path.join(ROOT, "paper_1902_08933_gb300", "csrc", "lbm_device.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("lbm_device.cuh", "lbm_step_x2.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1902_08933_gb300", "csrc", name), "rb").read())
+    sha = h.hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "step_kernel_bubble_1024x4096.md")
     if not os.path.exists(path):
         return None
