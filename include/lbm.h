@@ -120,6 +120,14 @@ typedef struct lbm_diag {
     int64_t time;                        /* steps taken since lbm_init                  */
 } lbm_diag;
 
+/* Per-step monitor record of one instance (see lbm_set_monitor). */
+typedef struct lbm_monitor {
+    double sum_phi;                      /* sum of phi over the lattice (Eq. 18)        */
+    double kinetic_energy;               /* sum of rho |u|^2 / 2 (u of Eq. 27a)         */
+    double max_u;                        /* max |u|                                     */
+    int64_t time;                        /* time level the sums belong to               */
+} lbm_monitor;
+
 typedef struct lbm_ctx lbm_ctx;
 
 /* Checks one parameter block on the host only (no CUDA call). */
@@ -149,10 +157,32 @@ lbm_status lbm_init_device(lbm_ctx* ctx, int instance, const double* phi0_device
 
 /* Advances every instance by nsteps time steps (one step = collision of h and g
  * with all forcing, then streaming: Eqs. 10 and 24). Asynchronous: returns once
- * the work is queued. Returns an error left by earlier asynchronous work
+ * the work is queued (directly or as CUDA graph replays, see lbm_set_graphs). Returns an error left by earlier asynchronous work
  * (LBM_ECUDA). nsteps >= 0; every instance must have been initialised (else
  * LBM_ESTATE). */
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Per-step monitor (the paper has no counterpart; it watches the conservation
+ * of sum(phi) that Eq. 18 and the streaming of Eq. 10 imply, and the flow's
+ * energy, without a separate pass over the state). When enabled, the last time
+ * step of every lbm_step call runs step kernels that also reduce, over the
+ * cells they collide, sum(phi), the kinetic energy sum(rho |u|^2 / 2) and
+ * max |u| of the fields at that step's input time level (the fields
+ * lbm_get_fields returns at that time), plus one small kernel that combines the
+ * per-block values of each instance in a fixed order; the other steps run the
+ * plain kernels. FP64 forms sum in FP64; FP32-arithmetic forms sum phi in a
+ * float-float pair per thread (about 48 bits) and the energy in FP32 per thread,
+ * then in FP64. Allocates the per-instance record on the first enable.
+ * Errors: LBM_EINVAL (NULL context), LBM_ENOMEM/LBM_ECUDA (allocation). */
+lbm_status lbm_set_monitor(lbm_ctx* ctx, int enable);
+
+/* Reads (synchronises the stream) the monitor record of one instance written by
+ * the last monitored step; out->time is that step's input time level, i.e.
+ * lbm_time() - 1 right after the lbm_step call. Errors: LBM_EINVAL (bad
+ * instance or NULL out), LBM_ESTATE (no monitored step since lbm_create,
+ * lbm_init of the instance or lbm_load), LBM_ETIMEOUT / LBM_ECUDA (as
+ * lbm_sync), LBM_ENONFINITE (phi or u not finite somewhere; *out is filled). */
+lbm_status lbm_read_monitor(lbm_ctx* ctx, int instance, lbm_monitor* out);
 
 /* Macroscopic fields of one instance at the current time, computed from the
  * current populations exactly as the next step's macroscopic stage would
@@ -177,7 +207,9 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, int instance, double* host_h, doubl
 /* Checkpoint: writes / reads the complete state (populations, stored phi*u and
  * p of the previous step, time, parameters) as a little-endian binary file
  * with a header. lbm_load requires a context created with the same parameters
- * and precision. Errors: LBM_EIO, LBM_EINVAL. */
+ * and precision; a successful lbm_load also clears a recorded device-wait
+ * timeout (the state it flagged has been replaced). Errors: LBM_EIO,
+ * LBM_EINVAL. */
 lbm_status lbm_save(lbm_ctx* ctx, const char* path);
 lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
@@ -210,6 +242,14 @@ enum {
     LBM_PIPELINE_PAIRS = 4
 };
 lbm_status lbm_set_pipeline(lbm_ctx* ctx, int mode);
+
+/* CUDA graphs: when enabled (the default) and the context's stream can be
+ * captured, lbm_step replays a captured graph of a fixed even number of steps
+ * (about 64 kernel launches) and launches the remainder directly; results are
+ * identical either way. enable = 0 launches every step directly. Streams that
+ * are being captured by the caller, and the legacy default stream, always get
+ * direct launches (so lbm_step can itself be captured into a caller's graph). */
+lbm_status lbm_set_graphs(lbm_ctx* ctx, int enable);
 
 /* Launch index (0 .. lbm_launches_per_step - 1) of one step: strip width,
  * number of thread blocks, and the load path it uses (0 plain, 1 cp.async,
@@ -253,10 +293,23 @@ int64_t lbm_time(const lbm_ctx* ctx, int instance);
 lbm_status lbm_reduce_fields_noalloc(const double* fields_device, int nx, int ny,
                                      void* cuda_stream, double* out_device);
 
+/* Failure-detection check (the paper has no counterpart; this is library
+ * infrastructure). Queues on the context's stream one single-thread kernel that
+ * arms a transaction mbarrier for 16 bytes no copy will deliver and waits on it
+ * with the same bounded wait the step kernels use, giving up after `rounds`
+ * try_wait rounds (1 <= rounds <= 2^21, the step kernels' own limit). The wait
+ * runs out by construction, so the kernel records a timeout in the context's
+ * status word exactly as a step kernel would and returns: nothing faults or
+ * hangs, and the CUDA context stays usable. Afterwards lbm_sync,
+ * lbm_get_fields and lbm_diagnostics return LBM_ETIMEOUT until lbm_load
+ * restores a checkpoint. Asynchronous. Errors: LBM_EINVAL (NULL context,
+ * rounds out of range), LBM_ECUDA (launch failed). */
+lbm_status lbm_inject_wait_timeout(lbm_ctx* ctx, int rounds);
+
 /* Waits for all queued work. Returns LBM_ECUDA if it failed, LBM_ETIMEOUT if a
  * bounded device wait of the step kernel ran out (the state is then suspect;
- * the status stays set for the life of the context). lbm_get_fields and
- * lbm_diagnostics report the same status. */
+ * the status stays set until lbm_load replaces the whole state). lbm_get_fields
+ * and lbm_diagnostics report the same status. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 /* Last error message of the context ("" if none); valid until the next call. */

@@ -9,6 +9,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_mbar.cuh"
 
 using lbm::AuxArgs;
 using lbm::DevInst;
@@ -143,6 +144,18 @@ struct lbm_ctx {
     std::vector<WorkItem> work;
     WorkItem* d_work = nullptr;
     bool plan_dirty = true;
+    // CUDA graph of 2 * graph_pairs steps starting from cur == 0 (built on first use,
+    // dropped when the plan changes)
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    // per-step monitor of the last step of each lbm_step call
+    bool monitor = false;
+    double* d_mon_partials = nullptr;   // kMonQ doubles per work item
+    int* d_mon_csr = nullptr;           // per instance: work items [ptr[k], ptr[k+1]) of idx
+    double* d_mon = nullptr;            // kMonQ doubles per instance
+    double* h_mon = nullptr;            // pinned: kMonQ doubles + the status word
+    std::vector<int64_t> mon_time;      // time level of the recorded sums (-1: none)
+    bool use_graphs = true;
     double* d_tmp = nullptr;       // 2 * max_cells
     double* d_out = nullptr;       // field staging, grown on demand
     size_t d_out_cells = 0;
@@ -184,6 +197,7 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.inst = c->d_inst;
     a.work = nullptr;
     a.status = c->d_status;
+    a.mon = nullptr;
     return a;
 }
 
@@ -262,6 +276,26 @@ lbm_status plan(lbm_ctx* c) {
         f_tma = lbm::has_tma_t<decltype(F)::value>();
         return cudaSuccess;
     });
+    // Several instances: one run length for all, sized so the blocks fill about two
+    // waves of the GPU (at least 4 rows a block: each run re-reads 4 halo rows).
+    int batch_rows = 32;
+    if (c->n > 1) {
+        long long strip_rows = 0;
+        int occ_min = 1 << 30;
+        for (int k = 0; k < c->n; ++k) {
+            int tx = 0, variant = 0;
+            choose(c, c->params[k], f_pairs, f_async, f_tma, &tx, &variant);
+            strip_rows += (long long)((c->params[k].nx + tx - 1) / tx) * c->params[k].ny;
+            int occ = 0;
+            by_form(c->form, [&](auto F) {
+                occ = lbm::step_occupancy_t<decltype(F)::value>(tx, variant);
+                return cudaSuccess;
+            });
+            occ_min = std::min(occ_min, std::max(occ, 1));
+        }
+        const long long target = 2LL * sms * occ_min;
+        batch_rows = (int)std::max<long long>(4, std::min<long long>(64, strip_rows / target));
+    }
     for (int k = 0; k < c->n; ++k) {
         const lbm_params& p = c->params[k];
         int tx = 0, variant = 0;
@@ -280,7 +314,7 @@ lbm_status plan(lbm_ctx* c) {
                 const long long chunks = std::max<long long>(1, (target + strips - 1) / strips);
                 rows = (int)std::max<long long>(8, (p.ny + chunks - 1) / chunks);
             } else {
-                rows = 32;
+                rows = batch_rows;
             }
         }
         rows = std::min(rows, p.ny);
@@ -306,11 +340,31 @@ lbm_status plan(lbm_ctx* c) {
         c->launches.push_back({tiles[k / 4], (int)c->work.size(), (int)by_class[k].size(), k % 4});
         c->work.insert(c->work.end(), by_class[k].begin(), by_class[k].end());
     }
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_steps = 0;
+    }
     if (c->d_work) cudaFree(c->d_work);
     c->d_work = nullptr;
     LBM_CK(c, cudaMalloc(&c->d_work, c->work.size() * sizeof(WorkItem)));
     LBM_CK(c, cudaMemcpy(c->d_work, c->work.data(), c->work.size() * sizeof(WorkItem),
                          cudaMemcpyHostToDevice));
+    // monitor: per-block slots and, per instance, the list of its work items
+    std::vector<int> csr(c->n + 1 + c->work.size(), 0);
+    for (const WorkItem& w : c->work) ++csr[w.inst + 1];
+    for (int k = 0; k < c->n; ++k) csr[k + 1] += csr[k];
+    {
+        std::vector<int> fill(csr.begin(), csr.begin() + c->n);
+        for (size_t j = 0; j < c->work.size(); ++j) csr[c->n + 1 + fill[c->work[j].inst]++] = (int)j;
+    }
+    cudaFree(c->d_mon_partials);
+    cudaFree(c->d_mon_csr);
+    c->d_mon_partials = nullptr;
+    c->d_mon_csr = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_mon_partials, c->work.size() * lbm::kMonQ * sizeof(double)));
+    LBM_CK(c, cudaMalloc(&c->d_mon_csr, csr.size() * sizeof(int)));
+    LBM_CK(c, cudaMemcpy(c->d_mon_csr, csr.data(), csr.size() * sizeof(int), cudaMemcpyHostToDevice));
     c->plan_dirty = false;
     return LBM_OK;
 }
@@ -365,7 +419,12 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_status);
+    cudaFree(c->d_mon_partials);
+    cudaFree(c->d_mon_csr);
+    cudaFree(c->d_mon);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->h_result) cudaFreeHost(c->h_result);
+    if (c->h_mon) cudaFreeHost(c->h_mon);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -405,6 +464,7 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     c->form = precision;
     c->params.assign(params, params + n_instances);
     c->time.assign(n_instances, 0);
+    c->mon_time.assign(n_instances, -1);
     c->ready.assign(n_instances, 0);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
@@ -472,6 +532,7 @@ static lbm_status init_common(lbm_ctx* c, int instance, const double* phi0_dev) 
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->time[instance] = 0;
+    c->mon_time[instance] = -1;
     c->ready[instance] = 1;
     return LBM_OK;
 }
@@ -499,6 +560,83 @@ lbm_status lbm_init_device(lbm_ctx* c, int instance, const double* phi0_device) 
     return init_common(c, instance, phi0_device);
 }
 
+namespace {
+// Queues one step (every launch class) reading the buffers of parity `in`.
+// One warp per instance adds the monitor slots of its work items in work-list
+// order (fixed, so the sums do not depend on timing); max |u|^2 -> max |u|.
+__global__ void monitor_final(const double* __restrict__ partials, const int* __restrict__ csr, int n,
+                              double* __restrict__ out) {
+    const int k = blockIdx.x, q = threadIdx.x;
+    if (q >= lbm::kMonQ) return;
+    const int* idx = csr + n + 1;
+    double v = 0.0;
+    for (int j = csr[k]; j < csr[k + 1]; ++j) {
+        const double x = partials[(long long)idx[j] * lbm::kMonQ + q];
+        v = q == 2 ? fmax(v, x) : v + x;
+    }
+    out[k * lbm::kMonQ + q] = q == 2 ? sqrt(v) : v;
+}
+
+// Queues one time step (all launches of the plan) reading buffer set `in`; with
+// `monitor` the step kernels also write their monitor slots, reduced per instance.
+cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false) {
+    StepArgs a = step_args(c, in);
+    for (const auto& L : c->launches) {
+        a.work = c->d_work + L.offset;
+        a.mon = monitor ? c->d_mon_partials + (long long)L.offset * lbm::kMonQ : nullptr;
+        cudaError_t e = by_form(c->form, [&](auto F) {
+            return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream, L.variant, monitor);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    if (monitor) {
+        monitor_final<<<c->n, 32, 0, c->stream>>>(c->d_mon_partials, c->d_mon_csr, c->n, c->d_mon);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+// Captures an even number of steps (starting from parity 0) into a CUDA graph, so
+// that long runs of small grids are not bound by launch overhead. Returns false
+// (and the caller launches directly) if the stream cannot be captured: the legacy
+// default stream, or a stream the caller is capturing itself.
+bool build_graph(lbm_ctx* c) {
+    if (c->graph) return true;
+    if (!c->use_graphs || c->stream == nullptr || c->stream == cudaStreamLegacy) return false;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return false;
+    // about 64 launches a graph
+    const int per_step = std::max<int>(1, (int)c->launches.size());
+    const int steps = 2 * std::max(1, 32 / per_step);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < steps && e == cudaSuccess; ++t) e = enqueue_step(c, t & 1);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->use_graphs = false;
+        return false;
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->use_graphs = false;
+        return false;
+    }
+    c->graph = x;
+    c->graph_steps = steps;
+    return true;
+}
+}  // namespace
+
 lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (!c) return LBM_EINVAL;
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
@@ -508,18 +646,85 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     lbm_status st = sticky(c);
     if (st != LBM_OK) return st;
     if (c->plan_dirty && (st = plan(c)) != LBM_OK) return st;
-    for (int t = 0; t < nsteps; ++t) {
-        StepArgs a = step_args(c, c->cur);
-        for (const auto& L : c->launches) {
-            a.work = c->d_work + L.offset;
-            cudaError_t e = by_form(c->form, [&](auto F) {
-                return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream, L.variant);
-            });
+    // with the monitor on, the last step runs the monitored kernels
+    const bool mon_last = c->monitor && nsteps > 0;
+    int left = mon_last ? nsteps - 1 : nsteps;
+    // graph replays cover whole multiples of the captured steps from parity 0
+    if (left >= 2 && c->use_graphs) {
+        if (c->cur == 1) {
+            cudaError_t e = enqueue_step(c, 1);
             if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+            c->cur = 0;
+            --left;
         }
+        if (left >= 2 && build_graph(c)) {
+            while (left >= c->graph_steps) {
+                cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+                if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+                left -= c->graph_steps;   // even: parity unchanged
+            }
+        }
+    }
+    for (; left > 0; --left) {
+        cudaError_t e = enqueue_step(c, c->cur);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
         c->cur ^= 1;
     }
-    for (int k = 0; k < c->n; ++k) c->time[k] += nsteps;
+    if (mon_last) {
+        cudaError_t e = enqueue_step(c, c->cur, true);
+        if (e != cudaSuccess) return cuda_fail(c, e, "monitored step launch");
+        c->cur ^= 1;
+    }
+    for (int k = 0; k < c->n; ++k) {
+        c->time[k] += nsteps;
+        if (mon_last) c->mon_time[k] = c->time[k] - 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_monitor(lbm_ctx* c, int enable) {
+    if (!c) return LBM_EINVAL;
+    LBM_CK(c, cudaSetDevice(c->device));
+    if (enable && !c->d_mon) {
+        LBM_CK(c, cudaMalloc(&c->d_mon, (size_t)c->n * lbm::kMonQ * sizeof(double)));
+        LBM_CK(c, cudaMallocHost(&c->h_mon, (lbm::kMonQ + 1) * sizeof(double)));
+    }
+    c->monitor = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_read_monitor(lbm_ctx* c, int instance, lbm_monitor* out) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!out) return fail(c, LBM_EINVAL, "out is NULL");
+    if (!c->d_mon || c->mon_time[instance] < 0)
+        return fail(c, LBM_ESTATE, "no monitored step yet (lbm_set_monitor, then lbm_step)");
+    LBM_CK(c, cudaSetDevice(c->device));
+    if ((st = sticky(c)) != LBM_OK) return st;
+    double* h = c->h_mon;
+    LBM_CK(c, cudaMemcpyAsync(h, c->d_mon + (size_t)instance * lbm::kMonQ, lbm::kMonQ * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaMemcpyAsync(h + lbm::kMonQ, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    int status = 0;
+    std::memcpy(&status, h + lbm::kMonQ, sizeof(int));
+    if (status != 0) return device_status(c);
+    out->sum_phi = h[0];
+    out->kinetic_energy = h[1];
+    out->max_u = h[2];
+    out->time = c->mon_time[instance];
+    if (h[3] != 0.0) return fail(c, LBM_ENONFINITE, "non-finite phi or velocity in the monitored step");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_graphs(lbm_ctx* c, int enable) {
+    if (!c) return LBM_EINVAL;
+    c->use_graphs = enable != 0;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_steps = 0;
+    }
     return LBM_OK;
 }
 
@@ -720,7 +925,10 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     }
     std::fclose(f);
     c->time = ts;
+    c->mon_time.assign(c->n, -1);
     c->ready.assign(c->n, 1);
+    // the whole state was replaced: a timeout recorded before no longer applies
+    LBM_CK(c, cudaMemset(c->d_status, 0, sizeof(int)));
     return LBM_OK;
 }
 
@@ -820,6 +1028,33 @@ int lbm_launches_per_step(const lbm_ctx* c) {
 int64_t lbm_time(const lbm_ctx* c, int instance) {
     if (!c || instance < 0 || instance >= c->n) return -1;
     return c->time[instance];
+}
+
+namespace {
+
+// One thread arms an mbarrier for 16 bytes that no copy will ever deliver and
+// waits on it with the step kernel's bounded wait; when the wait gives up it
+// records the timeout in the status word, as the step kernel does.
+__global__ void wait_timeout_kernel(int rounds, int* status) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = lbm::smem_u32(&bar);
+    lbm::mbar_init(b, 1);
+    lbm::fence_mbar_init();
+    lbm::mbar_expect_tx(b, 16);
+    if (!lbm::mbar_wait(b, 0, rounds)) atomicExch(status, lbm::kStatusTimeout);
+}
+
+}  // namespace
+
+lbm_status lbm_inject_wait_timeout(lbm_ctx* c, int rounds) {
+    if (!c) return LBM_EINVAL;
+    if (rounds < 1 || rounds > lbm::kWaitLimit)
+        return fail(c, LBM_EINVAL, "rounds must be in 1 .. 2^21");
+    LBM_CK(c, cudaSetDevice(c->device));
+    wait_timeout_kernel<<<1, 32, 0, c->stream>>>(rounds, c->d_status);
+    LBM_CK(c, cudaGetLastError());
+    return LBM_OK;
 }
 
 lbm_status lbm_sync(lbm_ctx* c) {

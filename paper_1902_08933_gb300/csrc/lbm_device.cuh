@@ -435,6 +435,70 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
+// Per-step monitor (optional, a template switch of the step kernels): mass
+// sum(phi), kinetic energy sum(rho |u|^2 / 2) and max |u| of the cells each block
+// collides, at the time level of the step's input. FP32 forms add phi in a
+// float-float pair (TwoSum), so the block sum keeps about 48 bits -- sum(phi)
+// stays exact enough to watch its conservation -- at a few FP32 operations a
+// cell; the block's result is combined in FP64 and written to its own slot of
+// StepArgs::mon (kMonQ doubles), with no atomics, so the sums do not depend on
+// timing.
+template <typename R> struct MonAcc;
+template <> struct MonAcc<double> {
+    double m = 0.0, ke = 0.0, u2 = 0.0;
+    __device__ __forceinline__ void add(double phi, double lo, double rho, double ux, double uy) {
+        m += phi + lo;
+        const double uu = ux * ux + uy * uy;
+        ke += 0.5 * rho * uu;
+        u2 = fmax(u2, uu);
+    }
+    __device__ __forceinline__ void result(double& mass, double& kin, double& umax2) const {
+        mass = m; kin = ke; umax2 = u2;
+    }
+};
+template <> struct MonAcc<float> {
+    float mh = 0.f, ml = 0.f, ke = 0.f, u2 = 0.f;
+    __device__ __forceinline__ void add(float phi, float lo, float rho, float ux, float uy) {
+        float sm, e;
+        two_sum(mh, phi, sm, e);
+        mh = sm;
+        ml += e + lo;
+        const float uu = ux * ux + uy * uy;
+        ke += 0.5f * rho * uu;
+        u2 = fmaxf(u2, uu);
+    }
+    __device__ __forceinline__ void result(double& mass, double& kin, double& umax2) const {
+        mass = double(mh) + double(ml); kin = double(ke); umax2 = double(u2);
+    }
+};
+
+// Block reduction of the monitor sums; thread 0 writes {sum phi, kinetic
+// energy, max |u|^2, non-finite flag} to out. Every thread of the block calls it.
+template <typename R>
+__device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, double* out) {
+    __shared__ double red[3][32];
+    double v[3];
+    acc.result(v[0], v[1], v[2]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+        v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+        v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+    }
+    if (lane == 0) { red[0][warp] = v[0]; red[1][warp] = v[1]; red[2][warp] = v[2]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = red[0][0], k = red[1][0], u = red[2][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { m += red[0][w]; k += red[1][w]; u = fmax(u, red[2][w]); }
+        out[0] = m;
+        out[1] = k;
+        out[2] = u;
+        out[3] = (isfinite(m) && isfinite(k)) ? 0.0 : 1.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The fused step kernel. Rings in shared memory (slots by row number, powers of
 // two so a slot is one AND):
 //   phi   [8][TX+4]      rows Y-2 .. Y+2 (and the lead row being written)
@@ -472,7 +536,7 @@ struct StepOcc {
 template <int FORM>
 constexpr bool kAsyncOk = sizeof(typename Form<FORM>::R) == 4 && !Form<FORM>::h16;
 
-template <int FORM, int TX, bool ASYNC>
+template <int FORM, int TX, bool ASYNC, bool MON = false>
 __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(const StepArgs a) {
     using F = Form<FORM>;
     using R = typename F::R;
@@ -507,6 +571,7 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
     const AT* p_in = static_cast<const AT*>(a.p_in);
     AT* p_out = static_cast<AT*>(a.p_out);
     AT* phiu = static_cast<AT*>(a.phiu);
+    MonAcc<R> mon;
 
     auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
     auto rowg = [ny, walls](int y) { return walls ? y : (y < 0 ? y + ny : (y >= ny ? y - ny : y)); };
@@ -678,6 +743,7 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
 
         const Macro<R> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
         const R phiux = phi * m.ux, phiuy = phi * m.uy;
+        if constexpr (MON) mon.add(phi, F::cons ? h[0] : R(0), m.rho, m.ux, m.uy);
         R gpost[9], hpost[9];
         collide_cell(C, m, phi, mu, phiux - pux, phiuy - puy, g, h, gpost, hpost);
 
@@ -766,6 +832,7 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
         __syncthreads();
         collide_row(Y, g, pux, puy);
     }
+    if constexpr (MON) mon_block_store(mon, a.mon + (long long)blockIdx.x * kMonQ);
 }
 
 // ---------------------------------------------------------------------------

@@ -46,7 +46,12 @@ struct StepArgs {
     const DevInst* inst;
     const WorkItem* work;
     int* status;                        // device status word (0 = ok), see kStatusTimeout
+    double* mon;                        // monitor: kMonQ doubles per block of this launch
 };
+
+// Doubles a block of a monitored step writes: sum phi, kinetic energy,
+// max |u|^2, non-finite flag.
+constexpr int kMonQ = 4;
 
 // Value a kernel writes to the status word when a bounded device wait runs out
 // (equal to LBM_ETIMEOUT of include/lbm.h).
@@ -75,7 +80,7 @@ constexpr int kDiagBlocks = 304;      // 2 x 152 SMs
 // two cells per thread in packed FP32 (FP32 arithmetic, nx even, tile >= 64).
 enum StepVariant { kPlain = 0, kAsync = 1, kTma = 2, kPairs = 3 };
 template <int FORM> cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s,
-                                              int variant);
+                                              int variant, bool monitor);
 template <int FORM> cudaError_t prepare_step_t();          // opt-in shared memory sizes
 template <int FORM> size_t step_smem_t(int tile_x);
 template <int FORM> int step_occupancy_t(int tile_x, int variant);   // resident blocks per SM

@@ -22,15 +22,21 @@ bool has_pairs_t() { return kHasTma<FORM>; }   // the FP32-arithmetic forms
 
 // paired kernel: tile_x columns per block, tile_x / 2 threads
 template <int FORM, int TX>
-static cudaError_t launch_pairs_tx(const StepArgs& a, int nwork, cudaStream_t s) {
-    step_kernel_x2<FORM, TX><<<nwork, TX, X2Smem<FORM, TX>::bytes, s>>>(a);
+static cudaError_t launch_pairs_tx(const StepArgs& a, int nwork, cudaStream_t s, bool monitor) {
+    if (monitor) step_kernel_x2<FORM, TX, true><<<nwork, TX, X2Smem<FORM, TX>::bytes, s>>>(a);
+    else step_kernel_x2<FORM, TX><<<nwork, TX, X2Smem<FORM, TX>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 // variant: kPlain (synchronous loads), kAsync (per-thread cp.async prefetch),
-// kTma (bulk copies); the caller only asks for a variant the form has.
+// kTma (bulk copies); the caller only asks for a variant the form has. A
+// monitored step always runs the synchronous-load kernel with the monitor.
 template <int FORM, int TX>
-static cudaError_t launch_step_tx(const StepArgs& a, int nwork, cudaStream_t s, int variant) {
+static cudaError_t launch_step_tx(const StepArgs& a, int nwork, cudaStream_t s, int variant, bool monitor) {
+    if (monitor) {
+        step_kernel<FORM, TX, false, true><<<nwork, TX, StepSmem<FORM, TX>::bytes, s>>>(a);
+        return cudaGetLastError();
+    }
     if constexpr (kHasTma<FORM>) {
         if (variant == kTma) {
             step_kernel_tma<FORM, TX><<<nwork, TX, TmaSmem<FORM, TX>::bytes, s>>>(a);
@@ -48,23 +54,25 @@ static cudaError_t launch_step_tx(const StepArgs& a, int nwork, cudaStream_t s, 
 }
 
 template <int FORM>
-cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s, int variant) {
+cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s, int variant,
+                          bool monitor) {
     if (nwork <= 0) return cudaSuccess;
+    if (monitor && a.mon == nullptr) return cudaErrorInvalidValue;
     if constexpr (kHasTma<FORM>) {
         if (variant == kPairs) {
             switch (tile_x) {
-                case 64: return launch_pairs_tx<FORM, 32>(a, nwork, s);
-                case 128: return launch_pairs_tx<FORM, 64>(a, nwork, s);
-                case 256: return launch_pairs_tx<FORM, 128>(a, nwork, s);
+                case 64: return launch_pairs_tx<FORM, 32>(a, nwork, s, monitor);
+                case 128: return launch_pairs_tx<FORM, 64>(a, nwork, s, monitor);
+                case 256: return launch_pairs_tx<FORM, 128>(a, nwork, s, monitor);
                 default: return cudaErrorInvalidValue;
             }
         }
     }
     switch (tile_x) {
-        case 32: return launch_step_tx<FORM, 32>(a, nwork, s, variant);
-        case 64: return launch_step_tx<FORM, 64>(a, nwork, s, variant);
-        case 128: return launch_step_tx<FORM, 128>(a, nwork, s, variant);
-        case 256: return launch_step_tx<FORM, 256>(a, nwork, s, variant);
+        case 32: return launch_step_tx<FORM, 32>(a, nwork, s, variant, monitor);
+        case 64: return launch_step_tx<FORM, 64>(a, nwork, s, variant, monitor);
+        case 128: return launch_step_tx<FORM, 128>(a, nwork, s, variant, monitor);
+        case 256: return launch_step_tx<FORM, 256>(a, nwork, s, variant, monitor);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -74,6 +82,9 @@ static cudaError_t prep_tx() {
     cudaError_t e = cudaFuncSetAttribute(step_kernel<FORM, TX, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)StepSmem<FORM, TX>::bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_kernel<FORM, TX, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)StepSmem<FORM, TX>::bytes);
     if constexpr (kAsyncOk<FORM>) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(step_kernel<FORM, TX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -83,9 +94,14 @@ static cudaError_t prep_tx() {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(step_kernel_tma<FORM, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)TmaSmem<FORM, TX>::bytes);
-        if (e == cudaSuccess && TX >= 32 && TX <= 128)
-            e = cudaFuncSetAttribute(step_kernel_x2<FORM, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)X2Smem<FORM, TX>::bytes);
+        if constexpr (TX >= 32 && TX <= 128) {   // paired kernel: 64..256 columns
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(step_kernel_x2<FORM, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)X2Smem<FORM, TX>::bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(step_kernel_x2<FORM, TX, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X2Smem<FORM, TX>::bytes);
+        }
     }
     return e;
 }
@@ -193,7 +209,7 @@ cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h, do
 }
 
 #define LBM_INSTANTIATE_FORM(F)                                                               \
-    template cudaError_t launch_step_t<F>(int, const StepArgs&, int, cudaStream_t, int);      \
+    template cudaError_t launch_step_t<F>(int, const StepArgs&, int, cudaStream_t, int, bool); \
     template cudaError_t prepare_step_t<F>();                                                 \
     template size_t step_smem_t<F>(int);                                                      \
     template int step_occupancy_t<F>(int, int);                                               \

@@ -57,7 +57,7 @@ struct X2Occ {   // register budget: 128 registers a thread
     static constexpr int value = (512 / TX) > 0 ? 512 / TX : 1;
 };
 
-template <int FORM, int TX>
+template <int FORM, int TX, bool MON = false>
 __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(const StepArgs a) {
     using F = Form<FORM>;
     using HT = typename F::HT;
@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
     float* p_out = static_cast<float*>(a.p_out);
     float* phiu = static_cast<float*>(a.phiu);
     const float hs = C.hs, ihs = C.ihs, gs = C.gs, igs = C.igs;
+    MonAcc<float> mon;
 
     auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
     auto rowg = [ny, walls](int y) { return walls ? y : (y < 0 ? y + ny : (y >= ny ? y - ny : y)); };
@@ -283,6 +284,10 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
 
         const Macro<F2> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
         const F2 phiux = phi * m.ux, phiuy = phi * m.uy;
+        if constexpr (MON) {
+            mon.add(phi.v.x, lo.v.x, m.rho.v.x, m.ux.v.x, m.uy.v.x);
+            mon.add(phi.v.y, lo.v.y, m.rho.v.y, m.ux.v.y, m.uy.v.y);
+        }
         // Push-streaming as each result is formed (halfway bounce-back into walls;
         // wall rows uniform per row). Conservative forms: h_0 goes last, as phi
         // minus the stored h_1..h_8 (per cell, as in step_kernel).
@@ -371,6 +376,7 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
         __syncthreads();
         collide_row(Y, g, pux, puy);
     }
+    if constexpr (MON) mon_block_store(mon, a.mon + (long long)blockIdx.x * kMonQ);
 }
 
 }  // namespace lbm

@@ -63,6 +63,11 @@ class lbm_diag(ctypes.Structure):
                                      ("time", ctypes.c_int64)]
 
 
+class lbm_monitor(ctypes.Structure):
+    _fields_ = [("sum_phi", ctypes.c_double), ("kinetic_energy", ctypes.c_double),
+                ("max_u", ctypes.c_double), ("time", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 _VP = ctypes.c_void_p
@@ -76,6 +81,8 @@ SIGNATURES = [
     ("lbm_init", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     ("lbm_init_device", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_set_monitor", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_read_monitor", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_monitor)]),
     ("lbm_get_fields", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _DP]),
     ("lbm_get_fields_device", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _VP]),
     ("lbm_diagnostics", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_diag)]),
@@ -84,12 +91,14 @@ SIGNATURES = [
     ("lbm_load", ctypes.c_int, [_VP, ctypes.c_char_p]),
     ("lbm_set_launch", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("lbm_set_pipeline", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_set_graphs", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_launch_info", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_launches_per_step", ctypes.c_int, [_VP]),
     ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
     ("lbm_reduce_fields_noalloc", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    ("lbm_inject_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_sync", ctypes.c_int, [_VP]),
     ("lbm_last_error", ctypes.c_char_p, [_VP]),
     ("lbm_destroy", None, [_VP]),
@@ -162,6 +171,20 @@ def lbm_step(ctx, nsteps: int):
     _check(library().lbm_step(ctx, int(nsteps)), ctx)
 
 
+def lbm_set_monitor(ctx, enable: bool):
+    _check(library().lbm_set_monitor(ctx, 1 if enable else 0), ctx)
+
+
+def lbm_read_monitor(ctx, instance: int) -> dict:
+    """Monitor record of the last monitored step; 'status' is LBM_OK or LBM_ENONFINITE."""
+    m = lbm_monitor()
+    st = library().lbm_read_monitor(ctx, int(instance), ctypes.byref(m))
+    if st not in (LBM_OK, LBM_ENONFINITE):
+        _check(st, ctx)
+    return {"sum_phi": m.sum_phi, "kinetic_energy": m.kinetic_energy, "max_u": m.max_u,
+            "time": m.time, "status": st}
+
+
 def lbm_get_fields(ctx, instance, mask: int, out: np.ndarray):
     assert out.dtype == np.float64 and out.flags.c_contiguous
     _check(library().lbm_get_fields(ctx, instance, mask, out.ctypes.data_as(_DP)), ctx)
@@ -204,6 +227,10 @@ def lbm_set_pipeline(ctx, mode: int):
     _check(library().lbm_set_pipeline(ctx, int(mode)), ctx)
 
 
+def lbm_set_graphs(ctx, enable: bool):
+    _check(library().lbm_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
 def lbm_launch_info(ctx, index: int) -> dict:
     t, b, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(library().lbm_launch_info(ctx, int(index), ctypes.byref(t), ctypes.byref(b), ctypes.byref(m)), ctx)
@@ -228,6 +255,10 @@ def lbm_reduce_fields_noalloc(fields_dev_ptr: int, nx: int, ny: int, stream, out
     """Returns the status code (allocation-free FP64 reduction of caller fields)."""
     return library().lbm_reduce_fields_noalloc(_VP(fields_dev_ptr), int(nx), int(ny),
                                                _VP(stream or 0), _VP(out_dev_ptr))
+
+
+def lbm_inject_wait_timeout(ctx, rounds: int):
+    _check(library().lbm_inject_wait_timeout(ctx, int(rounds)), ctx)
 
 
 def lbm_sync(ctx):

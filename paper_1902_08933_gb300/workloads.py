@@ -107,8 +107,10 @@ def layered_poiseuille(nx: int = 8, ny: int = 256, rho_ratio: float = 1.0,
                        tau_min: float = 0.6, qim: int = 1, sigma: float = 0.001,
                        M: float = 0.1, tau_h: float = 1.0) -> dict:
     """Phase A (phi = 1) in the lower half, B above, walls in y. mu_ratio is the
-    dynamic ratio mu_A / mu_B; the less viscous fluid (kinematic) gets tau_min."""
+    dynamic ratio mu_A / mu_B; the less viscous fluid (kinematic) gets tau_min.
+    M is capped by stable_mobility (unchanged for rho_ratio <= 3)."""
     rho_A, rho_B = rho_ratio, 1.0
+    M = stable_mobility(M, rho_A, rho_B)
     # mu_A = mu_ratio * mu_B; nu = mu / rho
     nuA_over_nuB = mu_ratio * rho_B / rho_A
     nu_min = _nu_from_tau(tau_min)
