@@ -276,8 +276,11 @@ lbm_status plan(lbm_ctx* c) {
         f_tma = lbm::has_tma_t<decltype(F)::value>();
         return cudaSuccess;
     });
-    // Several instances: one run length for all, sized so the blocks fill about two
-    // waves of the GPU (at least 4 rows a block: each run re-reads 4 halo rows).
+    // Several instances: one run length for all, sized for about eight waves of
+    // blocks (blocks of different instances differ in width and length, so one
+    // exact wave cannot be had; many short runs balance, at the price of the 4
+    // halo rows each run re-reads, mostly from L2). Tiny batches get 1-row runs:
+    // there the step is bound by the latency of a block's row march.
     int batch_rows = 32;
     if (c->n > 1) {
         long long strip_rows = 0;
@@ -293,8 +296,8 @@ lbm_status plan(lbm_ctx* c) {
             });
             occ_min = std::min(occ_min, std::max(occ, 1));
         }
-        const long long target = 2LL * sms * occ_min;
-        batch_rows = (int)std::max<long long>(4, std::min<long long>(64, strip_rows / target));
+        const long long target = 8LL * sms * occ_min;
+        batch_rows = (int)std::max<long long>(1, std::min<long long>(64, strip_rows / target));
     }
     for (int k = 0; k < c->n; ++k) {
         const lbm_params& p = c->params[k];

@@ -52,9 +52,17 @@ struct X2Smem {
     static_assert(SLOT % 16 == 0 && RINGS % 16 == 0, "h slots must stay 16-byte aligned");
 };
 
+// Resident blocks per SM the kernel is compiled for. Measured on the 1024 x 4096
+// bubble: 384 / TX blocks (up to 168 registers a thread) beat 512 / TX (128
+// registers) by 17 % for FP32 storage -- the extra registers let the loads of
+// the collision row fly longer -- while the FP16-h form, with half the bytes
+// a cell to wait for, is faster with the fourth block. Never more blocks than
+// the shared-memory rings allow (228 KB a SM, 1 KB of it reserved per block).
 template <int FORM, int TX>
-struct X2Occ {   // register budget: 128 registers a thread
-    static constexpr int value = (512 / TX) > 0 ? 512 / TX : 1;
+struct X2Occ {
+    static constexpr int by_regs = ((Form<FORM>::h16 ? 512 : 384) / TX) > 0 ? (Form<FORM>::h16 ? 512 : 384) / TX : 1;
+    static constexpr int by_smem = (int)((228u * 1024u) / (X2Smem<FORM, TX>::bytes + 1024u));
+    static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
 };
 
 template <int FORM, int TX, bool MON = false>
