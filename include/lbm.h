@@ -120,11 +120,15 @@ typedef struct lbm_diag {
     int64_t time;                        /* steps taken since lbm_init                  */
 } lbm_diag;
 
-/* Per-step monitor record of one instance (see lbm_set_monitor). */
+/* Per-step monitor record of one instance (see lbm_set_monitor); written on the
+ * GPU in this layout and copied to the host as it is. */
 typedef struct lbm_monitor {
     double sum_phi;                      /* sum of phi over the lattice (Eq. 18)        */
     double kinetic_energy;               /* sum of rho |u|^2 / 2 (u of Eq. 27a)         */
     double max_u;                        /* max |u|                                     */
+    int32_t nonfinite;                   /* 1 if phi or u was NaN or infinite somewhere */
+    int32_t device_status;               /* the context's device status word then (0 ok,
+                                            LBM_ETIMEOUT: a bounded wait ran out)       */
     int64_t time;                        /* time level the sums belong to               */
 } lbm_monitor;
 
@@ -183,6 +187,15 @@ lbm_status lbm_set_monitor(lbm_ctx* ctx, int enable);
  * lbm_init of the instance or lbm_load), LBM_ETIMEOUT / LBM_ECUDA (as
  * lbm_sync), LBM_ENONFINITE (phi or u not finite somewhere; *out is filled). */
 lbm_status lbm_read_monitor(lbm_ctx* ctx, int instance, lbm_monitor* out);
+
+/* As lbm_read_monitor without the wait: queues on the context's stream the copy
+ * of the record into host_out (caller-owned; pinned memory, e.g. from
+ * cudaMallocHost, keeps the copy asynchronous) and returns. The record is valid
+ * once the stream has passed this point (lbm_sync, or a CUDA event recorded on
+ * the stream after the call); the caller checks its nonfinite and device_status
+ * fields. A later monitored step does not disturb a copy already queued.
+ * Errors: as lbm_read_monitor, except the device ones (they are in the record). */
+lbm_status lbm_read_monitor_async(lbm_ctx* ctx, int instance, lbm_monitor* host_out);
 
 /* Macroscopic fields of one instance at the current time, computed from the
  * current populations exactly as the next step's macroscopic stage would

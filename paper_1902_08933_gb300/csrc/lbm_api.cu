@@ -152,8 +152,10 @@ struct lbm_ctx {
     bool monitor = false;
     double* d_mon_partials = nullptr;   // kMonQ doubles per work item
     int* d_mon_csr = nullptr;           // per instance: work items [ptr[k], ptr[k+1]) of idx
-    double* d_mon = nullptr;            // kMonQ doubles per instance
-    double* h_mon = nullptr;            // pinned: kMonQ doubles + the status word
+    lbm_monitor* d_mon = nullptr;       // one record per instance
+    int64_t steps_total = 0;            // steps taken by the context
+    int64_t* d_time_base = nullptr;     // per instance: time - steps_total (device copy)
+    lbm_monitor* h_mon = nullptr;       // pinned staging record
     std::vector<int64_t> mon_time;      // time level of the recorded sums (-1: none)
     bool use_graphs = true;
     double* d_tmp = nullptr;       // 2 * max_cells
@@ -425,6 +427,7 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_mon_partials);
     cudaFree(c->d_mon_csr);
     cudaFree(c->d_mon);
+    cudaFree(c->d_time_base);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->h_mon) cudaFreeHost(c->h_mon);
@@ -504,8 +507,11 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
         (e = alloc((void**)&c->d_partials, lbm::kDiagBlocks * lbm::kDiagQuantities * sizeof(double))) !=
             cudaSuccess ||
         (e = alloc((void**)&c->d_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess ||
-        (e = alloc((void**)&c->d_status, sizeof(int))) != cudaSuccess)
+        (e = alloc((void**)&c->d_status, sizeof(int))) != cudaSuccess ||
+        (e = alloc((void**)&c->d_time_base, n_instances * sizeof(int64_t))) != cudaSuccess)
         return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+    if ((e = cudaMemset(c->d_time_base, 0, n_instances * sizeof(int64_t))) != cudaSuccess)
+        return cleanup(LBM_ECUDA);
     if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(LBM_ECUDA);
     if ((e = cudaMallocHost((void**)&c->h_result, lbm::kDiagQuantities * sizeof(double))) != cudaSuccess)
         return cleanup(LBM_ENOMEM);
@@ -536,6 +542,9 @@ static lbm_status init_common(lbm_ctx* c, int instance, const double* phi0_dev) 
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->time[instance] = 0;
     c->mon_time[instance] = -1;
+    const int64_t base = -c->steps_total;
+    e = cudaMemcpy(c->d_time_base + instance, &base, sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "time base upload");
     c->ready[instance] = 1;
     return LBM_OK;
 }
@@ -564,25 +573,57 @@ lbm_status lbm_init_device(lbm_ctx* c, int instance, const double* phi0_device) 
 }
 
 namespace {
-// Queues one step (every launch class) reading the buffers of parity `in`.
-// One warp per instance adds the monitor slots of its work items in work-list
-// order (fixed, so the sums do not depend on timing); max |u|^2 -> max |u|.
-__global__ void monitor_final(const double* __restrict__ partials, const int* __restrict__ csr, int n,
-                              double* __restrict__ out) {
-    const int k = blockIdx.x, q = threadIdx.x;
-    if (q >= lbm::kMonQ) return;
+// One block per instance adds the monitor slots of its work items: thread t
+// takes items t, t + 128, ..., then a fixed shuffle / shared-memory tree combines
+// the threads (a fixed order, so the sums do not depend on timing). Then max
+// |u|^2 becomes max |u| and the record gets the non-finite flag, the status word
+// as the stream reaches it, and the time level.
+constexpr int kMonThreads = 128;
+__global__ void __launch_bounds__(kMonThreads) monitor_final(const double* __restrict__ partials,
+                                                             const int* __restrict__ csr, int n,
+                                                             const int* __restrict__ status, int64_t step,
+                                                             const int64_t* __restrict__ time_base,
+                                                             lbm_monitor* __restrict__ out) {
+    const int k = blockIdx.x, t = threadIdx.x;
     const int* idx = csr + n + 1;
-    double v = 0.0;
-    for (int j = csr[k]; j < csr[k + 1]; ++j) {
-        const double x = partials[(long long)idx[j] * lbm::kMonQ + q];
-        v = q == 2 ? fmax(v, x) : v + x;
+    double m = 0.0, e = 0.0, u = 0.0, f = 0.0;
+    for (int j = csr[k] + t; j < csr[k + 1]; j += kMonThreads) {
+        const double* p = partials + (long long)idx[j] * lbm::kMonQ;
+        m += p[0];
+        e += p[1];
+        u = fmax(u, p[2]);
+        f += p[3];
     }
-    out[k * lbm::kMonQ + q] = q == 2 ? sqrt(v) : v;
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_down_sync(0xffffffffu, m, o);
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        u = fmax(u, __shfl_down_sync(0xffffffffu, u, o));
+        f += __shfl_down_sync(0xffffffffu, f, o);
+    }
+    __shared__ double red[4][kMonThreads / 32];
+    const int lane = t & 31, w = t >> 5;
+    if (lane == 0) { red[0][w] = m; red[1][w] = e; red[2][w] = u; red[3][w] = f; }
+    __syncthreads();
+    if (t == 0) {
+        for (int v = 1; v < kMonThreads / 32; ++v) {
+            m += red[0][v];
+            e += red[1][v];
+            u = fmax(u, red[2][v]);
+            f += red[3][v];
+        }
+        lbm_monitor& r = out[k];
+        r.sum_phi = m;
+        r.kinetic_energy = e;
+        r.max_u = sqrt(u);
+        r.nonfinite = f != 0.0 ? 1 : 0;
+        r.device_status = *status;
+        r.time = step + time_base[k];
+    }
 }
 
 // Queues one time step (all launches of the plan) reading buffer set `in`; with
 // `monitor` the step kernels also write their monitor slots, reduced per instance.
-cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false) {
+cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
     StepArgs a = step_args(c, in);
     for (const auto& L : c->launches) {
         a.work = c->d_work + L.offset;
@@ -593,7 +634,8 @@ cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false) {
         if (e != cudaSuccess) return e;
     }
     if (monitor) {
-        monitor_final<<<c->n, 32, 0, c->stream>>>(c->d_mon_partials, c->d_mon_csr, c->n, c->d_mon);
+        monitor_final<<<c->n, kMonThreads, 0, c->stream>>>(c->d_mon_partials, c->d_mon_csr, c->n, c->d_status,
+                                                   mon_step, c->d_time_base, c->d_mon);
         return cudaGetLastError();
     }
     return cudaSuccess;
@@ -674,10 +716,12 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         c->cur ^= 1;
     }
     if (mon_last) {
-        cudaError_t e = enqueue_step(c, c->cur, true);
+        // the record's time level is the monitored step's input level
+        cudaError_t e = enqueue_step(c, c->cur, true, c->steps_total + nsteps - 1);
         if (e != cudaSuccess) return cuda_fail(c, e, "monitored step launch");
         c->cur ^= 1;
     }
+    c->steps_total += nsteps;
     for (int k = 0; k < c->n; ++k) {
         c->time[k] += nsteps;
         if (mon_last) c->mon_time[k] = c->time[k] - 1;
@@ -689,10 +733,23 @@ lbm_status lbm_set_monitor(lbm_ctx* c, int enable) {
     if (!c) return LBM_EINVAL;
     LBM_CK(c, cudaSetDevice(c->device));
     if (enable && !c->d_mon) {
-        LBM_CK(c, cudaMalloc(&c->d_mon, (size_t)c->n * lbm::kMonQ * sizeof(double)));
-        LBM_CK(c, cudaMallocHost(&c->h_mon, (lbm::kMonQ + 1) * sizeof(double)));
+        LBM_CK(c, cudaMalloc(&c->d_mon, (size_t)c->n * sizeof(lbm_monitor)));
+        LBM_CK(c, cudaMallocHost(&c->h_mon, sizeof(lbm_monitor)));
     }
     c->monitor = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_read_monitor_async(lbm_ctx* c, int instance, lbm_monitor* host_out) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!host_out) return fail(c, LBM_EINVAL, "out is NULL");
+    if (!c->d_mon || c->mon_time[instance] < 0)
+        return fail(c, LBM_ESTATE, "no monitored step yet (lbm_set_monitor, then lbm_step)");
+    LBM_CK(c, cudaSetDevice(c->device));
+    if ((st = sticky(c)) != LBM_OK) return st;
+    LBM_CK(c, cudaMemcpyAsync(host_out, c->d_mon + instance, sizeof(lbm_monitor), cudaMemcpyDeviceToHost,
+                              c->stream));
     return LBM_OK;
 }
 
@@ -702,21 +759,12 @@ lbm_status lbm_read_monitor(lbm_ctx* c, int instance, lbm_monitor* out) {
     if (!out) return fail(c, LBM_EINVAL, "out is NULL");
     if (!c->d_mon || c->mon_time[instance] < 0)
         return fail(c, LBM_ESTATE, "no monitored step yet (lbm_set_monitor, then lbm_step)");
-    LBM_CK(c, cudaSetDevice(c->device));
-    if ((st = sticky(c)) != LBM_OK) return st;
-    double* h = c->h_mon;
-    LBM_CK(c, cudaMemcpyAsync(h, c->d_mon + (size_t)instance * lbm::kMonQ, lbm::kMonQ * sizeof(double),
-                              cudaMemcpyDeviceToHost, c->stream));
-    LBM_CK(c, cudaMemcpyAsync(h + lbm::kMonQ, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    st = lbm_read_monitor_async(c, instance, c->h_mon);
+    if (st != LBM_OK) return st;
     LBM_CK(c, cudaStreamSynchronize(c->stream));
-    int status = 0;
-    std::memcpy(&status, h + lbm::kMonQ, sizeof(int));
-    if (status != 0) return device_status(c);
-    out->sum_phi = h[0];
-    out->kinetic_energy = h[1];
-    out->max_u = h[2];
-    out->time = c->mon_time[instance];
-    if (h[3] != 0.0) return fail(c, LBM_ENONFINITE, "non-finite phi or velocity in the monitored step");
+    *out = *c->h_mon;
+    if (out->device_status != 0) return device_status(c);
+    if (out->nonfinite) return fail(c, LBM_ENONFINITE, "non-finite phi or velocity in the monitored step");
     return LBM_OK;
 }
 
@@ -929,6 +977,11 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     std::fclose(f);
     c->time = ts;
     c->mon_time.assign(c->n, -1);
+    {
+        std::vector<int64_t> base(c->n);
+        for (int k = 0; k < c->n; ++k) base[k] = c->time[k] - c->steps_total;
+        LBM_CK(c, cudaMemcpy(c->d_time_base, base.data(), c->n * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
     c->ready.assign(c->n, 1);
     // the whole state was replaced: a timeout recorded before no longer applies
     LBM_CK(c, cudaMemset(c->d_status, 0, sizeof(int)));

@@ -2,6 +2,7 @@
 // Included by lbm_form<N>.cu, which instantiates them for its form.
 #pragma once
 
+#include "lbm_aux.cuh"
 #include "lbm_device.cuh"
 #include "lbm_step_tma.cuh"
 #include "lbm_step_x2.cuh"
@@ -197,7 +198,7 @@ cudaError_t launch_diag_t(const AuxArgs& a, int ncells, cudaStream_t s) {
     phi_pass<FORM><<<g, 256, 0, s>>>(a);
     mu_pass<FORM><<<g, 256, 0, s>>>(a);
     diag_pass<FORM><<<kDiagBlocks, 256, 0, s>>>(a);
-    diag_final<<<1, 32, 0, s>>>(a.partials, kDiagBlocks, a.result);
+    diag_final<<<1, kDiagFinalThreads, 0, s>>>(a.partials, kDiagBlocks, a.result);
     return cudaGetLastError();
 }
 

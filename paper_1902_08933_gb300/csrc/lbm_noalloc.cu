@@ -93,17 +93,34 @@ __global__ void __launch_bounds__(kThreads) reduce_fields_blocks(const double* _
     }
 }
 
-// One warp adds the partials of the blocks of this call in block order.
-__global__ void reduce_fields_final(const double* __restrict__ partials, int nblocks,
-                                    double* __restrict__ out) {
-    const int q = threadIdx.x;
-    if (q >= kQ) return;
-    double v = partials[q];
-    for (int b = 1; b < nblocks; ++b) {
-        const double x = partials[b * kQ + q];
-        v = (q == 3) ? fmax(v, x) : v + x;
+// One block adds the partials of this call's blocks: thread t takes blocks t,
+// t + 256, ..., then a fixed shuffle / shared-memory tree combines the threads.
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) reduce_fields_final(const double* __restrict__ partials,
+                                                                     int nblocks, double* __restrict__ out) {
+    const int t = threadIdx.x;
+    double acc[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
+    for (int b = t; b < nblocks; b += kFinalThreads)
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const double x = partials[b * kQ + q];
+            acc[q] = (q == 3) ? fmax(acc[q], x) : acc[q] + x;
+        }
+    __shared__ double red[kQ][kFinalThreads / 32];
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const double v = (q == 3) ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if (lane == 0) red[q][warp] = v;
     }
-    out[q] = v;
+    __syncthreads();
+    if (t < kQ) {
+        double v = red[t][0];
+        for (int w = 1; w < kFinalThreads / 32; ++w) v = (t == 3) ? fmax(v, red[t][w]) : v + red[t][w];
+        out[t] = v;
+    }
 }
 
 // Device address of g_partials on the current device, looked up once per device.
@@ -135,6 +152,6 @@ extern "C" lbm_status lbm_reduce_fields_noalloc(const double* fields_device, int
     const int nblocks = (int)((n + kCellsPerBlock - 1) / kCellsPerBlock);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     reduce_fields_blocks<<<nblocks, kThreads, 0, s>>>(fields_device, nx, n, partials);
-    reduce_fields_final<<<1, 32, 0, s>>>(partials, nblocks, out_device);
+    reduce_fields_final<<<1, kFinalThreads, 0, s>>>(partials, nblocks, out_device);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

@@ -65,7 +65,8 @@ class lbm_diag(ctypes.Structure):
 
 class lbm_monitor(ctypes.Structure):
     _fields_ = [("sum_phi", ctypes.c_double), ("kinetic_energy", ctypes.c_double),
-                ("max_u", ctypes.c_double), ("time", ctypes.c_int64)]
+                ("max_u", ctypes.c_double), ("nonfinite", ctypes.c_int32),
+                ("device_status", ctypes.c_int32), ("time", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -83,6 +84,7 @@ SIGNATURES = [
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_set_monitor", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_read_monitor", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_monitor)]),
+    ("lbm_read_monitor_async", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     ("lbm_get_fields", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _DP]),
     ("lbm_get_fields_device", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _VP]),
     ("lbm_diagnostics", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_diag)]),
@@ -183,6 +185,12 @@ def lbm_read_monitor(ctx, instance: int) -> dict:
         _check(st, ctx)
     return {"sum_phi": m.sum_phi, "kinetic_energy": m.kinetic_energy, "max_u": m.max_u,
             "time": m.time, "status": st}
+
+
+def lbm_read_monitor_async(ctx, instance: int, host_record_ptr: int):
+    """Queues the copy of the record into caller memory at host_record_ptr (an
+    lbm_monitor's address, ideally pinned); read it after the stream passes."""
+    _check(library().lbm_read_monitor_async(ctx, int(instance), _VP(host_record_ptr)), ctx)
 
 
 def lbm_get_fields(ctx, instance, mask: int, out: np.ndarray):

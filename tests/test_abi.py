@@ -36,7 +36,7 @@ def test_struct_layouts_match_header(L):
     import ctypes
     assert ctypes.sizeof(L.lbm_params) == 8 * 4 + 11 * 8
     assert ctypes.sizeof(L.lbm_diag) == 14 * 8 + 2 * 4 + 8
-    assert ctypes.sizeof(L.lbm_monitor) == 3 * 8 + 8
+    assert ctypes.sizeof(L.lbm_monitor) == 3 * 8 + 2 * 4 + 8
 
 
 def _valid():
@@ -78,6 +78,7 @@ def test_null_context_calls_are_errors(L):
     assert lib.lbm_inject_wait_timeout(None, 16) == L.LBM_EINVAL
     assert lib.lbm_set_monitor(None, 1) == L.LBM_EINVAL
     assert lib.lbm_read_monitor(None, 0, None) == L.LBM_EINVAL
+    assert lib.lbm_read_monitor_async(None, 0, None) == L.LBM_EINVAL
     assert lib.lbm_time(None, 0) == -1
     assert lib.lbm_launches_per_step(None) == 0
     lib.lbm_destroy(None)

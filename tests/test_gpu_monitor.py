@@ -159,3 +159,49 @@ def test_monitor_states_and_nonfinite(L):
         with pytest.raises(L.LbmError) as e:
             L.lbm_read_monitor(sim.ctx, 0)            # monitor off: nothing recorded
         assert e.value.status == L.LBM_ESTATE
+
+
+def _record(L, buf):
+    import ctypes
+    return L.lbm_monitor.from_address(buf.data_ptr())
+
+
+def test_async_read_matches_and_times_are_per_instance(L):
+    import torch
+    cfgs = [wl.static_droplet(n=32, R=8.0), wl.static_droplet(n=40, R=10.0)]
+    phis = [wl.initial_phi(c) for c in cfgs]
+    stream = torch.cuda.Stream()
+    bufs = [torch.zeros(40, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    with L.Simulation(cfgs, "f32_c", stream=stream.cuda_stream, phi0=phis) as sim:
+        L.lbm_set_monitor(sim.ctx, True)
+        sim.step(10)
+        sim.init(1, phis[1])                  # instance 1 restarts at time 0
+        sim.step(5)
+        for k in range(2):
+            L.lbm_read_monitor_async(sim.ctx, k, bufs[k].data_ptr())
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        sim.step(3)                           # a later monitored step: the copies stay intact
+        ev.synchronize()
+        recs = [_record(L, b) for b in bufs]
+        assert (recs[0].time, recs[1].time) == (14, 4)
+        assert recs[0].nonfinite == 0 and recs[0].device_status == 0
+        sync0 = L.lbm_read_monitor(sim.ctx, 0)
+        assert sync0["time"] == 17
+    with L.Simulation(cfgs, "f32_c", stream=stream.cuda_stream, phi0=phis) as ref:
+        L.lbm_set_monitor(ref.ctx, True)
+        ref.step(15)
+        m = L.lbm_read_monitor(ref.ctx, 0)
+    assert m["time"] == 14
+    assert (m["sum_phi"], m["kinetic_energy"], m["max_u"]) == (recs[0].sum_phi, recs[0].kinetic_energy, recs[0].max_u)
+
+
+def test_monitor_record_carries_a_wait_timeout(L):
+    cfg = wl.static_droplet(n=16)
+    with L.Simulation(cfg, "f32_c", phi0=[wl.initial_phi(cfg)]) as sim:
+        L.lbm_set_monitor(sim.ctx, True)
+        L.lbm_inject_wait_timeout(sim.ctx, 1 << 12)
+        sim.step(1)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_read_monitor(sim.ctx, 0)
+        assert e.value.status == L.LBM_ETIMEOUT
