@@ -148,6 +148,10 @@ struct lbm_ctx {
     // dropped when the plan changes)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+    // graph capture with several launch classes: one branch per class
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     // per-step monitor of the last step of each lbm_step call
     bool monitor = false;
     double* d_mon_partials = nullptr;   // kMonQ doubles per work item
@@ -429,6 +433,9 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_mon);
     cudaFree(c->d_time_base);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaStream_t x : c->side) cudaStreamDestroy(x);
+    for (cudaEvent_t x : c->join) cudaEventDestroy(x);
+    if (c->fork) cudaEventDestroy(c->fork);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->h_mon) cudaFreeHost(c->h_mon);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -621,16 +628,21 @@ __global__ void __launch_bounds__(kMonThreads) monitor_final(const double* __res
     }
 }
 
+// Queues one launch class of one time step on stream s, reading buffer set `in`.
+cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStream_t s, bool monitor) {
+    StepArgs a = step_args(c, in);
+    a.work = c->d_work + L.offset;
+    a.mon = monitor ? c->d_mon_partials + (long long)L.offset * lbm::kMonQ : nullptr;
+    return by_form(c->form, [&](auto F) {
+        return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, s, L.variant, monitor);
+    });
+}
+
 // Queues one time step (all launches of the plan) reading buffer set `in`; with
 // `monitor` the step kernels also write their monitor slots, reduced per instance.
 cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
-    StepArgs a = step_args(c, in);
     for (const auto& L : c->launches) {
-        a.work = c->d_work + L.offset;
-        a.mon = monitor ? c->d_mon_partials + (long long)L.offset * lbm::kMonQ : nullptr;
-        cudaError_t e = by_form(c->form, [&](auto F) {
-            return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream, L.variant, monitor);
-        });
+        cudaError_t e = enqueue_class(c, in, L, c->stream, monitor);
         if (e != cudaSuccess) return e;
     }
     if (monitor) {
@@ -642,9 +654,13 @@ cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_s
 }
 
 // Captures an even number of steps (starting from parity 0) into a CUDA graph, so
-// that long runs of small grids are not bound by launch overhead. Returns false
-// (and the caller launches directly) if the stream cannot be captured: the legacy
-// default stream, or a stream the caller is capturing itself.
+// that long runs of small grids are not bound by launch overhead. With several
+// launch classes (strip widths / load paths) each class is its own branch of the
+// graph: a class holds whole instances, which depend on nothing else, so its
+// steps need not wait for the other classes' -- the classes overlap instead of
+// each step ending in the tails of 2-3 short launches. Returns false (and the
+// caller launches directly) if the stream cannot be captured: the legacy default
+// stream, or a stream the caller is capturing itself.
 bool build_graph(lbm_ctx* c) {
     if (c->graph) return true;
     if (!c->use_graphs || c->stream == nullptr || c->stream == cudaStreamLegacy) return false;
@@ -652,15 +668,38 @@ bool build_graph(lbm_ctx* c) {
     if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return false;
     // about 64 launches a graph
-    const int per_step = std::max<int>(1, (int)c->launches.size());
+    const int nl = (int)c->launches.size();
+    const int per_step = std::max(1, nl);
     const int steps = 2 * std::max(1, 32 / per_step);
+    if (nl > 1) {
+        while ((int)c->side.size() < nl) {
+            cudaStream_t x = nullptr;
+            cudaEvent_t ev = nullptr;
+            if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return false;
+            c->side.push_back(x);
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+            c->join.push_back(ev);
+        }
+        if (!c->fork && cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) return false;
+    }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     cudaError_t e = cudaSuccess;
-    for (int t = 0; t < steps && e == cudaSuccess; ++t) e = enqueue_step(c, t & 1);
+    if (nl > 1) {
+        e = cudaEventRecord(c->fork, c->stream);
+        for (int i = 0; i < nl && e == cudaSuccess; ++i) {
+            e = cudaStreamWaitEvent(c->side[i], c->fork, 0);
+            for (int t = 0; t < steps && e == cudaSuccess; ++t)
+                e = enqueue_class(c, t & 1, c->launches[i], c->side[i], false);
+            if (e == cudaSuccess) e = cudaEventRecord(c->join[i], c->side[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->join[i], 0);
+        }
+    } else {
+        for (int t = 0; t < steps && e == cudaSuccess; ++t) e = enqueue_step(c, t & 1);
+    }
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);

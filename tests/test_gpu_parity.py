@@ -336,9 +336,13 @@ def test_bubble_load_paths(L):
             assert L.lbm_launch_info(sim.ctx, 0)["variant"] == ("plain" if form == "f64" else "tma")
 
 
+@pytest.mark.parametrize("classes", [1, 3])
 @pytest.mark.parametrize("form", ["f64", "f32_c"])
-def test_graph_replay_matches_direct_launches(L, form):
+def test_graph_replay_matches_direct_launches(L, form, classes):
     cfgs = [wl.static_droplet(n=64, R=15), wl.rising_bubble(nx=96, ny=80, R=12, cy=30, W=4.0, Re=10.0)]
+    if classes == 3:
+        # three launch classes (strip widths / load paths): one graph branch each
+        cfgs += [wl.rising_bubble(nx=160, ny=48, R=10, cy=18, W=4.0, Re=10.0), wl.static_droplet(n=33, R=8)]
     phis = [wl.initial_phi(c) for c in cfgs]
     out = []
     for graphs in (True, False):
@@ -347,6 +351,8 @@ def test_graph_replay_matches_direct_launches(L, form):
             sim.step(1)          # odd start: the graph path first realigns the parity
             sim.step(157)
             sim.step(3)
-            out.append([sim.populations(k) for k in range(2)])
+            if form == "f32_c":
+                assert L.lbm_launches_per_step(sim.ctx) == classes
+            out.append([sim.populations(k) for k in range(len(cfgs))])
     for (ha, ga), (hb, gb) in zip(out[0], out[1]):
         assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
