@@ -145,6 +145,29 @@ def traffic_record(kernel_key):
     return float(t.group(1))
 
 
+# FP64 pipe of GB300: 2 FP64 FMA a clock per SM (the nominal 1.25 TFLOP/s at
+# 152 SMs and 2.07 GHz).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PIPE_OPS_PER_S = 152 * 2 * 2.07e9
+
+
+def fp64_roofline(mlups):
+    """ALU roofline of the FP64 form from the FP64 operation counts per lattice
+    update in the committed ncu summary (None if absent)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_f64_bubble_1024x4096.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    flop = re.search(r"fp64_flop_per_lup:\s*([0-9.]+)", text)
+    inst = re.search(r"fp64_inst_per_lup:\s*([0-9.]+)", text)
+    if not flop or not inst:
+        return None
+    achieved = float(flop.group(1)) * mlups * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+            "fp64_pipe_frac": float(inst.group(1)) * mlups * 1e6 / FP64_PIPE_OPS_PER_S}
+
+
 def rel_err(a, b):
     import numpy as np
     den = float(np.max(np.abs(b)))
@@ -349,6 +372,8 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
             gbs = BYTES_PER_LUP[form] * cells / (ms * 1e-3 / K) / 1e9
             forms[form] = {"MLUPS": mlups, "GBps": gbs, "frac_hbm": gbs / hbm_peak,
                            "steps": K,
+                           "roofline": fp64_roofline(mlups) if form == "f64" else
+                           {"bound": "hbm", "frac": gbs / hbm_peak},
                            "err_vs_f64_after_%d_steps" % acc_steps: (
                                None if form == "f64" else
                                {k: rel_err(f[k], ref[k]) for k in ("phi", "ux", "uy", "p")})}

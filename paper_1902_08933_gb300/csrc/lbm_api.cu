@@ -282,11 +282,12 @@ lbm_status plan(lbm_ctx* c) {
         f_tma = lbm::has_tma_t<decltype(F)::value>();
         return cudaSuccess;
     });
-    // Several instances: one run length for all, sized for about eight waves of
+    // Several instances: one run length for all, sized for about four waves of
     // blocks (blocks of different instances differ in width and length, so one
-    // exact wave cannot be had; many short runs balance, at the price of the 4
-    // halo rows each run re-reads, mostly from L2). Tiny batches get 1-row runs:
-    // there the step is bound by the latency of a block's row march.
+    // exact wave cannot be had; shorter runs balance better but re-read more
+    // halo rows -- 4 a run, mostly from L2 -- and the launch classes overlap as
+    // graph branches, which takes up much of the imbalance). Tiny batches get
+    // 1-row runs: there the step is bound by the latency of a block's row march.
     int batch_rows = 32;
     if (c->n > 1) {
         long long strip_rows = 0;
@@ -302,7 +303,7 @@ lbm_status plan(lbm_ctx* c) {
             });
             occ_min = std::min(occ_min, std::max(occ, 1));
         }
-        const long long target = 8LL * sms * occ_min;
+        const long long target = 4LL * sms * occ_min;
         batch_rows = (int)std::max<long long>(1, std::min<long long>(64, strip_rows / target));
     }
     for (int k = 0; k < c->n; ++k) {
