@@ -397,15 +397,17 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
             pux = ld_pair(phiu + c);
             puy = ld_pair(phiu + S + c);
         }
+        // the next collision row's g and phi*u into L2, issued with this row's loads
+        // (measured on the 1024 x 4096 bubble, FP32 h: +11 % against no prefetch;
+        // later in the iteration or further ahead gained less, lost from three
+        // rows ahead; FP16 h: no gain)
+        if constexpr (!F::h16)
+            if (k + 1 < wk.nrows) l2_prefetch_row(Y + d);
         lead_row_async(Y + 2 * d);
         __syncthreads();
         // every thread is past the collision of row Y - d: the h slot of row Y - d
         // and the p slot of row Y - 2d are free for the next iteration's rows
         if (k + 1 < wk.nrows) prefetch(Y + 3 * d, Y + 2 * d);
-        // next collision row into L2 (measured on the 1024 x 4096 bubble, FP32 h:
-        // +7 % at one row ahead, +4 % at two, -6 % at three; FP16 h: no gain)
-        if constexpr (!F::h16)
-            if (k + 1 < wk.nrows) l2_prefetch_row(Y + d);
         mu_row(Y + d);
         __syncthreads();
         collide_row(Y, g, pux, puy);
