@@ -103,6 +103,34 @@ int  orc_fields(const orc_params* P, const double* h, const double* g, const dou
 int  orc_diagnostics(const orc_params* P, const double* h, const double* g,
                      const double* p_prev, orc_diag* out);
 
+/* ---- the same model on the D3Q15 lattice (Sec. 2.2 after Eq. 25; d = 3 in
+ * Eq. 34 and in the printed G_0), oracle3d.c. Grid nx x ny x nz with x and z
+ * periodic and y as in 2-D (walls_y); buoyancy along -y. Layout
+ * a[(z * ny + y) * nx + x]; populations 15 planes in the paper's D3Q15 order;
+ * phiu_prev 3 planes; velocities passed as u[3]. ---- */
+void   orc3_lattice(int* cx, int* cy, int* cz, double* w, int* opposite);
+double orc3_s(int i, const double* u);
+void   orc3_geq(double p, double rho, const double* u, double rho0, double* geq);
+void   orc3_heq(double phi, double mu, double eta, const double* u, double* heq);
+void   orc3_force_dist(double S, double rho, double S1, const double* F, const double* Ft,
+                       const double* u, double* G);
+double orc3_G0_printed(double rho, double S1, const double* F, const double* dp, const double* u);
+void   orc3_source_R(double tau_h, const double* dphiu, double* R);
+double orc3_pressure(int scheme, const double* g, double S, double rho, const double* u,
+                     double tau_g, double G0);
+void   orc3_grad(const orc_params* P, int nz, const double* f, double* gx, double* gy, double* gz);
+void   orc3_lap(const orc_params* P, int nz, const double* f, double* lap);
+void   orc3_stream(const orc_params* P, int nz, const double* post, double* pre);
+int    orc3_init(const orc_params* P, int nz, const double* phi0, double* h, double* g,
+                 double* phiu_prev, double* p_prev);
+int    orc3_step(const orc_params* P, int nz, double* h, double* g, double* phiu_prev,
+                 double* p_prev, int nsteps);
+int    orc3_fields(const orc_params* P, int nz, const double* h, const double* g,
+                   const double* p_prev, double* phi, double* ux, double* uy, double* uz,
+                   double* p, double* rho, double* mu, double* Plap);
+int    orc3_diagnostics(const orc_params* P, int nz, const double* h, const double* g,
+                        const double* p_prev, orc_diag* out);
+
 /* Analytic layered Poiseuille profile, Eq. 37: y measured from the interface,
  * walls at y = -hh and y = +hh, dynamic viscosity mu_up for 0 < y <= hh and
  * mu_down for -hh <= y <= 0 (Eq. 37 names them mu_A and mu_B). */

@@ -20,6 +20,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
+SRC3 = os.path.join(HERE, "oracle3d.c")
 HDR = os.path.join(HERE, "oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
 
@@ -63,11 +64,12 @@ def build(force: bool = False) -> str:
     exactly as written). Rebuilds when the sources are newer than the library."""
     with _lock:
         stale = (not os.path.exists(LIB) or
-                 os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+                 os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(SRC3),
+                                             os.path.getmtime(HDR)))
         if force or stale:
             tmp = LIB + ".tmp.%d" % os.getpid()
             cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-                   "-shared", "-std=c11", SRC, "-o", tmp, "-lm"]
+                   "-shared", "-std=c11", SRC, SRC3, "-o", tmp, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, LIB)
     return LIB
@@ -103,6 +105,26 @@ def lib():
         L.orc_diagnostics.argtypes = [P, _DP, _DP, _DP, ctypes.POINTER(Diag)]
         L.orc_layered_ux.argtypes = [ctypes.c_double] * 5
         L.orc_layered_ux.restype = ctypes.c_double
+        IP = ctypes.POINTER(ctypes.c_int)
+        L.orc3_lattice.argtypes = [IP, IP, IP, _DP, IP]
+        L.orc3_s.argtypes = [ctypes.c_int, _DP]
+        L.orc3_s.restype = ctypes.c_double
+        L.orc3_geq.argtypes = [ctypes.c_double, ctypes.c_double, _DP, ctypes.c_double, _DP]
+        L.orc3_heq.argtypes = [ctypes.c_double] * 3 + [_DP, _DP]
+        L.orc3_force_dist.argtypes = [ctypes.c_double] * 3 + [_DP] * 4
+        L.orc3_G0_printed.argtypes = [ctypes.c_double, ctypes.c_double, _DP, _DP, _DP]
+        L.orc3_G0_printed.restype = ctypes.c_double
+        L.orc3_source_R.argtypes = [ctypes.c_double, _DP, _DP]
+        L.orc3_pressure.argtypes = [ctypes.c_int, _DP, ctypes.c_double, ctypes.c_double, _DP,
+                                    ctypes.c_double, ctypes.c_double]
+        L.orc3_pressure.restype = ctypes.c_double
+        L.orc3_grad.argtypes = [P, ctypes.c_int, _DP, _DP, _DP, _DP]
+        L.orc3_lap.argtypes = [P, ctypes.c_int, _DP, _DP]
+        L.orc3_stream.argtypes = [P, ctypes.c_int, _DP, _DP]
+        L.orc3_init.argtypes = [P, ctypes.c_int, _DP, _DP, _DP, _DP, _DP]
+        L.orc3_step.argtypes = [P, ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int]
+        L.orc3_fields.argtypes = [P, ctypes.c_int, _DP, _DP, _DP] + [_DP] * 8
+        L.orc3_diagnostics.argtypes = [P, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(Diag)]
         _lib = L
     return _lib
 
@@ -261,3 +283,118 @@ def run(cfg: dict, phi0, nsteps: int, **over):
     if nsteps:
         step(P, st, nsteps)
     return P, st
+
+
+# ---------------------------------------------------------------- D3Q15 (3-D)
+def lattice3():
+    """D3Q15 velocities, weights and opposite directions (Sec. 2.2)."""
+    cx, cy, cz, op = (ctypes.c_int * 15)(), (ctypes.c_int * 15)(), (ctypes.c_int * 15)(), (ctypes.c_int * 15)()
+    w = np.zeros(15)
+    lib().orc3_lattice(cx, cy, cz, _ptr(w), op)
+    return np.array([list(cx), list(cy), list(cz)]), w, np.array(list(op))
+
+
+def _v3(u):
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    assert a.shape == (3,)
+    return a
+
+
+def s3(i, u):
+    return lib().orc3_s(i, _ptr(_v3(u)))
+
+
+def geq3(p, rho, u, rho0=0.0):
+    out = np.zeros(15)
+    lib().orc3_geq(p, rho, _ptr(_v3(u)), rho0, _ptr(out))
+    return out
+
+
+def heq3(phi, mu, eta, u):
+    out = np.zeros(15)
+    lib().orc3_heq(phi, mu, eta, _ptr(_v3(u)), _ptr(out))
+    return out
+
+
+def force_dist3(S, rho, S1, F, Ft, u):
+    out = np.zeros(15)
+    lib().orc3_force_dist(S, rho, S1, _ptr(_v3(F)), _ptr(_v3(Ft)), _ptr(_v3(u)), _ptr(out))
+    return out
+
+
+def G0_printed3(rho, S1, F, dp, u):
+    return lib().orc3_G0_printed(rho, S1, _ptr(_v3(F)), _ptr(_v3(dp)), _ptr(_v3(u)))
+
+
+def source_R3(tau_h, dphiu):
+    out = np.zeros(15)
+    lib().orc3_source_R(tau_h, _ptr(_v3(dphiu)), _ptr(out))
+    return out
+
+
+def pressure3(scheme, g, S, rho, u, tau_g, G0):
+    return lib().orc3_pressure(scheme, _ptr(np.ascontiguousarray(g, dtype=np.float64)), S, rho,
+                               _ptr(_v3(u)), tau_g, G0)
+
+
+def grad3(P: Params, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    gx, gy, gz = np.zeros_like(f), np.zeros_like(f), np.zeros_like(f)
+    lib().orc3_grad(ctypes.byref(P), f.shape[0], _ptr(f), _ptr(gx), _ptr(gy), _ptr(gz))
+    return gx, gy, gz
+
+
+def lap3(P: Params, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros_like(f)
+    lib().orc3_lap(ctypes.byref(P), f.shape[0], _ptr(f), _ptr(out))
+    return out
+
+
+def stream3(P: Params, post):
+    post = np.ascontiguousarray(post, dtype=np.float64)
+    out = np.zeros_like(post)
+    lib().orc3_stream(ctypes.byref(P), post.shape[1], _ptr(post), _ptr(out))
+    return out
+
+
+def init3(P: Params, phi0) -> dict:
+    """State of a D3Q15 grid from phi0 of shape (nz, ny, nx)."""
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    nz, ny, nx = phi0.shape
+    assert (ny, nx) == (P.ny, P.nx)
+    st = {"nz": nz, "h": np.zeros((15, nz, ny, nx)), "g": np.zeros((15, nz, ny, nx)),
+          "phiu_prev": np.zeros((3, nz, ny, nx)), "p_prev": np.zeros((nz, ny, nx))}
+    rc = lib().orc3_init(ctypes.byref(P), nz, _ptr(phi0), _ptr(st["h"]), _ptr(st["g"]),
+                         _ptr(st["phiu_prev"]), _ptr(st["p_prev"]))
+    if rc:
+        raise ValueError("orc3_init failed (%d)" % rc)
+    return st
+
+
+def step3(P: Params, st: dict, n: int) -> dict:
+    rc = lib().orc3_step(ctypes.byref(P), st["nz"], _ptr(st["h"]), _ptr(st["g"]),
+                         _ptr(st["phiu_prev"]), _ptr(st["p_prev"]), int(n))
+    if rc:
+        raise ValueError("orc3_step failed (%d)" % rc)
+    return st
+
+
+def fields3(P: Params, st: dict) -> dict:
+    shape = st["p_prev"].shape
+    names = ("phi", "ux", "uy", "uz", "p", "rho", "mu", "P")
+    out = {k: np.zeros(shape) for k in names}
+    rc = lib().orc3_fields(ctypes.byref(P), st["nz"], _ptr(st["h"]), _ptr(st["g"]), _ptr(st["p_prev"]),
+                           *[_ptr(out[k]) for k in names])
+    if rc:
+        raise ValueError("orc3_fields failed (%d)" % rc)
+    return out
+
+
+def diagnostics3(P: Params, st: dict) -> dict:
+    D = Diag()
+    rc = lib().orc3_diagnostics(ctypes.byref(P), st["nz"], _ptr(st["h"]), _ptr(st["g"]),
+                                _ptr(st["p_prev"]), ctypes.byref(D))
+    if rc:
+        raise ValueError("orc3_diagnostics failed (%d)" % rc)
+    return {k: getattr(D, k) for k, _ in Diag._fields_}

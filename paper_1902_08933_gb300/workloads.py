@@ -46,6 +46,9 @@ def uniform01(seed: int, n: int) -> np.ndarray:
 # Initial fields (Sec. 4): droplet Eq. 36, planar interface Eq. 9, bubble (the
 # droplet profile with the phases swapped, Sec. 4.4), noisy mixture (Sec. 4.1).
 def initial_phi(cfg: dict) -> np.ndarray:
+    """phi_0 of shape (ny, nx), or (nz, ny, nx) for a D3Q15 workload (nz > 1)."""
+    if int(cfg.get("nz", 0)) > 1:
+        return _initial_phi3(cfg)
     nx, ny = int(cfg["nx"]), int(cfg["ny"])
     spec = cfg["init"]
     kind = spec["kind"]
@@ -70,6 +73,34 @@ def initial_phi(cfg: dict) -> np.ndarray:
     else:
         raise ValueError("unknown init kind %r" % kind)
     return np.array(np.broadcast_to(phi, (ny, nx)), dtype=np.float64, order="C")
+
+
+def _initial_phi3(cfg: dict) -> np.ndarray:
+    """3-D phi_0: a sphere (Eq. 36 with the 3-D distance), a planar interface
+    normal to y (Eq. 9), noise or a uniform field."""
+    nx, ny, nz = int(cfg["nx"]), int(cfg["ny"]), int(cfg["nz"])
+    spec = cfg["init"]
+    kind = spec["kind"]
+    W = float(cfg["W"])
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    y = np.arange(ny, dtype=np.float64)[None, :, None]
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+    if kind in ("droplet", "bubble"):
+        r = np.sqrt((x - spec["cx"]) ** 2 + (y - spec["cy"]) ** 2 + (z - spec["cz"]) ** 2)
+        prof = 0.5 + 0.5 * np.tanh(2.0 * (spec["R"] - r) / W)
+        phi = prof if kind == "droplet" else 1.0 - prof
+    elif kind == "layered":
+        yc = y + 0.5 - ny / 2.0
+        sgn = -1.0 if spec.get("A_below", True) else 1.0
+        phi = 0.5 + 0.5 * np.tanh(sgn * 2.0 * yc / W) + 0.0 * x + 0.0 * z
+    elif kind == "noise":
+        u = uniform01(int(spec["seed"]), nx * ny * nz).reshape(nz, ny, nx)
+        phi = spec["mean"] + spec["amp"] * (2.0 * u - 1.0)
+    elif kind == "uniform":
+        phi = np.full((nz, ny, nx), float(spec["value"]))
+    else:
+        raise ValueError("unknown init kind %r" % kind)
+    return np.array(np.broadcast_to(phi, (nz, ny, nx)), dtype=np.float64, order="C")
 
 
 def _nu_from_tau(tau: float) -> float:
@@ -198,3 +229,43 @@ def lups(cfgs, steps: int) -> float:
 def laplace_dp_expected(cfg: dict) -> float:
     """Laplace's law of Sec. 4.2, dP = sigma / R (2-D)."""
     return float(cfg["sigma"]) / float(cfg["init"]["R"])
+
+
+# ----------------------------------------------------------------------------------
+# Three-dimensional (D3Q15) workloads: the same physics with nz planes, x and z
+# periodic, walls (if any) normal to y.
+def static_droplet3(n: int = 32, R: float | None = None, rho_ratio: float = 10.0,
+                    sigma: float = 0.01, W: float = 4.0, tau_g: float = 0.8, tau_h: float = 0.8,
+                    M: float = 0.02, qim: int = 1, pressure: int = 0) -> dict:
+    """Sphere of phase A in phase B, periodic cube (Sec. 4.2 set-up in 3-D;
+    Laplace's law reads Delta p = 2 sigma / R)."""
+    cfg = static_droplet(n=n, R=R, rho_ratio=rho_ratio, sigma=sigma, W=W, tau_g=tau_g,
+                         tau_h=tau_h, M=M, qim=qim, pressure=pressure)
+    cfg["nz"] = n
+    cfg["init"] = dict(kind="droplet", cx=n / 2.0, cy=n / 2.0, cz=n / 2.0, R=cfg["init"]["R"])
+    cfg["name"] = "droplet3_%d_r%g" % (n, rho_ratio)
+    return cfg
+
+
+def layered_poiseuille3(nx: int = 4, ny: int = 64, nz: int = 4, **kw) -> dict:
+    """The layered channel of Sec. 4.3 with nz periodic planes in z."""
+    cfg = layered_poiseuille(nx=nx, ny=ny, **kw)
+    cfg["nz"] = nz
+    cfg["name"] = "layered3_%dx%dx%d" % (nx, ny, nz)
+    return cfg
+
+
+def rising_bubble3(nx: int = 128, ny: int = 256, nz: int = 128, R: float = 24.0,
+                   cy: float = 64.0, **kw) -> dict:
+    """Light sphere in heavy fluid between walls normal to y (the rising-bubble
+    set-up of Sec. 4.4 in 3-D; parameters from Eo and Re as in 2-D)."""
+    cfg = rising_bubble(nx=nx, ny=ny, R=R, cy=cy, **kw)
+    cfg["nz"] = nz
+    cfg["init"] = dict(kind="bubble", cx=nx / 2.0, cy=cy, cz=nz / 2.0, R=R)
+    cfg["name"] = "bubble3_%dx%dx%d_r%g" % (nx, ny, nz, cfg["rho_A"])
+    return cfg
+
+
+def laplace_dp_expected3(cfg: dict) -> float:
+    """Laplace's law for a sphere, Delta p = 2 sigma / R."""
+    return 2.0 * float(cfg["sigma"]) / float(cfg["init"]["R"])
