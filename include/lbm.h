@@ -75,15 +75,23 @@ enum { LBM_VISC_INV_LINEAR = 0, LBM_VISC_STEP = 1 };
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_G16 = 2, LBM_F32_H16 = 3, LBM_F32_C = 4 };
 
 /* Field selection bits for lbm_get_fields*: outputs are written field-major in
- * this bit order, each field nx*ny doubles. P is the Laplace-law pressure of
- * Sec. 4.2, P = p_0 - kappa phi lap(phi) + kappa |grad phi|^2 / 2 + p. */
+ * this bit order, each field nx*ny doubles (nx*ny*nz on a D3Q15 lattice, cell
+ * (x, y, z) at (z * ny + y) * nx + x). P is the Laplace-law pressure of
+ * Sec. 4.2, P = p_0 - kappa phi lap(phi) + kappa |grad phi|^2 / 2 + p. UZ exists
+ * on D3Q15 lattices only. */
 enum {
     LBM_FIELD_PHI = 1, LBM_FIELD_UX = 2, LBM_FIELD_UY = 4, LBM_FIELD_P = 8,
-    LBM_FIELD_RHO = 16, LBM_FIELD_MU = 32, LBM_FIELD_PLAP = 64
+    LBM_FIELD_RHO = 16, LBM_FIELD_MU = 32, LBM_FIELD_PLAP = 64, LBM_FIELD_UZ = 128
 };
 
 /* Parameters of one simulation instance (Sec. 3; values per experiment in Sec. 4).
- * Validation (lbm_create, lbm_validate_params): nx >= 3, ny >= 3, nx*ny < 2^31
+ * nz selects the lattice (Sec. 2.2): 0 or 1, the two-dimensional D2Q9 lattice;
+ * 2 or more, the three-dimensional D3Q15 lattice with nz planes in z (periodic
+ * in x and z; bc_y walls are normal to y; buoyancy along -y; the same model with
+ * d = 3 in Eq. 34 and the printed G_0). A context is all D2Q9 or all D3Q15; the
+ * D3Q15 lattice takes the storage forms LBM_F64, LBM_F32 and LBM_F32_C.
+ * Validation (lbm_create, lbm_validate_params): nx >= 3, ny >= 3, nz >= 0,
+ * nx*ny*max(nz,1) < 2^31
  * (lbm_create: all instances together, each padded to a multiple of 64 cells, < 2^31),
  * rho_A, rho_B, nu_A, nu_B, W > 0, sigma >= 0, mobility >= 0, tau_h > 1/2,
  * every enum in range; all values finite. */
@@ -94,7 +102,7 @@ typedef struct lbm_params {
     int32_t pressure_scheme;  /* LBM_P_*                                                  */
     int32_t surface_force;    /* LBM_FS_*                                                 */
     int32_t viscosity_model;  /* LBM_VISC_*                                               */
-    int32_t reserved;         /* must be 0                                                */
+    int32_t nz;               /* 0 or 1: D2Q9 (2-D); >= 2: D3Q15 with nz planes in z      */
     double rho_A, rho_B;      /* densities of phase A (phi = 1) and phase B (phi = 0)    */
     double nu_A, nu_B;        /* kinematic viscosities; tau_g = nu / c_s^2 + 1/2         */
     double sigma, W;          /* surface tension, interface width: beta = 12 sigma / W,

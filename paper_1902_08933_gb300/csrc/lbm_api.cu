@@ -37,7 +37,10 @@ size_t h_elem(int form) { return form == 0 ? 8 : (form == 3 ? 2 : 4); }
 size_t g_elem(int form) { return form == 0 ? 8 : ((form == 2 || form == 3) ? 2 : 4); }
 size_t a_elem(int form) { return form == 0 ? 8 : 4; }
 bool conservative(int form) { return form >= 2; }
-int h_planes(int form) { return conservative(form) ? 8 : 9; }
+int h_planes(int form, int q = 9) { return conservative(form) ? q - 1 : q; }
+// lattice of an instance: nz >= 2 selects D3Q15 (Sec. 2.2)
+bool is_d3(const lbm_params& p) { return p.nz >= 2; }
+long long cells_of(const lbm_params& p) { return (long long)p.nx * p.ny * (is_d3(p) ? p.nz : 1); }
 
 // Largest power of two s with s * bound <= 2048: keeps FP16-stored values
 // (|v| * s) at least 30x below the FP16 maximum and far above its subnormals.
@@ -56,7 +59,8 @@ bool finite_all(const lbm_params& p) {
 
 const char* check_params(const lbm_params& p) {
     if (p.nx < 3 || p.ny < 3) return "nx and ny must be >= 3";
-    if ((long long)p.nx * p.ny >= (1LL << 31)) return "nx*ny must be < 2^31";
+    if (p.nz < 0) return "nz must be >= 0";
+    if (cells_of(p) >= (1LL << 31)) return "nx*ny*nz must be < 2^31";
     if (p.bc_y != LBM_BC_PERIODIC && p.bc_y != LBM_BC_BOUNCEBACK) return "bc_y out of range";
     if (p.variant != LBM_IM && p.variant != LBM_QIM) return "variant out of range";
     if (p.pressure_scheme < LBM_P_MODIFIED_PRINTED || p.pressure_scheme > LBM_P_PREVIOUS)
@@ -65,7 +69,6 @@ const char* check_params(const lbm_params& p) {
         return "surface_force out of range";
     if (p.viscosity_model != LBM_VISC_INV_LINEAR && p.viscosity_model != LBM_VISC_STEP)
         return "viscosity_model out of range";
-    if (p.reserved != 0) return "reserved must be 0";
     if (!finite_all(p)) return "parameters must be finite";
     if (!(p.rho_A > 0 && p.rho_B > 0)) return "densities must be > 0";
     if (!(p.nu_A > 0 && p.nu_B > 0)) return "viscosities must be > 0";
@@ -83,6 +86,7 @@ DevInst derive(const lbm_params& p, long long base, int form) {
     d.base = base;
     d.nx = p.nx;
     d.ny = p.ny;
+    d.nz = is_d3(p) ? p.nz : 1;
     d.walls = p.bc_y == LBM_BC_BOUNCEBACK;
     d.qim = p.variant == LBM_QIM;
     d.pscheme = p.pressure_scheme;
@@ -122,6 +126,9 @@ DevInst derive(const lbm_params& p, long long base, int form) {
 
 struct lbm_ctx {
     int n = 0, form = 0, device = 0;
+    bool d3 = false;                 // D3Q15 lattice (every instance)
+    int q = 9;                       // populations a set: 9 (D2Q9) or 15 (D3Q15)
+    lbm::D3Scratch sc{nullptr, nullptr, nullptr};   // D3Q15 scratch planes
     std::vector<lbm_params> params;
     std::vector<DevInst> inst;
     std::vector<int64_t> time;
@@ -266,6 +273,15 @@ void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, b
 // share a run boundary read its halo rows at the same time (both at their start
 // or both at their end), from L2 rather than HBM.
 lbm_status plan(lbm_ctx* c) {
+    if (c->d3) {   // D3Q15: three fixed kernels an instance, no work list
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+            c->graph_steps = 0;
+        }
+        c->plan_dirty = false;
+        return LBM_OK;
+    }
     const int tiles[4] = {32, 64, 128, 256};
     auto tile_index = [&](int tx) {
         for (int k = 0; k < 4; ++k)
@@ -422,6 +438,9 @@ void release(lbm_ctx* c) {
         cudaFree(c->p[b]);
     }
     cudaFree(c->phiu);
+    cudaFree(c->sc.phi);
+    cudaFree(c->sc.mu);
+    cudaFree(c->sc.philo);
     cudaFree(c->d_inst);
     cudaFree(c->d_work);
     cudaFree(c->d_tmp);
@@ -442,11 +461,14 @@ void release(lbm_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-int popcount7(unsigned m) {
+int popcount8(unsigned m) {
     int k = 0;
-    for (int b = 0; b < 7; ++b) k += (m >> b) & 1u;
+    for (int b = 0; b < 8; ++b) k += (m >> b) & 1u;
     return k;
 }
+
+// valid field masks: the seven D2Q9 fields, plus uz on D3Q15 lattices
+bool mask_ok(const lbm_ctx* c, unsigned mask) { return mask != 0 && mask < (c->d3 ? 256u : 128u); }
 
 }  // namespace
 
@@ -465,17 +487,23 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     if (precision < 0 || precision >= kForms) return LBM_EINVAL;
     for (int k = 0; k < n_instances; ++k)
         if (check_params(params[k])) return LBM_EINVAL;
+    const bool d3 = is_d3(params[0]);
+    for (int k = 0; k < n_instances; ++k)
+        if (is_d3(params[k]) != d3) return LBM_EINVAL;   // one lattice a context
+    if (d3 && !lbm::d3_form_ok(precision)) return LBM_EINVAL;
 
     // Instance placement: each instance starts on a 64-cell boundary; the kernels
     // index cells with 32-bit integers, so the padded total must stay below 2^31.
     long long total = 0;
     for (int k = 0; k < n_instances; ++k)
-        total += ((long long)params[k].nx * params[k].ny + 63) / 64 * 64;
+        total += (cells_of(params[k]) + 63) / 64 * 64;
     if (total >= (1LL << 31)) return LBM_EINVAL;
 
     lbm_ctx* c = new lbm_ctx();
     c->n = n_instances;
     c->form = precision;
+    c->d3 = d3;
+    c->q = d3 ? 15 : 9;
     c->params.assign(params, params + n_instances);
     c->time.assign(n_instances, 0);
     c->mon_time.assign(n_instances, -1);
@@ -489,7 +517,7 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     long long base = 0;
     for (int k = 0; k < n_instances; ++k) {
         c->inst.push_back(derive(params[k], base, precision));
-        const long long cells = (long long)params[k].nx * params[k].ny;
+        const long long cells = cells_of(params[k]);
         c->max_cells = std::max(c->max_cells, cells);
         base += (cells + 63) / 64 * 64;
     }
@@ -502,14 +530,18 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
     const size_t S = (size_t)c->S;
     for (int b = 0; b < 2; ++b) {
-        if ((e = alloc(&c->h[b], h_planes(precision) * S * h_elem(precision))) != cudaSuccess ||
-            (e = alloc(&c->g[b], 9 * S * g_elem(precision))) != cudaSuccess ||
+        if ((e = alloc(&c->h[b], h_planes(precision, c->q) * S * h_elem(precision))) != cudaSuccess ||
+            (e = alloc(&c->g[b], c->q * S * g_elem(precision))) != cudaSuccess ||
             (e = alloc(&c->p[b], S * a_elem(precision))) != cudaSuccess)
             return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
         if (conservative(precision) && (e = alloc(&c->h0[b], S * 2 * sizeof(float))) != cudaSuccess)
             return cleanup(LBM_ENOMEM);
     }
-    if ((e = alloc(&c->phiu, 2 * S * a_elem(precision))) != cudaSuccess ||
+    if (d3 && ((e = alloc(&c->sc.phi, S * a_elem(precision))) != cudaSuccess ||
+               (e = alloc(&c->sc.mu, S * a_elem(precision))) != cudaSuccess ||
+               (conservative(precision) && (e = alloc((void**)&c->sc.philo, S * sizeof(float))) != cudaSuccess)))
+        return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+    if ((e = alloc(&c->phiu, (d3 ? 3 : 2) * S * a_elem(precision))) != cudaSuccess ||
         (e = alloc((void**)&c->d_inst, n_instances * sizeof(DevInst))) != cudaSuccess ||
         (e = alloc((void**)&c->d_tmp, 2 * (size_t)c->max_cells * sizeof(double))) != cudaSuccess ||
         (e = alloc((void**)&c->d_partials, lbm::kDiagBlocks * lbm::kDiagQuantities * sizeof(double))) !=
@@ -542,11 +574,13 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
 
 static lbm_status init_common(lbm_ctx* c, int instance, const double* phi0_dev) {
     const lbm_params& p = c->params[instance];
-    const int ncells = p.nx * p.ny;
+    const int ncells = (int)cells_of(p);
     StepArgs a = step_args(c, 1 - c->cur);   // writes into the current buffers
-    cudaError_t e = by_form(c->form, [&](auto F) {
-        return lbm::launch_init_t<decltype(F)::value>(a, phi0_dev, instance, ncells, c->stream);
-    });
+    cudaError_t e = c->d3 ? lbm::launch_init3(c->form, a, c->sc, instance, ncells, phi0_dev, c->stream)
+                          : by_form(c->form, [&](auto F) {
+                                return lbm::launch_init_t<decltype(F)::value>(a, phi0_dev, instance, ncells,
+                                                                              c->stream);
+                            });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->time[instance] = 0;
     c->mon_time[instance] = -1;
@@ -563,7 +597,7 @@ lbm_status lbm_init(lbm_ctx* c, int instance, const double* phi0_host) {
     if (!phi0_host) return fail(c, LBM_EINVAL, "phi0 is NULL");
     LBM_CK(c, cudaSetDevice(c->device));
     const lbm_params& p = c->params[instance];
-    const size_t bytes = (size_t)p.nx * p.ny * sizeof(double);
+    const size_t bytes = (size_t)cells_of(p) * sizeof(double);
     LBM_CK(c, cudaMemcpyAsync(c->d_tmp, phi0_host, bytes, cudaMemcpyHostToDevice, c->stream));
     st = init_common(c, instance, c->d_tmp);
     if (st != LBM_OK) return st;
@@ -642,6 +676,14 @@ cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStre
 // Queues one time step (all launches of the plan) reading buffer set `in`; with
 // `monitor` the step kernels also write their monitor slots, reduced per instance.
 cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
+    if (c->d3) {
+        const StepArgs a = step_args(c, in);
+        for (int k = 0; k < c->n; ++k) {
+            cudaError_t e = lbm::launch_step3(c->form, a, c->sc, k, (int)cells_of(c->params[k]), c->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (const auto& L : c->launches) {
         cudaError_t e = enqueue_class(c, in, L, c->stream, monitor);
         if (e != cudaSuccess) return e;
@@ -670,7 +712,7 @@ bool build_graph(lbm_ctx* c) {
         return false;
     // about 64 launches a graph
     const int nl = (int)c->launches.size();
-    const int per_step = std::max(1, nl);
+    const int per_step = c->d3 ? 3 * c->n : std::max(1, nl);
     const int steps = 2 * std::max(1, 32 / per_step);
     if (nl > 1) {
         while ((int)c->side.size() < nl) {
@@ -771,6 +813,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
 
 lbm_status lbm_set_monitor(lbm_ctx* c, int enable) {
     if (!c) return LBM_EINVAL;
+    if (c->d3 && enable) return fail(c, LBM_EINVAL, "the per-step monitor serves D2Q9 contexts");
     LBM_CK(c, cudaSetDevice(c->device));
     if (enable && !c->d_mon) {
         LBM_CK(c, cudaMalloc(&c->d_mon, (size_t)c->n * sizeof(lbm_monitor)));
@@ -821,6 +864,11 @@ lbm_status lbm_set_graphs(lbm_ctx* c, int enable) {
 
 static lbm_status fields_to_device(lbm_ctx* c, int instance, unsigned mask, double* dev_out) {
     const lbm_params& p = c->params[instance];
+    if (c->d3) {
+        cudaError_t e = lbm::launch_fields3(c->form, step_args(c, c->cur), c->sc, instance, (int)cells_of(p),
+                                            mask, dev_out, nullptr, nullptr, c->stream);
+        return e == cudaSuccess ? LBM_OK : cuda_fail(c, e, "fields kernels");
+    }
     AuxArgs a = aux_args(c, instance);
     a.out = dev_out;
     a.mask = mask;
@@ -834,12 +882,12 @@ static lbm_status fields_to_device(lbm_ctx* c, int instance, unsigned mask, doub
 lbm_status lbm_get_fields(lbm_ctx* c, int instance, unsigned mask, double* host_out) {
     lbm_status st = check_instance(c, instance);
     if (st != LBM_OK) return st;
-    if (!host_out || mask == 0 || mask >= 128u) return fail(c, LBM_EINVAL, "bad mask or output");
+    if (!host_out || !mask_ok(c, mask)) return fail(c, LBM_EINVAL, "bad mask or output");
     if (!c->ready[instance]) return fail(c, LBM_ESTATE, "instance not initialised");
     LBM_CK(c, cudaSetDevice(c->device));
     if ((st = sticky(c)) != LBM_OK) return st;
     const lbm_params& p = c->params[instance];
-    const size_t cells = (size_t)p.nx * p.ny * popcount7(mask);
+    const size_t cells = (size_t)cells_of(p) * popcount8(mask);
     if ((st = ensure_out(c, cells)) != LBM_OK) return st;
     if ((st = fields_to_device(c, instance, mask, c->d_out)) != LBM_OK) return st;
     LBM_CK(c, cudaMemcpyAsync(host_out, c->d_out, cells * sizeof(double), cudaMemcpyDeviceToHost,
@@ -851,7 +899,7 @@ lbm_status lbm_get_fields(lbm_ctx* c, int instance, unsigned mask, double* host_
 lbm_status lbm_get_fields_device(lbm_ctx* c, int instance, unsigned mask, double* dev_out) {
     lbm_status st = check_instance(c, instance);
     if (st != LBM_OK) return st;
-    if (!dev_out || mask == 0 || mask >= 128u) return fail(c, LBM_EINVAL, "bad mask or output");
+    if (!dev_out || !mask_ok(c, mask)) return fail(c, LBM_EINVAL, "bad mask or output");
     if (!c->ready[instance]) return fail(c, LBM_ESTATE, "instance not initialised");
     LBM_CK(c, cudaSetDevice(c->device));
     if ((st = sticky(c)) != LBM_OK) return st;
@@ -867,9 +915,12 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int instance, lbm_diag* out) {
     if ((st = sticky(c)) != LBM_OK) return st;
     const lbm_params& p = c->params[instance];
     AuxArgs a = aux_args(c, instance);
-    cudaError_t e = by_form(c->form, [&](auto F) {
-        return lbm::launch_diag_t<decltype(F)::value>(a, p.nx * p.ny, c->stream);
-    });
+    cudaError_t e = c->d3 ? lbm::launch_fields3(c->form, step_args(c, c->cur), c->sc, instance,
+                                                (int)cells_of(p), 0u, nullptr, c->d_partials, c->d_result,
+                                                c->stream)
+                          : by_form(c->form, [&](auto F) {
+                                return lbm::launch_diag_t<decltype(F)::value>(a, p.nx * p.ny, c->stream);
+                            });
     if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernels");
     LBM_CK(c, cudaMemcpyAsync(c->h_result, c->d_result, lbm::kDiagQuantities * sizeof(double),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -904,19 +955,22 @@ lbm_status lbm_get_populations(lbm_ctx* c, int instance, double* host_h, double*
     LBM_CK(c, cudaSetDevice(c->device));
     if ((st = sticky(c)) != LBM_OK) return st;
     const lbm_params& p = c->params[instance];
-    const size_t n = (size_t)p.nx * p.ny;
-    if ((st = ensure_out(c, 18 * n)) != LBM_OK) return st;
+    const size_t n = (size_t)cells_of(p);
+    const size_t q = (size_t)c->q;
+    if ((st = ensure_out(c, 2 * q * n)) != LBM_OK) return st;
     AuxArgs a = aux_args(c, instance);
-    cudaError_t e = by_form(c->form, [&](auto F) {
-        return lbm::launch_populations_t<decltype(F)::value>(a, (int)n, c->d_out, c->d_out + 9 * n,
-                                                             c->stream);
-    });
+    cudaError_t e = c->d3 ? lbm::launch_populations3(c->form, step_args(c, c->cur), c->sc, instance, (int)n,
+                                                     c->d_out, c->d_out + q * n, c->stream)
+                          : by_form(c->form, [&](auto F) {
+                                return lbm::launch_populations_t<decltype(F)::value>(
+                                    a, (int)n, c->d_out, c->d_out + 9 * n, c->stream);
+                            });
     if (e != cudaSuccess) return cuda_fail(c, e, "populations kernel");
     if (host_h)
-        LBM_CK(c, cudaMemcpyAsync(host_h, c->d_out, 9 * n * sizeof(double), cudaMemcpyDeviceToHost,
+        LBM_CK(c, cudaMemcpyAsync(host_h, c->d_out, q * n * sizeof(double), cudaMemcpyDeviceToHost,
                                   c->stream));
     if (host_g)
-        LBM_CK(c, cudaMemcpyAsync(host_g, c->d_out + 9 * n, 9 * n * sizeof(double),
+        LBM_CK(c, cudaMemcpyAsync(host_g, c->d_out + q * n, q * n * sizeof(double),
                                   cudaMemcpyDeviceToHost, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
@@ -930,10 +984,10 @@ struct Segment { void* dev; size_t elem; int planes; };
 
 std::vector<Segment> segments(lbm_ctx* c) {
     std::vector<Segment> s;
-    s.push_back({c->h[c->cur], h_elem(c->form), h_planes(c->form)});
+    s.push_back({c->h[c->cur], h_elem(c->form), h_planes(c->form, c->q)});
     if (conservative(c->form)) s.push_back({c->h0[c->cur], 8, 1});
-    s.push_back({c->g[c->cur], g_elem(c->form), 9});
-    s.push_back({c->phiu, a_elem(c->form), 2});
+    s.push_back({c->g[c->cur], g_elem(c->form), c->q});
+    s.push_back({c->phiu, a_elem(c->form), c->d3 ? 3 : 2});
     s.push_back({c->p[c->cur], a_elem(c->form), 1});
     return s;
 }
@@ -1041,6 +1095,7 @@ lbm_status lbm_set_launch(lbm_ctx* c, int tile_x, int rows) {
 
 lbm_status lbm_autotune(lbm_ctx* c, int* best_tile_x, int* best_rows) {
     if (!c) return LBM_EINVAL;
+    if (c->d3) return fail(c, LBM_EINVAL, "D3Q15 contexts have no launch shape to tune");
     for (int k = 0; k < c->n; ++k)
         if (!c->ready[k]) return fail(c, LBM_ESTATE, "instance not initialised");
     LBM_CK(c, cudaSetDevice(c->device));
@@ -1118,7 +1173,7 @@ int lbm_launches_per_step(const lbm_ctx* c) {
         lbm_ctx* m = const_cast<lbm_ctx*>(c);
         if (cudaSetDevice(m->device) != cudaSuccess || plan(m) != LBM_OK) return 0;
     }
-    return (int)c->launches.size();
+    return c->d3 ? 3 * c->n : (int)c->launches.size();
 }
 
 int64_t lbm_time(const lbm_ctx* c, int instance) {
@@ -1172,6 +1227,7 @@ lbm_status lbm_set_pipeline(lbm_ctx* c, int mode) {
 
 lbm_status lbm_launch_info(lbm_ctx* c, int index, int* tile_x, int* blocks, int* variant) {
     if (!c) return LBM_EINVAL;
+    if (c->d3) return fail(c, LBM_EINVAL, "D3Q15 contexts launch three fixed kernels an instance");
     if (c->plan_dirty) {
         LBM_CK(c, cudaSetDevice(c->device));
         lbm_status st = plan(c);

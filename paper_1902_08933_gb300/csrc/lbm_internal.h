@@ -12,6 +12,7 @@ namespace lbm {
 struct DevInst {
     long long base;          // first cell of the instance inside every SoA plane
     int nx, ny;
+    int nz;                  // D3Q15 contexts: planes in z (periodic); 1 for D2Q9
     int walls;               // 1: halfway bounce-back walls in y
     int qim;                 // 1: S1 = -gamma M lap(mu)
     int pscheme;             // LBM_P_*
@@ -93,5 +94,25 @@ template <int FORM> cudaError_t launch_fields_t(const AuxArgs& a, int ncells, cu
 template <int FORM> cudaError_t launch_diag_t(const AuxArgs& a, int ncells, cudaStream_t s);
 template <int FORM> cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h,
                                                      double* out_g, cudaStream_t s);
+
+// ---- D3Q15 (lbm_d3q15.cu): three kernels a step over each instance's cells.
+// Scratch planes of a 3-D context: phi and mu in the arithmetic type, the low
+// part of phi (conservative form) in FP32.
+struct D3Scratch {
+    void* phi;
+    void* mu;
+    float* philo;
+};
+bool d3_form_ok(int form);   // FP64, FP32, FP32 with the two-float h_0
+cudaError_t launch_step3(int form, const StepArgs& s, const D3Scratch& x, int instance, int ncells,
+                         cudaStream_t st);
+cudaError_t launch_init3(int form, const StepArgs& s, const D3Scratch& x, int instance, int ncells,
+                         const double* phi0, cudaStream_t st);
+// fields (mask bits: phi, ux, uy, p, rho, mu, P, uz) into out (may be null) and,
+// with partials, the kDiagQuantities diagnostics into result
+cudaError_t launch_fields3(int form, const StepArgs& s, const D3Scratch& x, int instance, int ncells,
+                           unsigned mask, double* out, double* partials, double* result, cudaStream_t st);
+cudaError_t launch_populations3(int form, const StepArgs& s, const D3Scratch& x, int instance, int ncells,
+                                double* out_h, double* out_g, cudaStream_t st);
 
 }  // namespace lbm

@@ -30,7 +30,8 @@ LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C = 0, 1, 2, 3, 4
 LBM_PIPELINE_AUTO, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC, LBM_PIPELINE_TMA, LBM_PIPELINE_PAIRS = 0, 1, 2, 3, 4
 VARIANTS = {0: "plain", 1: "async", 2: "tma", 3: "pairs"}
 FIELDS = ("phi", "ux", "uy", "p", "rho", "mu", "P")
-FIELD_BITS = {name: 1 << k for k, name in enumerate(FIELDS)}
+FIELDS3 = FIELDS + ("uz",)          # D3Q15 lattices (nz >= 2) also have uz
+FIELD_BITS = {name: 1 << k for k, name in enumerate(FIELDS3)}
 FORMS = {"f64": LBM_F64, "f32": LBM_F32, "f32_g16": LBM_F32_G16, "f32_h16": LBM_F32_H16,
          "f32_c": LBM_F32_C}
 # bytes moved per lattice update (every population read and written once, plus phi*u, p)
@@ -50,7 +51,7 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("pressure_scheme", ctypes.c_int32),
                 ("surface_force", ctypes.c_int32), ("viscosity_model", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)] + [
+                ("nz", ctypes.c_int32)] + [
         (n, ctypes.c_double) for n in ("rho_A", "rho_B", "nu_A", "nu_B", "sigma", "W", "tau_h",
                                        "mobility", "force_x", "force_y", "gravity")]
 
@@ -139,7 +140,7 @@ def make_params(cfg: dict) -> lbm_params:
     p.pressure_scheme = int(cfg.get("pressure", 0))
     p.surface_force = int(cfg.get("surface_force", 0))
     p.viscosity_model = int(cfg.get("viscosity", 0))
-    p.reserved = 0
+    p.nz = int(cfg.get("nz", 0))
     for k, src in (("rho_A", "rho_A"), ("rho_B", "rho_B"), ("nu_A", "nu_A"), ("nu_B", "nu_B"),
                    ("sigma", "sigma"), ("W", "W"), ("tau_h", "tau_h"), ("mobility", "M"),
                    ("force_x", "force_x"), ("force_y", "force_y"), ("gravity", "gravity")):
@@ -212,9 +213,11 @@ def lbm_diagnostics(ctx, instance) -> dict:
     return out
 
 
-def lbm_get_populations(ctx, instance, nx, ny):
-    h = np.zeros((9, ny, nx))
-    g = np.zeros((9, ny, nx))
+def lbm_get_populations(ctx, instance, nx, ny, nz=0):
+    """h, g in FP64: (9, ny, nx) on D2Q9, (15, nz, ny, nx) on D3Q15 (nz >= 2)."""
+    shape = (15, nz, ny, nx) if nz >= 2 else (9, ny, nx)
+    h = np.zeros(shape)
+    g = np.zeros(shape)
     _check(library().lbm_get_populations(ctx, instance, h.ctypes.data_as(_DP), g.ctypes.data_as(_DP)), ctx)
     return h, g
 
@@ -301,13 +304,20 @@ class Simulation:
     def step(self, n):
         lbm_step(self.ctx, n)
 
-    def fields(self, k=0, names=FIELDS) -> dict:
+    def _shape(self, k):
         c = self.cfgs[k]
+        nz = int(c.get("nz", 0))
+        return (nz, int(c["ny"]), int(c["nx"])) if nz >= 2 else (int(c["ny"]), int(c["nx"]))
+
+    def fields(self, k=0, names=None) -> dict:
+        shape = self._shape(k)
+        if names is None:
+            names = FIELDS3 if len(shape) == 3 else FIELDS
         mask = 0
         for n in names:
             mask |= FIELD_BITS[n]
-        order = [n for n in FIELDS if mask & FIELD_BITS[n]]
-        out = np.zeros((len(order), int(c["ny"]), int(c["nx"])))
+        order = [n for n in FIELDS3 if mask & FIELD_BITS[n]]
+        out = np.zeros((len(order),) + shape)
         lbm_get_fields(self.ctx, k, mask, out)
         return {n: out[i] for i, n in enumerate(order)}
 
@@ -316,7 +326,7 @@ class Simulation:
 
     def populations(self, k=0):
         c = self.cfgs[k]
-        return lbm_get_populations(self.ctx, k, int(c["nx"]), int(c["ny"]))
+        return lbm_get_populations(self.ctx, k, int(c["nx"]), int(c["ny"]), int(c.get("nz", 0)))
 
     def sync(self):
         lbm_sync(self.ctx)

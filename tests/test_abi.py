@@ -46,7 +46,7 @@ def _valid():
 
 @pytest.mark.parametrize("field,value", [
     ("nx", 2), ("ny", 0), ("bc_y", 2), ("variant", 5), ("pressure_scheme", 3),
-    ("surface_force", -1), ("viscosity_model", 2), ("reserved", 1), ("rho_A", 0.0),
+    ("surface_force", -1), ("viscosity_model", 2), ("nz", -1), ("rho_A", 0.0),
     ("rho_B", -1.0), ("nu_A", 0.0), ("W", 0.0), ("sigma", -1e-3), ("tau_h", 0.5),
     ("mobility", -0.1), ("gravity", float("nan")), ("force_x", float("inf"))])
 def test_validation_rejects(L, field, value):
@@ -69,6 +69,18 @@ def test_create_rejects_bad_input_without_touching_cuda(L):
     assert lib.lbm_create(good, 0, 0, None, ctypes.byref(out)) == L.LBM_EINVAL
     assert lib.lbm_create(good, 1, 7, None, ctypes.byref(out)) == L.LBM_EINVAL
     assert lib.lbm_create(good, 1, 0, None, None) == L.LBM_EINVAL
+    # D3Q15 (nz >= 2): one lattice a context, and no FP16 storage forms
+    p3 = _valid()
+    p3.nz = 8
+    assert L.lbm_validate_params(p3) == L.LBM_OK
+    mixed = (L.lbm_params * 2)(_valid(), p3)
+    assert lib.lbm_create(mixed, 2, 0, None, ctypes.byref(out)) == L.LBM_EINVAL
+    only3 = (L.lbm_params * 1)(p3)
+    for form in (L.LBM_F32_G16, L.LBM_F32_H16):
+        assert lib.lbm_create(only3, 1, form, None, ctypes.byref(out)) == L.LBM_EINVAL
+    big = _valid()
+    big.nx, big.ny, big.nz = 2048, 2048, 512
+    assert L.lbm_validate_params(big) == L.LBM_EINVAL     # 2^31 cells
 
 
 def test_null_context_calls_are_errors(L):
