@@ -36,6 +36,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176}
+# D3Q15: 15 + 15 populations, phi u (3), p, each read and written once
+BYTES_PER_LUP_D3 = {"f64": 544, "f32": 272, "f32_c": 280}
 METRIC = "MLUPS and % of HBM peak, FP64 vs FP32/FP16-storage vs batched, at stated error"
 L2_BYTES = 129e6
 
@@ -409,6 +411,20 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     batched["instances"] = len(cfgs)
     batched["cells"] = int(lups_per_step)
     out["batched"] = batched
+
+    # D3Q15: the rising bubble in 3-D, 128 x 256 x 128 (4.2 M cells), three kernels a step
+    cfg3 = wl.rising_bubble3()
+    phi3 = wl.initial_phi(cfg3)
+    cells3 = cfg3["nx"] * cfg3["ny"] * cfg3["nz"]
+    d3 = {"workload": cfg3["name"], "cells": cells3}
+    for form in ("f64", "f32", "f32_c"):
+        with lbm.Simulation(cfg3, form, stream=stream.cuda_stream, phi0=[phi3]) as sim:
+            K3 = max(20, K // (8 if form == "f64" else 2))
+            ms = time_steps(lbm, sim, stream, K3, 6)
+            gbs = BYTES_PER_LUP_D3[form] * cells3 / (ms * 1e-3 / K3) / 1e9
+            d3[form] = {"MLUPS": cells3 * K3 / (ms * 1e-3) / 1e6, "GBps_algorithmic": gbs,
+                        "frac_hbm": gbs / hbm_peak, "steps": K3}
+    out["d3q15"] = d3
 
     # end to end through the C ABI with host buffers: init from pinned host phi0,
     # each step one lbm_step whose kernels also reduce sum(phi), the kinetic energy
