@@ -257,7 +257,11 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
  *  LBM_PIPELINE_AUTO   (default) PAIRS where available, else ASYNC, else TMA,
  *                      else PLAIN.
  * An instance that cannot use a variant falls back to PLAIN. Takes effect at
- * the next lbm_step. LBM_EINVAL for an unknown mode. */
+ * the next lbm_step. LBM_EINVAL for an unknown mode.
+ * D3Q15 contexts: PLAIN runs the unfused step (phi, mu and the collision as
+ * three kernels over each instance, phi and mu through global scratch planes);
+ * every other mode runs the fused step, which marches tiles of 32 x 8 columns
+ * in z with phi, mu and p in shared-memory rings. Both give the same result. */
 enum {
     LBM_PIPELINE_AUTO = 0, LBM_PIPELINE_PLAIN = 1, LBM_PIPELINE_ASYNC = 2, LBM_PIPELINE_TMA = 3,
     LBM_PIPELINE_PAIRS = 4

@@ -272,16 +272,10 @@ void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, b
 // march in opposite directions (down, up, down, ...) so that two blocks that
 // share a run boundary read its halo rows at the same time (both at their start
 // or both at their end), from L2 rather than HBM.
+lbm_status plan_d3(lbm_ctx* c);
+
 lbm_status plan(lbm_ctx* c) {
-    if (c->d3) {   // D3Q15: three fixed kernels an instance, no work list
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-            c->graph_steps = 0;
-        }
-        c->plan_dirty = false;
-        return LBM_OK;
-    }
+    if (c->d3) return plan_d3(c);
     const int tiles[4] = {32, 64, 128, 256};
     auto tile_index = [&](int tx) {
         for (int k = 0; k < 4; ++k)
@@ -391,6 +385,67 @@ lbm_status plan(lbm_ctx* c) {
     LBM_CK(c, cudaMalloc(&c->d_mon_partials, c->work.size() * lbm::kMonQ * sizeof(double)));
     LBM_CK(c, cudaMalloc(&c->d_mon_csr, csr.size() * sizeof(int)));
     LBM_CK(c, cudaMemcpy(c->d_mon_csr, csr.data(), csr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->plan_dirty = false;
+    return LBM_OK;
+}
+
+// D3Q15 work list for the fused march: per instance, tiles of TX x TY columns,
+// each split into runs of planes in z; one instance fills one wave (runs sized
+// so tiles x runs = SMs x resident blocks), several instances about four waves.
+// Neighbouring runs march in opposite directions (halo planes read together).
+lbm_status plan_d3(lbm_ctx* c) {
+    int tx = 32, ty = 8;
+    lbm::march3_tile(&tx, &ty);
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int occ = std::max(1, lbm::march3_occupancy(c->form));
+    long long tile_planes = 0;
+    for (const lbm_params& p : c->params)
+        tile_planes += (long long)((p.nx + tx - 1) / tx) * ((p.ny + ty - 1) / ty) * p.nz;
+    const int batch_rows =
+        (int)std::max<long long>(2, std::min<long long>(64, tile_planes / (4LL * sms * occ)));
+    c->work.clear();
+    for (int k = 0; k < c->n; ++k) {
+        const lbm_params& p = c->params[k];
+        const int tiles_x = (p.nx + tx - 1) / tx, tiles_y = (p.ny + ty - 1) / ty;
+        int rows = c->rows_req;
+        if (rows <= 0) {
+            if (c->n == 1) {
+                const long long target = (long long)sms * occ;
+                const long long runs = std::max<long long>(1, (target + tiles_x * tiles_y - 1) / (tiles_x * tiles_y));
+                rows = (int)std::max<long long>(4, (p.nz + runs - 1) / runs);
+            } else {
+                rows = batch_rows;
+            }
+        }
+        rows = std::min(rows, p.nz);
+        const int nruns = (p.nz + rows - 1) / rows;
+        for (int by = 0; by < tiles_y; ++by)
+            for (int bx = 0; bx < tiles_x; ++bx)
+                for (int r = 0; r < nruns; ++r) {
+                    const int z0 = r * rows, z1 = std::min(p.nz, z0 + rows);
+                    WorkItem w;
+                    w.inst = k;
+                    w.x0 = bx * tx;
+                    w.pad = by * ty;
+                    w.nrows = z1 - z0;
+                    w.dir = (r % 2 == 0) ? -1 : 1;
+                    w.ystart = w.dir < 0 ? z1 - 1 : z0;
+                    c->work.push_back(w);
+                }
+    }
+    c->launches.clear();
+    c->launches.push_back({tx, 0, (int)c->work.size(), -1});
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_steps = 0;
+    }
+    if (c->d_work) cudaFree(c->d_work);
+    c->d_work = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_work, c->work.size() * sizeof(WorkItem)));
+    LBM_CK(c, cudaMemcpy(c->d_work, c->work.data(), c->work.size() * sizeof(WorkItem),
+                         cudaMemcpyHostToDevice));
     c->plan_dirty = false;
     return LBM_OK;
 }
@@ -565,7 +620,8 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     if ((e = cudaMemcpy(c->d_inst, c->inst.data(), n_instances * sizeof(DevInst),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(LBM_ECUDA);
-    e = by_form(precision, [](auto F) { return lbm::prepare_step_t<decltype(F)::value>(); });
+    e = d3 ? lbm::prepare_march3(precision)
+           : by_form(precision, [](auto F) { return lbm::prepare_step_t<decltype(F)::value>(); });
     if (e != cudaSuccess) return cleanup(LBM_ECUDA);
     if (plan(c) != LBM_OK) return cleanup(LBM_ECUDA);
     *out = c;
@@ -678,11 +734,14 @@ cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStre
 cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
     if (c->d3) {
         const StepArgs a = step_args(c, in);
-        for (int k = 0; k < c->n; ++k) {
-            cudaError_t e = lbm::launch_step3(c->form, a, c->sc, k, (int)cells_of(c->params[k]), c->stream);
-            if (e != cudaSuccess) return e;
+        if (c->pipeline == LBM_PIPELINE_PLAIN) {   // the unfused three-kernel step
+            for (int k = 0; k < c->n; ++k) {
+                cudaError_t e = lbm::launch_step3(c->form, a, c->sc, k, (int)cells_of(c->params[k]), c->stream);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
         }
-        return cudaSuccess;
+        return lbm::launch_march3(c->form, a, c->sc, c->d_work, (int)c->work.size(), c->stream);
     }
     for (const auto& L : c->launches) {
         cudaError_t e = enqueue_class(c, in, L, c->stream, monitor);
@@ -712,7 +771,7 @@ bool build_graph(lbm_ctx* c) {
         return false;
     // about 64 launches a graph
     const int nl = (int)c->launches.size();
-    const int per_step = c->d3 ? 3 * c->n : std::max(1, nl);
+    const int per_step = std::max(1, nl);
     const int steps = 2 * std::max(1, 32 / per_step);
     if (nl > 1) {
         while ((int)c->side.size() < nl) {
@@ -1173,7 +1232,7 @@ int lbm_launches_per_step(const lbm_ctx* c) {
         lbm_ctx* m = const_cast<lbm_ctx*>(c);
         if (cudaSetDevice(m->device) != cudaSuccess || plan(m) != LBM_OK) return 0;
     }
-    return c->d3 ? 3 * c->n : (int)c->launches.size();
+    return (c->d3 && c->pipeline == LBM_PIPELINE_PLAIN) ? 3 * c->n : (int)c->launches.size();
 }
 
 int64_t lbm_time(const lbm_ctx* c, int instance) {

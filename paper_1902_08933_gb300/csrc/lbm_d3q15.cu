@@ -216,39 +216,31 @@ __device__ __forceinline__ Macro3<R> macroscopic3(const Consts<R>& C, const R g[
     return m;
 }
 
-// 4 blocks of 256 threads a SM (64 registers): measured on the 128 x 256 x 128
-// bubble, FP32 6.5k -> 8.5k MLUPS against the unbounded 108 registers (2 blocks),
-// the small spill costing less than the latency the extra warps hide.
+// Collision and push-streaming of one cell, given phi (and its low part in the
+// conservative form), mu and the three stencils; loads the cell's own g, h and
+// the previous step's phi u, stores both sets at their destinations, phi u and p.
 template <int FORM>
-__global__ void __launch_bounds__(256, 4) collide3_kernel(const Args a) {
+__device__ __forceinline__ void collide_cell3(const Args& a, const DevInst& P, const Geo& Gm,
+                                              const Consts<typename F3<FORM>::R>& C, int x, int y, int z,
+                                              typename F3<FORM>::R phi, typename F3<FORM>::R phi_lo,
+                                              typename F3<FORM>::R mu,
+                                              const Grad3<typename F3<FORM>::R>& dphi,
+                                              const Grad3<typename F3<FORM>::R>& dmu,
+                                              const Grad3<typename F3<FORM>::R>& dp) {
     using R = typename F3<FORM>::R;
     constexpr bool cons = F3<FORM>::cons;
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= a.ncells) return;
-    const DevInst& P = a.s.inst[a.instance];
-    Geo Gm;
-    Gm.load(P);
-    Consts<R> C;
-    C.load(P);
-    int x, y, z;
-    cell_xyz<FORM>(Gm, cell, x, y, z);
-    const long long c = P.base + cell;
+    const long long c = P.base + ((long long)z * Gm.ny + y) * Gm.nx + x;
     const long long S = a.s.S;
     const R* hin = static_cast<const R*>(a.s.h_in);
     const R* gin = static_cast<const R*>(a.s.g_in);
     R* hout = static_cast<R*>(a.s.h_out);
     R* gout = static_cast<R*>(a.s.g_out);
     R* phiu = static_cast<R*>(a.s.phiu);
-    const R* phi_f = static_cast<const R*>(a.phi);
-    const R* mu_f = static_cast<const R*>(a.mu);
-    const R* p_in = static_cast<const R*>(a.s.p_in);
 
     R g[Q], h[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = gin[(long long)i * S + c];
-    R phi_lo = R(0);
     if constexpr (cons) {
-        phi_lo = a.philo[c];
 #pragma unroll
         for (int i = 1; i < Q; ++i) h[i] = hin[(long long)(i - 1) * S + c];
         h[0] = R(0);   // unused: the conservative h_0 is formed from phi below
@@ -256,12 +248,7 @@ __global__ void __launch_bounds__(256, 4) collide3_kernel(const Args a) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] = hin[(long long)i * S + c];
     }
-    const R phi = phi_f[c], mu = mu_f[c];
-    const Grad3<R> dphi = stencil<R>(phi_f, Gm, x, y, z, phi);
-    const Grad3<R> dmu = stencil<R>(mu_f, Gm, x, y, z, mu);
-    const Grad3<R> dp = stencil<R>(p_in, Gm, x, y, z, p_in[c]);
     const Macro3<R> m = macroscopic3(C, g, phi, mu, dphi, dmu, dp);
-
     const R pu[3] = {phi * m.u[0], phi * m.u[1], phi * m.u[2]};
     const R dpu[3] = {pu[0] - phiu[c], pu[1] - phiu[S + c], pu[2] - phiu[2 * S + c]};
     const R uu = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
@@ -321,6 +308,213 @@ __global__ void __launch_bounds__(256, 4) collide3_kernel(const Args a) {
     phiu[S + c] = pu[1];
     phiu[2 * S + c] = pu[2];
     static_cast<R*>(a.s.p_out)[c] = m.p;
+}
+
+// Unfused step, third kernel (phi and mu from the scratch planes); also the
+// step of LBM_PIPELINE_PLAIN. 4 blocks of 256 threads a SM (64 registers):
+// measured on the 128 x 256 x 128 bubble, FP32 6.5k -> 8.5k MLUPS against the
+// unbounded 108 registers (2 blocks).
+template <int FORM>
+__global__ void __launch_bounds__(256, 4) collide3_kernel(const Args a) {
+    using R = typename F3<FORM>::R;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= a.ncells) return;
+    const DevInst& P = a.s.inst[a.instance];
+    Geo Gm;
+    Gm.load(P);
+    Consts<R> C;
+    C.load(P);
+    int x, y, z;
+    cell_xyz<FORM>(Gm, cell, x, y, z);
+    const long long c = P.base + cell;
+    const R* phi_f = static_cast<const R*>(a.phi);
+    const R* mu_f = static_cast<const R*>(a.mu);
+    const R* p_in = static_cast<const R*>(a.s.p_in);
+    const R phi = phi_f[c], mu = mu_f[c];
+    const R phi_lo = F3<FORM>::cons ? R(a.philo[c]) : R(0);
+    const Grad3<R> dphi = stencil<R>(phi_f, Gm, x, y, z, phi);
+    const Grad3<R> dmu = stencil<R>(mu_f, Gm, x, y, z, mu);
+    const Grad3<R> dp = stencil<R>(p_in, Gm, x, y, z, p_in[c]);
+    collide_cell3<FORM>(a, P, Gm, C, x, y, z, phi, phi_lo, mu, dphi, dmu, dp);
+}
+
+// ---------------------------------------------------------------------------
+// Fused step: a block owns a TX x TY tile of (x, y) columns of one instance and
+// marches in z over a run of planes (direction d = +-1), as the 2-D kernels march
+// rows. Per collision plane Z:
+//   (A) phi of plane Z + 2d over the tile and a 2-cell halo, from the 15 h of
+//       each cell (global memory), into a ring of 8 planes in shared memory;
+//       p of plane Z + 2d (previous step) over the tile and a 1-cell halo;
+//   (B) mu of plane Z + d over the tile and a 1-cell halo, from the phi ring;
+//   (C) the collision of plane Z with the phi, mu and p stencils from shared
+//       memory (collide_cell3 reloads the cell's own h, now in L2).
+// Two barriers a plane; (A) of the next plane writes ring slots that (C) of this
+// plane does not read. Halo cells beyond a wall are the mirror cells (Q7).
+template <int FORM, int TX, int TY>
+struct March3 {
+    using R = typename F3<FORM>::R;
+    static constexpr int PX = TX + 4, PY = TY + 4;   // phi tile + 2-cell halo
+    static constexpr int MX = TX + 2, MY = TY + 2;   // mu / p tile + 1-cell halo
+    static constexpr int NT = TX * TY;
+    // dynamic shared memory: phi ring (8 planes), mu ring (4), p ring (8), low
+    // parts of phi (4 planes of the tile, conservative form)
+    static constexpr size_t PHI = 0;
+    static constexpr size_t MU = PHI + sizeof(R) * 8 * PX * PY;
+    static constexpr size_t PP = MU + sizeof(R) * 4 * MX * MY;
+    static constexpr size_t LO = PP + sizeof(R) * 8 * MX * MY;
+    static constexpr size_t bytes = LO + (F3<FORM>::cons ? sizeof(float) * 4 * NT : 0);
+};
+
+// resident blocks the register budget is sized for: FP32 3 (85 registers), FP64 2
+template <int FORM> constexpr int kMarchOcc = FORM == 0 ? 2 : 3;
+
+template <int FORM, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, kMarchOcc<FORM>) march3_kernel(const Args a,
+                                                                          const WorkItem* __restrict__ work) {
+    using R = typename F3<FORM>::R;
+    using L = March3<FORM, TX, TY>;
+    constexpr int PX = L::PX, PY = L::PY, MX = L::MX, MY = L::MY, NT = L::NT;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    R (*phiR)[PY * PX] = reinterpret_cast<R (*)[PY * PX]>(smem3 + L::PHI);
+    R (*muR)[MY * MX] = reinterpret_cast<R (*)[MY * MX]>(smem3 + L::MU);
+    R (*pR)[MY * MX] = reinterpret_cast<R (*)[MY * MX]>(smem3 + L::PP);
+    float (*loR)[NT] = reinterpret_cast<float (*)[NT]>(smem3 + L::LO);   // conservative form only
+
+    const WorkItem wk = work[blockIdx.x];
+    const DevInst& P = a.s.inst[wk.inst];
+    Geo Gm;
+    Gm.load(P);
+    Consts<R> C;
+    C.load(P);
+    const int x0 = wk.x0, y0 = wk.pad, d = wk.dir;
+    const int wx = min(TX, Gm.nx - x0), wy = min(TY, Gm.ny - y0);
+    const int t = threadIdx.x;
+    const long long S = a.s.S;
+    const R* hin = static_cast<const R*>(a.s.h_in);
+    const R* p_in = static_cast<const R*>(a.s.p_in);
+
+    auto ymap = [&](int y) {   // halo row -> stored row (mirror at walls, wrap otherwise)
+        if (Gm.walls) return y < 0 ? -1 - y : (y >= Gm.ny ? 2 * Gm.ny - 1 - y : y);
+        return Gm.wrap(y, Gm.ny);
+    };
+    auto cellidx = [&](int x, int y, int z) { return P.base + ((long long)z * Gm.ny + y) * Gm.nx + x; };
+    auto slot8 = [](int z) { return (z + 1024) & 7; };
+    auto slot4 = [](int z) { return (z + 1024) & 3; };
+
+    // (A) phi of plane Zl (tile + 2-cell halo), low parts of the tile cells.
+    auto phi_plane = [&](int Zl) {
+        const int zz = Gm.wrap(Zl, Gm.nz);
+        R* dst = phiR[slot8(Zl)];
+        for (int k = t; k < PX * PY; k += NT) {
+            const int hx = k % PX - 2, hy = k / PX - 2;
+            if (hx >= wx + 2 || hy >= wy + 2) continue;
+            const long long c = cellidx(Gm.wrap(x0 + hx, Gm.nx), ymap(y0 + hy), zz);
+            if constexpr (F3<FORM>::cons) {
+                float rest = 0.f;
+#pragma unroll
+                for (int i = 1; i < Q; ++i) rest += hin[(long long)(i - 1) * S + c];
+                const float2 h0 = static_cast<const float2*>(a.s.h0_in)[c];
+                float sm, e, hi, lo;
+                two_sum(h0.x, rest, sm, e);
+                fast_two_sum(sm, e + h0.y, hi, lo);
+                dst[k] = hi;
+                if (hx >= 0 && hx < TX && hy >= 0 && hy < TY) loR[slot4(Zl)][hy * TX + hx] = lo;
+            } else {
+                R sum = hin[c];
+#pragma unroll
+                for (int i = 1; i < Q; ++i) sum += hin[(long long)i * S + c];
+                dst[k] = sum;
+            }
+        }
+    };
+    // p of plane Zp (tile + 1-cell halo); 8 planes: the next plane's (A) writes
+    // p of Z + 3d while lagging threads may still read p of Z - d in (C)
+    auto p_plane = [&](int Zp) {
+        const int zz = Gm.wrap(Zp, Gm.nz);
+        R* dst = pR[slot8(Zp)];
+        for (int k = t; k < MX * MY; k += NT) {
+            const int hx = k % MX - 1, hy = k / MX - 1;
+            if (hx >= wx + 1 || hy >= wy + 1) continue;
+            dst[k] = p_in[cellidx(Gm.wrap(x0 + hx, Gm.nx), ymap(y0 + hy), zz)];
+        }
+    };
+    auto phi_at = [&](int Zc, int hx, int hy) { return phiR[slot8(Zc)][(hy + 2) * PX + hx + 2]; };
+    // (B) mu of plane Zm (tile + 1-cell halo)
+    auto mu_plane = [&](int Zm) {
+        R* dst = muR[slot4(Zm)];
+        for (int k = t; k < MX * MY; k += NT) {
+            const int hx = k % MX - 1, hy = k / MX - 1;
+            if (hx >= wx + 1 || hy >= wy + 1) continue;
+            const R c0 = phi_at(Zm, hx, hy);
+            R lap = R(0);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) lap += R(w(i)) * (phi_at(Zm + cz(i), hx + cx(i), hy + cy(i)) - c0);
+            dst[k] = chem_pot(C, c0, R(6) * lap);
+        }
+    };
+    // Eq. 30 stencils at the tile cell (tx, ty) of plane Zc
+    auto grad_phi = [&](int Zc, int tx, int ty) {
+        Grad3<R> g{R(0), R(0), R(0), R(0)};
+        const R c0 = phi_at(Zc, tx, ty);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const R v = phi_at(Zc + cz(i), tx + cx(i), ty + cy(i));
+            const R wv = R(w(i)) * v;
+            if (cx(i)) g.x += cx(i) > 0 ? wv : -wv;
+            if (cy(i)) g.y += cy(i) > 0 ? wv : -wv;
+            if (cz(i)) g.z += cz(i) > 0 ? wv : -wv;
+            g.lap += R(w(i)) * (v - c0);
+        }
+        g.x *= R(3); g.y *= R(3); g.z *= R(3); g.lap *= R(6);
+        return g;
+    };
+    auto grad_m = [&](R (*ring)[MY * MX], int ring_mask, int Zc, int tx, int ty) {
+        Grad3<R> g{R(0), R(0), R(0), R(0)};
+        auto sl = [&](int z) { return (z + 1024) & ring_mask; };
+        const R c0 = ring[sl(Zc)][(ty + 1) * MX + tx + 1];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const R v = ring[sl(Zc + cz(i))][(ty + 1 + cy(i)) * MX + tx + 1 + cx(i)];
+            const R wv = R(w(i)) * v;
+            if (cx(i)) g.x += cx(i) > 0 ? wv : -wv;
+            if (cy(i)) g.y += cy(i) > 0 ? wv : -wv;
+            if (cz(i)) g.z += cz(i) > 0 ? wv : -wv;
+            g.lap += R(w(i)) * (v - c0);
+        }
+        g.x *= R(3); g.y *= R(3); g.z *= R(3); g.lap *= R(6);
+        return g;
+    };
+
+    const int Z0 = wk.ystart;
+    // prologue: phi of planes Z0-2d .. Z0+d, mu of Z0-d and Z0, p of Z0-d .. Z0+d
+    for (int k = -2; k <= 1; ++k) phi_plane(Z0 + k * d);
+    p_plane(Z0 - d);
+    p_plane(Z0);
+    p_plane(Z0 + d);
+    __syncthreads();
+    mu_plane(Z0 - d);
+    mu_plane(Z0);
+    __syncthreads();
+    const int tx = t % TX, ty = t / TX;
+    const bool act = tx < wx && ty < wy;
+    for (int k = 0; k < wk.nrows; ++k) {
+        const int Z = Z0 + k * d;
+        phi_plane(Z + 2 * d);       // (A)
+        p_plane(Z + 2 * d);
+        __syncthreads();
+        mu_plane(Z + d);            // (B)
+        __syncthreads();
+        if (act) {                  // (C)
+            const R phi = phi_at(Z, tx, ty);
+            const R phi_lo = F3<FORM>::cons ? R(loR[slot4(Z)][ty * TX + tx]) : R(0);
+            const R mu = muR[slot4(Z)][(ty + 1) * MX + tx + 1];
+            const Grad3<R> dphi = grad_phi(Z, tx, ty);
+            const Grad3<R> dmu = grad_m(muR, 3, Z, tx, ty);
+            const Grad3<R> dp = grad_m(pR, 7, Z, tx, ty);
+            collide_cell3<FORM>(a, P, Gm, C, x0 + tx, y0 + ty, Gm.wrap(Z, Gm.nz), phi, phi_lo, mu, dphi, dmu,
+                                dp);
+        }
+    }
 }
 
 // Initial state (reading Q6): h = h^eq(phi0, mu0, u = 0), g = 0 (g^eq at p = 0,
@@ -553,6 +747,46 @@ cudaError_t launch_phi_mu3(int form, const StepArgs& s, const D3Scratch& x, int 
         constexpr int FORM = decltype(F)::value;
         d3::phi3_kernel<FORM><<<d3::blocks_for(ncells), 256, 0, st>>>(a);
         d3::mu3_kernel<FORM><<<d3::blocks_for(ncells), 256, 0, st>>>(a);
+        return cudaGetLastError();
+    });
+}
+
+// tile of the fused march: 32 x 8 columns
+constexpr int kMarchTX = 32, kMarchTY = 8;
+
+void march3_tile(int* tx, int* ty) {
+    *tx = kMarchTX;
+    *ty = kMarchTY;
+}
+
+cudaError_t prepare_march3(int form) {
+    return d3::by_form3(form, [&](auto F) {
+        constexpr int FORM = decltype(F)::value;
+        return cudaFuncSetAttribute(d3::march3_kernel<FORM, kMarchTX, kMarchTY>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)d3::March3<FORM, kMarchTX, kMarchTY>::bytes);
+    });
+}
+
+int march3_occupancy(int form) {
+    int n = 0;
+    d3::by_form3(form, [&](auto F) {
+        constexpr int FORM = decltype(F)::value;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, d3::march3_kernel<FORM, kMarchTX, kMarchTY>,
+                                                             kMarchTX * kMarchTY,
+                                                             d3::March3<FORM, kMarchTX, kMarchTY>::bytes);
+    });
+    return n;
+}
+
+cudaError_t launch_march3(int form, const StepArgs& s, const D3Scratch& x, const WorkItem* work, int nwork,
+                          cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    const d3::Args a = d3::make_args(s, x, 0, 0);
+    return d3::by_form3(form, [&](auto F) {
+        constexpr int FORM = decltype(F)::value;
+        d3::march3_kernel<FORM, kMarchTX, kMarchTY>
+            <<<nwork, kMarchTX * kMarchTY, d3::March3<FORM, kMarchTX, kMarchTY>::bytes, st>>>(a, work);
         return cudaGetLastError();
     });
 }

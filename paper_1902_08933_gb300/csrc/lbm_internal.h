@@ -104,8 +104,16 @@ struct D3Scratch {
     float* philo;
 };
 bool d3_form_ok(int form);   // FP64, FP32, FP32 with the two-float h_0
+// unfused step (phi, mu, collide kernels) of one instance
 cudaError_t launch_step3(int form, const StepArgs& s, const D3Scratch& x, int instance, int ncells,
                          cudaStream_t st);
+// fused step: one launch over a work list of (instance, x0, y0 = pad, z run)
+// items, tiles of march3_tile() columns
+void march3_tile(int* tx, int* ty);
+cudaError_t prepare_march3(int form);
+int march3_occupancy(int form);
+cudaError_t launch_march3(int form, const StepArgs& s, const D3Scratch& x, const WorkItem* work, int nwork,
+                          cudaStream_t st);
 cudaError_t launch_init3(int form, const StepArgs& s, const D3Scratch& x, int instance, int ncells,
                          const double* phi0, cudaStream_t st);
 // fields (mask bits: phi, ux, uy, p, rho, mu, P, uz) into out (may be null) and,
