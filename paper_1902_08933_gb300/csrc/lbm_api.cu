@@ -411,9 +411,16 @@ lbm_status plan_d3(lbm_ctx* c) {
         int rows = c->rows_req;
         if (rows <= 0) {
             if (c->n == 1) {
-                const long long target = (long long)sms * occ;
-                const long long runs = std::max<long long>(1, (target + tiles_x * tiles_y - 1) / (tiles_x * tiles_y));
-                rows = (int)std::max<long long>(4, (p.nz + runs - 1) / runs);
+                // runs per tile column: least (waves) x (planes a run + 2 for the
+                // prologue's four phi and two mu planes), waves counted whole
+                const long long target = (long long)sms * occ, tiles = (long long)tiles_x * tiles_y;
+                long long best = -1, best_cost = 0;
+                for (long long r = 1; r <= p.nz; ++r) {
+                    const long long waves = (tiles * r + target - 1) / target;
+                    const long long cost = waves * ((p.nz + r - 1) / r + 2);
+                    if (best < 0 || cost < best_cost) { best = r; best_cost = cost; }
+                }
+                rows = (int)((p.nz + best - 1) / best);
             } else {
                 rows = batch_rows;
             }

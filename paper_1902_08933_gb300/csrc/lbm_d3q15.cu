@@ -257,6 +257,10 @@ __device__ __forceinline__ void collide_cell3(const Args& a, const DevInst& P, c
     const R ih = C.inv_tau_h, srch = C.src_h;
     const R em = C.eta * mu;
     const bool bot = Gm.walls && y == 0, top = Gm.walls && y == Gm.ny - 1;
+    // destination coordinates for offsets -1, 0, +1 (cell indices fit 32 bits)
+    const int xs[3] = {Gm.wrap(x - 1, Gm.nx), x, Gm.wrap(x + 1, Gm.nx)};
+    const int ys[3] = {Gm.walls ? y - 1 : Gm.wrap(y - 1, Gm.ny), y, Gm.walls ? y + 1 : Gm.wrap(y + 1, Gm.ny)};
+    const int zs[3] = {Gm.wrap(z - 1, Gm.nz), z, Gm.wrap(z + 1, Gm.nz)};
     float rest = 0.f;   // conservative form: sum of the stored h_1 .. h_14
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -284,9 +288,7 @@ __device__ __forceinline__ void collide_cell3(const Args& a, const DevInst& P, c
             dst = c;
             k = opp(i);
         } else {
-            const int xx = Gm.wrap(x + cx(i), Gm.nx), zz = Gm.wrap(z + cz(i), Gm.nz);
-            const int yy = Gm.walls ? y + cy(i) : Gm.wrap(y + cy(i), Gm.ny);
-            dst = P.base + ((long long)zz * Gm.ny + yy) * Gm.nx + xx;
+            dst = P.base + ((zs[cz(i) + 1] * Gm.ny + ys[cy(i) + 1]) * Gm.nx + xs[cx(i) + 1]);
         }
         gout[(long long)k * S + dst] = gpost;
         if constexpr (cons) {
@@ -397,18 +399,44 @@ __global__ void __launch_bounds__(TX * TY, kMarchOcc<FORM>) march3_kernel(const 
         if (Gm.walls) return y < 0 ? -1 - y : (y >= Gm.ny ? 2 * Gm.ny - 1 - y : y);
         return Gm.wrap(y, Gm.ny);
     };
-    auto cellidx = [&](int x, int y, int z) { return P.base + ((long long)z * Gm.ny + y) * Gm.nx + x; };
+    const int plane = Gm.nx * Gm.ny;   // cells of one z plane (instance cells fit 32 bits)
+
+    // Loop-invariant per-thread work of the plane phases: each thread handles at
+    // most two phi cells (tile + 2-cell halo) and two mu / p cells (tile + 1-cell
+    // halo); their in-plane global offsets and ring indices are fixed for the run.
+    constexpr int NA = (PX * PY + NT - 1) / NT, NB = (MX * MY + NT - 1) / NT;
+    static_assert(NA <= 2 && NB <= 2, "tile too small for two cells a thread");
+    int a_yx[NA], a_sm[NA], a_lo[NA];
+    int b_yx[NB], b_sm[NB], b_phi[NB];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const int k = t + j * NT;
+        const int hx = k % PX - 2, hy = k / PX - 2;
+        const bool ok = k < PX * PY && hx < wx + 2 && hy < wy + 2;
+        a_sm[j] = ok ? k : -1;
+        a_yx[j] = ok ? ymap(y0 + hy) * Gm.nx + Gm.wrap(x0 + hx, Gm.nx) : 0;
+        a_lo[j] = (ok && hx >= 0 && hx < TX && hy >= 0 && hy < TY) ? hy * TX + hx : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const int k = t + j * NT;
+        const int hx = k % MX - 1, hy = k / MX - 1;
+        const bool ok = k < MX * MY && hx < wx + 1 && hy < wy + 1;
+        b_sm[j] = ok ? k : -1;
+        b_yx[j] = ok ? ymap(y0 + hy) * Gm.nx + Gm.wrap(x0 + hx, Gm.nx) : 0;
+        b_phi[j] = (hy + 2) * PX + hx + 2;
+    }
     auto slot8 = [](int z) { return (z + 1024) & 7; };
     auto slot4 = [](int z) { return (z + 1024) & 3; };
 
     // (A) phi of plane Zl (tile + 2-cell halo), low parts of the tile cells.
     auto phi_plane = [&](int Zl) {
-        const int zz = Gm.wrap(Zl, Gm.nz);
+        const long long zb = P.base + (long long)Gm.wrap(Zl, Gm.nz) * plane;
         R* dst = phiR[slot8(Zl)];
-        for (int k = t; k < PX * PY; k += NT) {
-            const int hx = k % PX - 2, hy = k / PX - 2;
-            if (hx >= wx + 2 || hy >= wy + 2) continue;
-            const long long c = cellidx(Gm.wrap(x0 + hx, Gm.nx), ymap(y0 + hy), zz);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (a_sm[j] < 0) continue;
+            const long long c = zb + a_yx[j];
             if constexpr (F3<FORM>::cons) {
                 float rest = 0.f;
 #pragma unroll
@@ -417,72 +445,62 @@ __global__ void __launch_bounds__(TX * TY, kMarchOcc<FORM>) march3_kernel(const 
                 float sm, e, hi, lo;
                 two_sum(h0.x, rest, sm, e);
                 fast_two_sum(sm, e + h0.y, hi, lo);
-                dst[k] = hi;
-                if (hx >= 0 && hx < TX && hy >= 0 && hy < TY) loR[slot4(Zl)][hy * TX + hx] = lo;
+                dst[a_sm[j]] = hi;
+                if (a_lo[j] >= 0) loR[slot4(Zl)][a_lo[j]] = lo;
             } else {
                 R sum = hin[c];
 #pragma unroll
                 for (int i = 1; i < Q; ++i) sum += hin[(long long)i * S + c];
-                dst[k] = sum;
+                dst[a_sm[j]] = sum;
             }
         }
     };
     // p of plane Zp (tile + 1-cell halo); 8 planes: the next plane's (A) writes
     // p of Z + 3d while lagging threads may still read p of Z - d in (C)
     auto p_plane = [&](int Zp) {
-        const int zz = Gm.wrap(Zp, Gm.nz);
+        const long long zb = P.base + (long long)Gm.wrap(Zp, Gm.nz) * plane;
         R* dst = pR[slot8(Zp)];
-        for (int k = t; k < MX * MY; k += NT) {
-            const int hx = k % MX - 1, hy = k / MX - 1;
-            if (hx >= wx + 1 || hy >= wy + 1) continue;
-            dst[k] = p_in[cellidx(Gm.wrap(x0 + hx, Gm.nx), ymap(y0 + hy), zz)];
-        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (b_sm[j] >= 0) dst[b_sm[j]] = p_in[zb + b_yx[j]];
     };
-    auto phi_at = [&](int Zc, int hx, int hy) { return phiR[slot8(Zc)][(hy + 2) * PX + hx + 2]; };
+    // 14-neighbour Eq. 30 stencil over three ring planes (z - 1, z, z + 1) at a
+    // ring index; the neighbour offsets are compile-time
+    auto stencil_ring = [&](const R* zm, const R* z0, const R* zp, int at, int rowlen) {
+        Grad3<R> g{R(0), R(0), R(0), R(0)};
+        const R c0 = z0[at];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const R* pl = cz(i) < 0 ? zm : (cz(i) > 0 ? zp : z0);
+            const R v = pl[at + cy(i) * rowlen + cx(i)];
+            const R wv = R(w(i)) * v;
+            if (cx(i)) g.x += cx(i) > 0 ? wv : -wv;
+            if (cy(i)) g.y += cy(i) > 0 ? wv : -wv;
+            if (cz(i)) g.z += cz(i) > 0 ? wv : -wv;
+            g.lap += R(w(i)) * (v - c0);
+        }
+        g.x *= R(3); g.y *= R(3); g.z *= R(3); g.lap *= R(6);
+        return g;
+    };
     // (B) mu of plane Zm (tile + 1-cell halo)
     auto mu_plane = [&](int Zm) {
         R* dst = muR[slot4(Zm)];
-        for (int k = t; k < MX * MY; k += NT) {
-            const int hx = k % MX - 1, hy = k / MX - 1;
-            if (hx >= wx + 1 || hy >= wy + 1) continue;
-            const R c0 = phi_at(Zm, hx, hy);
+        const R* f0 = phiR[slot8(Zm - 1)];
+        const R* f1 = phiR[slot8(Zm)];
+        const R* f2 = phiR[slot8(Zm + 1)];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (b_sm[j] < 0) continue;
+            const int at = b_phi[j];
+            const R c0 = f1[at];
             R lap = R(0);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) lap += R(w(i)) * (phi_at(Zm + cz(i), hx + cx(i), hy + cy(i)) - c0);
-            dst[k] = chem_pot(C, c0, R(6) * lap);
+            for (int i = 1; i < Q; ++i) {
+                const R* pl = cz(i) < 0 ? f0 : (cz(i) > 0 ? f2 : f1);
+                lap += R(w(i)) * (pl[at + cy(i) * PX + cx(i)] - c0);
+            }
+            dst[b_sm[j]] = chem_pot(C, c0, R(6) * lap);
         }
-    };
-    // Eq. 30 stencils at the tile cell (tx, ty) of plane Zc
-    auto grad_phi = [&](int Zc, int tx, int ty) {
-        Grad3<R> g{R(0), R(0), R(0), R(0)};
-        const R c0 = phi_at(Zc, tx, ty);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const R v = phi_at(Zc + cz(i), tx + cx(i), ty + cy(i));
-            const R wv = R(w(i)) * v;
-            if (cx(i)) g.x += cx(i) > 0 ? wv : -wv;
-            if (cy(i)) g.y += cy(i) > 0 ? wv : -wv;
-            if (cz(i)) g.z += cz(i) > 0 ? wv : -wv;
-            g.lap += R(w(i)) * (v - c0);
-        }
-        g.x *= R(3); g.y *= R(3); g.z *= R(3); g.lap *= R(6);
-        return g;
-    };
-    auto grad_m = [&](R (*ring)[MY * MX], int ring_mask, int Zc, int tx, int ty) {
-        Grad3<R> g{R(0), R(0), R(0), R(0)};
-        auto sl = [&](int z) { return (z + 1024) & ring_mask; };
-        const R c0 = ring[sl(Zc)][(ty + 1) * MX + tx + 1];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const R v = ring[sl(Zc + cz(i))][(ty + 1 + cy(i)) * MX + tx + 1 + cx(i)];
-            const R wv = R(w(i)) * v;
-            if (cx(i)) g.x += cx(i) > 0 ? wv : -wv;
-            if (cy(i)) g.y += cy(i) > 0 ? wv : -wv;
-            if (cz(i)) g.z += cz(i) > 0 ? wv : -wv;
-            g.lap += R(w(i)) * (v - c0);
-        }
-        g.x *= R(3); g.y *= R(3); g.z *= R(3); g.lap *= R(6);
-        return g;
     };
 
     const int Z0 = wk.ystart;
@@ -497,6 +515,7 @@ __global__ void __launch_bounds__(TX * TY, kMarchOcc<FORM>) march3_kernel(const 
     __syncthreads();
     const int tx = t % TX, ty = t / TX;
     const bool act = tx < wx && ty < wy;
+    const int at_phi = (ty + 2) * PX + tx + 2, at_m = (ty + 1) * MX + tx + 1;
     for (int k = 0; k < wk.nrows; ++k) {
         const int Z = Z0 + k * d;
         phi_plane(Z + 2 * d);       // (A)
@@ -505,12 +524,13 @@ __global__ void __launch_bounds__(TX * TY, kMarchOcc<FORM>) march3_kernel(const 
         mu_plane(Z + d);            // (B)
         __syncthreads();
         if (act) {                  // (C)
-            const R phi = phi_at(Z, tx, ty);
+            const R* f1 = phiR[slot8(Z)];
+            const R phi = f1[at_phi];
             const R phi_lo = F3<FORM>::cons ? R(loR[slot4(Z)][ty * TX + tx]) : R(0);
-            const R mu = muR[slot4(Z)][(ty + 1) * MX + tx + 1];
-            const Grad3<R> dphi = grad_phi(Z, tx, ty);
-            const Grad3<R> dmu = grad_m(muR, 3, Z, tx, ty);
-            const Grad3<R> dp = grad_m(pR, 7, Z, tx, ty);
+            const R mu = muR[slot4(Z)][at_m];
+            const Grad3<R> dphi = stencil_ring(phiR[slot8(Z - 1)], f1, phiR[slot8(Z + 1)], at_phi, PX);
+            const Grad3<R> dmu = stencil_ring(muR[slot4(Z - 1)], muR[slot4(Z)], muR[slot4(Z + 1)], at_m, MX);
+            const Grad3<R> dp = stencil_ring(pR[slot8(Z - 1)], pR[slot8(Z)], pR[slot8(Z + 1)], at_m, MX);
             collide_cell3<FORM>(a, P, Gm, C, x0 + tx, y0 + ty, Gm.wrap(Z, Gm.nz), phi, phi_lo, mu, dphi, dmu,
                                 dp);
         }
