@@ -330,9 +330,19 @@ lbm_status plan(lbm_ctx* c) {
                     occ = lbm::step_occupancy_t<decltype(F)::value>(tx, variant);
                     return cudaSuccess;
                 });
+                // runs per strip: least (waves) x (rows a run + 3 for the prologue),
+                // waves counted whole -- one exact wave where the strips allow it
                 const long long target = (long long)sms * std::max(occ, 1);
-                const long long chunks = std::max<long long>(1, (target + strips - 1) / strips);
-                rows = (int)std::max<long long>(8, (p.ny + chunks - 1) / chunks);
+                long long best = -1, best_cost = 0;
+                for (long long r = 1; r <= p.ny; ++r) {
+                    const long long rr = (p.ny + r - 1) / r;
+                    if (rr < 8 && r > 1) break;   // runs of at least 8 rows
+                    const long long runs = (p.ny + rr - 1) / rr;
+                    const long long waves = (strips * runs + target - 1) / target;
+                    const long long cost = waves * (rr + 3);
+                    if (best < 0 || cost < best_cost) { best = rr; best_cost = cost; }
+                }
+                rows = (int)best;
             } else {
                 rows = batch_rows;
             }
