@@ -131,6 +131,29 @@ int    orc3_fields(const orc_params* P, int nz, const double* h, const double* g
 int    orc3_diagnostics(const orc_params* P, int nz, const double* h, const double* g,
                         const double* p_prev, orc_diag* out);
 
+/* ---- single-phase model of Remark 3 (Sec. 2.3): incompressible flow with a
+ * mass source S(x) (div u = S), rho~ = rho_0, rho = 1, D2Q9; oracle_sp.c ---- */
+typedef struct {
+    int nx, ny;
+    int walls_y;          /* 0 periodic in y, 1 halfway bounce-back walls        */
+    double nu;            /* kinematic viscosity: tau_g = nu / c_s^2 + 1/2       */
+    double xi;            /* bulk viscosity in Q = (2/d) rho c_s^2 - xi/(tau_g - 1/2) */
+    double force_x, force_y;
+    double rho0;          /* rho~ = rho_0 of the equilibrium                     */
+} orc_sp_params;
+
+double orc_sp_tau(const orc_sp_params* P);
+void   orc_sp_geq(double p, double ux, double uy, double rho0, double* geq);
+void   orc_sp_force(const orc_sp_params* P, double S, double Fx, double Fy, double ux, double uy,
+                    double* G);
+void   orc_sp_moments(const orc_sp_params* P, const double* g, double S, double* ux, double* uy,
+                      double* p);
+int    orc_sp_init(const orc_sp_params* P, double* g);
+/* S: source field, nx*ny; g: 9 planes of nx*ny */
+int    orc_sp_step(const orc_sp_params* P, const double* S, double* g, int nsteps);
+int    orc_sp_fields(const orc_sp_params* P, const double* S, const double* g, double* ux, double* uy,
+                     double* p);
+
 /* Analytic layered Poiseuille profile, Eq. 37: y measured from the interface,
  * walls at y = -hh and y = +hh, dynamic viscosity mu_up for 0 < y <= hh and
  * mu_down for -hh <= y <= 0 (Eq. 37 names them mu_A and mu_B). */

@@ -21,6 +21,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 SRC3 = os.path.join(HERE, "oracle3d.c")
+SRCSP = os.path.join(HERE, "oracle_sp.c")
 HDR = os.path.join(HERE, "oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
 
@@ -59,17 +60,23 @@ class Diag(ctypes.Structure):
         ("nonfinite", ctypes.c_int)]
 
 
+class SpParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls_y", ctypes.c_int),
+                ("nu", ctypes.c_double), ("xi", ctypes.c_double), ("force_x", ctypes.c_double),
+                ("force_y", ctypes.c_double), ("rho0", ctypes.c_double)]
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (FP contraction off, so a*b+c rounds twice
     exactly as written). Rebuilds when the sources are newer than the library."""
     with _lock:
         stale = (not os.path.exists(LIB) or
                  os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(SRC3),
-                                             os.path.getmtime(HDR)))
+                                             os.path.getmtime(SRCSP), os.path.getmtime(HDR)))
         if force or stale:
             tmp = LIB + ".tmp.%d" % os.getpid()
             cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-                   "-shared", "-std=c11", SRC, SRC3, "-o", tmp, "-lm"]
+                   "-shared", "-std=c11", SRC, SRC3, SRCSP, "-o", tmp, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, LIB)
     return LIB
@@ -125,6 +132,15 @@ def lib():
         L.orc3_step.argtypes = [P, ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int]
         L.orc3_fields.argtypes = [P, ctypes.c_int, _DP, _DP, _DP] + [_DP] * 8
         L.orc3_diagnostics.argtypes = [P, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(Diag)]
+        SP = ctypes.POINTER(SpParams)
+        L.orc_sp_tau.argtypes = [SP]
+        L.orc_sp_tau.restype = ctypes.c_double
+        L.orc_sp_geq.argtypes = [ctypes.c_double] * 4 + [_DP]
+        L.orc_sp_force.argtypes = [SP] + [ctypes.c_double] * 5 + [_DP]
+        L.orc_sp_moments.argtypes = [SP, _DP, ctypes.c_double, _DP, _DP, _DP]
+        L.orc_sp_init.argtypes = [SP, _DP]
+        L.orc_sp_step.argtypes = [SP, _DP, _DP, ctypes.c_int]
+        L.orc_sp_fields.argtypes = [SP, _DP, _DP, _DP, _DP, _DP]
         _lib = L
     return _lib
 
@@ -398,3 +414,54 @@ def diagnostics3(P: Params, st: dict) -> dict:
     if rc:
         raise ValueError("orc3_diagnostics failed (%d)" % rc)
     return {k: getattr(D, k) for k, _ in Diag._fields_}
+
+
+# ------------------------------------------------- single-phase model of Remark 3
+def sp_params(cfg: dict) -> SpParams:
+    P = SpParams()
+    P.nx, P.ny, P.walls_y = int(cfg["nx"]), int(cfg["ny"]), int(cfg.get("walls_y", 0))
+    P.nu, P.xi = float(cfg["nu"]), float(cfg.get("xi", 0.0))
+    P.force_x, P.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))
+    P.rho0 = float(cfg.get("rho0", 0.0))
+    return P
+
+
+def sp_geq(p, ux, uy, rho0=0.0):
+    out = np.zeros(9)
+    lib().orc_sp_geq(p, ux, uy, rho0, _ptr(out))
+    return out
+
+
+def sp_force(P: SpParams, S, Fx, Fy, ux, uy):
+    out = np.zeros(9)
+    lib().orc_sp_force(ctypes.byref(P), S, Fx, Fy, ux, uy, _ptr(out))
+    return out
+
+
+def sp_moments(P: SpParams, g, S):
+    ux, uy, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().orc_sp_moments(ctypes.byref(P), _ptr(np.ascontiguousarray(g, dtype=np.float64)), S,
+                         ctypes.cast(ctypes.byref(ux), _DP), ctypes.cast(ctypes.byref(uy), _DP),
+                         ctypes.cast(ctypes.byref(p), _DP))
+    return ux.value, uy.value, p.value
+
+
+def sp_init(P: SpParams) -> np.ndarray:
+    g = np.zeros((9, P.ny, P.nx))
+    lib().orc_sp_init(ctypes.byref(P), _ptr(g))
+    return g
+
+
+def sp_step(P: SpParams, S, g, n: int):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    rc = lib().orc_sp_step(ctypes.byref(P), _ptr(S), _ptr(g), int(n))
+    if rc:
+        raise ValueError("orc_sp_step failed (%d)" % rc)
+    return g
+
+
+def sp_fields(P: SpParams, S, g) -> dict:
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    out = {k: np.zeros((P.ny, P.nx)) for k in ("ux", "uy", "p")}
+    lib().orc_sp_fields(ctypes.byref(P), _ptr(S), _ptr(g), _ptr(out["ux"]), _ptr(out["uy"]), _ptr(out["p"]))
+    return out

@@ -1,0 +1,148 @@
+/*
+ * oracle_sp.c -- plain FP64 CPU oracle of the single-phase model of Remark 3
+ * (Sec. 2.3) of arXiv:1902.08933: the generalized lattice Boltzmann model with
+ * rho~ = rho_0 and a constant density rho (= 1), which recovers the
+ * incompressible Navier-Stokes equations with a mass source,
+ *   div u = S,
+ *   d_t u + div(u u) = -grad p + div[nu (grad u + grad u^T)] + div[-(2/3) nu div u I] + F.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h). Build: gcc -O2 -ffp-contract=off.
+ *
+ * One time step on the D2Q9 lattice (Sec. 2.2), following Remark 3:
+ *   u = sum_i c_i g_i + F/2                                   (Eq. 27a, rho = 1)
+ *   G_i = w_i { S + c_i.F / c_s^2
+ *              + (c_i c_i - c_s^2 I) : (u F + F u + Q S I) / (2 c_s^4) },
+ *   Q = (2/d) rho c_s^2 - xi / (tau_g - 1/2)                  (after Eq. 27)
+ *   p = c_s^2 / (1 - w_0) [ sum_{i != 0} g_i + S/2 + s_0(u) + (tau_g - 1/2) G_0 ]   (Eq. 28)
+ *   g_i^eq = rho_0 + (p / c_s^2)(w_0 - 1) + s_0(u)  (i = 0),  (p / c_s^2) w_i + s_i(u)  (i != 0)
+ *   g_i(x + c_i, t + 1) = g_i - (g_i - g_i^eq) / tau_g + (1 - 1/(2 tau_g)) G_i   (Eq. 24)
+ * with tau_g = nu / c_s^2 + 1/2, a source field S(x) and a uniform force F;
+ * x periodic, y periodic or halfway bounce-back walls. Layout as oracle.c.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define QS 9
+static const int SX[QS] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int SY[QS] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double SW[QS] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double SCS2 = 1.0 / 3.0;
+
+static int sp_opposite(int i) {
+    for (int k = 0; k < QS; ++k)
+        if (SX[k] == -SX[i] && SY[k] == -SY[i]) return k;
+    return -1;
+}
+
+static double sp_s(int i, double ux, double uy) {
+    const double cu = SX[i] * ux + SY[i] * uy, uu = ux * ux + uy * uy;
+    return SW[i] * (cu / SCS2 + cu * cu / (2.0 * SCS2 * SCS2) - uu / (2.0 * SCS2));
+}
+
+double orc_sp_tau(const orc_sp_params* P) { return P->nu / SCS2 + 0.5; }
+
+/* Remark 3 equilibrium (Eq. 25 with rho~ = rho_0, rho = 1). */
+void orc_sp_geq(double p, double ux, double uy, double rho0, double* geq) {
+    for (int i = 0; i < QS; ++i)
+        geq[i] = (i == 0 ? rho0 + p / SCS2 * (SW[0] - 1.0) : p / SCS2 * SW[i]) + sp_s(i, ux, uy);
+}
+
+/* Remark 3 force distribution, the contraction written out over alpha, beta. */
+void orc_sp_force(const orc_sp_params* P, double S, double Fx, double Fy, double ux, double uy,
+                  double* G) {
+    const double rho = 1.0, tau = orc_sp_tau(P);
+    const double Qc = (2.0 / 2.0) * rho * SCS2 - P->xi / (tau - 0.5);
+    const double u[2] = {ux, uy}, F[2] = {Fx, Fy};
+    double A[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) A[a][b] = u[a] * F[b] + F[a] * u[b] + (a == b ? Qc * S : 0.0);
+    for (int i = 0; i < QS; ++i) {
+        const double c[2] = {(double)SX[i], (double)SY[i]};
+        double contraction = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) contraction += (c[a] * c[b] - (a == b ? SCS2 : 0.0)) * A[a][b];
+        G[i] = SW[i] * (S + (c[0] * Fx + c[1] * Fy) / SCS2 + contraction / (2.0 * SCS2 * SCS2));
+    }
+}
+
+/* u (Eq. 27a) and p (Eq. 28) of one cell from its populations. */
+void orc_sp_moments(const orc_sp_params* P, const double* g, double S, double* ux, double* uy,
+                    double* p) {
+    double jx = 0.0, jy = 0.0, rest = 0.0;
+    for (int i = 0; i < QS; ++i) {
+        jx += SX[i] * g[i];
+        jy += SY[i] * g[i];
+        if (i) rest += g[i];
+    }
+    *ux = jx + 0.5 * P->force_x;
+    *uy = jy + 0.5 * P->force_y;
+    double G[QS];
+    orc_sp_force(P, S, P->force_x, P->force_y, *ux, *uy, G);
+    const double tau = orc_sp_tau(P);
+    *p = SCS2 / (1.0 - SW[0]) * (rest + 0.5 * S + sp_s(0, *ux, *uy) + (tau - 0.5) * G[0]);
+}
+
+int orc_sp_init(const orc_sp_params* P, double* g) {
+    const long N = (long)P->nx * P->ny;
+    double geq[QS];
+    orc_sp_geq(0.0, 0.0, 0.0, P->rho0, geq);
+    for (int i = 0; i < QS; ++i)
+        for (long c = 0; c < N; ++c) g[i * N + c] = geq[i];
+    return 0;
+}
+
+int orc_sp_step(const orc_sp_params* P, const double* S, double* g, int nsteps) {
+    const int nx = P->nx, ny = P->ny;
+    const long N = (long)nx * ny;
+    const double tau = orc_sp_tau(P);
+    double* post = (double*)malloc((size_t)(QS * N) * sizeof(double));
+    if (!post) return 2;
+    for (int step = 0; step < nsteps; ++step) {
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < N; ++c) {
+            double gc[QS], geq[QS], G[QS], ux, uy, p;
+            for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
+            orc_sp_moments(P, gc, S[c], &ux, &uy, &p);
+            orc_sp_geq(p, ux, uy, P->rho0, geq);
+            orc_sp_force(P, S[c], P->force_x, P->force_y, ux, uy, G);
+            for (int i = 0; i < QS; ++i)
+                post[i * N + c] = gc[i] - (gc[i] - geq[i]) / tau + (1.0 - 1.0 / (2.0 * tau)) * G[i];
+        }
+        /* streaming (pull), halfway bounce-back at y walls */
+        for (int i = 0; i < QS; ++i) {
+            const int oi = sp_opposite(i);
+#pragma omp parallel for schedule(static)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const long here = (long)y * nx + x;
+                    const int ys = y - SY[i];
+                    if (P->walls_y && (ys < 0 || ys >= ny)) {
+                        g[i * N + here] = post[oi * N + here];
+                    } else {
+                        const int xs = ((x - SX[i]) % nx + nx) % nx, yw = (ys % ny + ny) % ny;
+                        g[i * N + here] = post[i * N + (long)yw * nx + xs];
+                    }
+                }
+        }
+    }
+    free(post);
+    return 0;
+}
+
+int orc_sp_fields(const orc_sp_params* P, const double* S, const double* g, double* ux, double* uy,
+                  double* p) {
+    const long N = (long)P->nx * P->ny;
+    for (long c = 0; c < N; ++c) {
+        double gc[QS], a, b, q;
+        for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
+        orc_sp_moments(P, gc, S[c], &a, &b, &q);
+        if (ux) ux[c] = a;
+        if (uy) uy[c] = b;
+        if (p) p[c] = q;
+    }
+    return 0;
+}

@@ -1,0 +1,104 @@
+"""Pins of the oracle of Remark 3 (Sec. 2.3): the generalized model with
+rho~ = rho_0 and constant density, the incompressible Navier-Stokes equations
+with a mass source (div u = S).
+
+Checked against the moment conditions the remark's equilibrium and force term
+must meet (App. A with rho = 1), pressure recovery from Eq. 28, a closed-form
+steady flow with a sinusoidal mass source (div u = S fixes u; second-order
+convergence), the body-force Poiseuille profile with S = 0 (Guo's model, as
+the remark notes), and exact translation equivariance.
+"""
+import numpy as np
+import pytest
+
+CS2 = 1.0 / 3.0
+RNG = np.random.default_rng(33)
+C = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], dtype=float)
+
+
+def test_remark3_equilibrium_moments(orc):
+    for rho0 in (0.0, 1.0):
+        for _ in range(4):
+            p = RNG.uniform(-1e-2, 1e-2)
+            u = RNG.uniform(-0.05, 0.05, 2)
+            g = orc.sp_geq(p, u[0], u[1], rho0)
+            assert np.isclose(g.sum(), rho0, atol=1e-15)
+            assert np.allclose(g @ C, u, atol=1e-16)
+            assert np.allclose(np.einsum("i,ia,ib->ab", g, C, C), p * np.eye(2) + np.outer(u, u), atol=1e-15)
+
+
+@pytest.mark.parametrize("xi", [0.0, 0.05])
+def test_remark3_force_moments(orc, xi):
+    P = orc.sp_params(dict(nx=4, ny=4, nu=0.1, xi=xi))
+    tau = 0.1 / CS2 + 0.5
+    Q = CS2 - xi / (tau - 0.5)
+    for _ in range(4):
+        S = RNG.uniform(-1e-3, 1e-3)
+        F = RNG.uniform(-1e-4, 1e-4, 2)
+        u = RNG.uniform(-0.05, 0.05, 2)
+        G = orc.sp_force(P, S, F[0], F[1], u[0], u[1])
+        assert np.isclose(G.sum(), S, atol=1e-18)
+        assert np.allclose(G @ C, F, atol=1e-18)
+        M2 = np.einsum("i,ia,ib->ab", G, C, C)
+        assert np.allclose(M2, CS2 * S * np.eye(2) + np.outer(u, F) + np.outer(F, u) + Q * S * np.eye(2),
+                           atol=1e-18)
+
+
+def test_remark3_pressure_recovery(orc):
+    # g = g^eq(p, u), F = 0: Eq. 28 returns p + c_s^2/(1 - w_0) (S/2 + (tau - 1/2) G_0)
+    P = orc.sp_params(dict(nx=4, ny=4, nu=0.1))
+    tau = 0.1 / CS2 + 0.5
+    for _ in range(4):
+        p, S = RNG.uniform(-1e-2, 1e-2), RNG.uniform(-1e-3, 1e-3)
+        u = RNG.uniform(-0.05, 0.05, 2)
+        g = orc.sp_geq(p, u[0], u[1], 0.0)
+        ux, uy, pout = orc.sp_moments(P, g, S)
+        G0 = orc.sp_force(P, S, 0.0, 0.0, u[0], u[1])[0]
+        assert np.allclose([ux, uy], u, atol=1e-17)
+        assert np.isclose(pout, p + 0.6 * (0.5 * S + (tau - 0.5) * G0), atol=1e-16)
+
+
+def _source_flow_error(orc, nx, steps=80000):
+    P = orc.sp_params(dict(nx=nx, ny=2, nu=0.1))
+    k, A = 2 * np.pi / nx, 1e-4
+    x = np.arange(nx)
+    S = np.tile(A * np.sin(k * x), (2, 1))
+    g = orc.sp_init(P)
+    orc.sp_step(P, S, g, steps)
+    f = orc.sp_fields(P, S, g)
+    ua = -(A / k) * np.cos(k * x)              # div u = S, zero mean momentum
+    return np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua)), f
+
+
+def test_mass_source_flow_closed_form(orc):
+    e32, f32 = _source_flow_error(orc, 32)
+    e64, _ = _source_flow_error(orc, 64)
+    assert np.abs(f32["uy"]).max() == 0.0
+    assert e64 < 1e-3
+    assert 3.5 < e32 / e64 < 4.5               # second order in space
+
+
+def test_poiseuille_without_source(orc):
+    # S = 0: Guo's incompressible model; body-force Poiseuille flow between
+    # halfway walls at y = -1/2 and ny - 1/2. BGK with halfway bounce-back
+    # reproduces the parabola exactly at tau = 1/2 + sqrt(3/16) (elsewhere the
+    # walls slip by a tau-dependent multiple of F)
+    ny, F = 24, 1e-6
+    nu = CS2 * np.sqrt(3.0 / 16.0)
+    P = orc.sp_params(dict(nx=2, ny=ny, walls_y=1, nu=nu, force_x=F))
+    S = np.zeros((ny, 2))
+    g = orc.sp_init(P)
+    orc.sp_step(P, S, g, 30000)
+    ux = orc.sp_fields(P, S, g)["ux"][:, 0]
+    y = np.arange(ny)
+    ua = F / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux - ua)) / ua.max() < 1e-11
+
+
+def test_translation_equivariance_sp(orc):
+    P = orc.sp_params(dict(nx=12, ny=10, nu=0.05, force_x=1e-5, force_y=-2e-5))
+    S = RNG.uniform(-1e-3, 1e-3, (10, 12))
+    a, b = orc.sp_init(P), orc.sp_init(P)
+    orc.sp_step(P, S, a, 20)
+    orc.sp_step(P, np.roll(S, (3, 5), axis=(0, 1)), b, 20)
+    assert np.array_equal(np.roll(a, (3, 5), axis=(1, 2)), b)
