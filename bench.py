@@ -426,6 +426,28 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
                         "frac_hbm": gbs / hbm_peak, "steps": K3}
     out["d3q15"] = d3
 
+    # single-phase model of Remark 3 (div u = S): 4096 x 4096, sinusoidal source
+    import numpy as np
+    n = 4096
+    src = np.ascontiguousarray(1e-4 * np.sin(2 * np.pi * np.arange(n) / n)[None, :] * np.ones((n, 1)))
+    sp = {"workload": "source_flow_4096x4096", "cells": n * n}
+    for form, bpl in (("f64", 152), ("f32", 76)):
+        with lbm.SourceFlow(dict(nx=n, ny=n, nu=0.1), form, stream=stream.cuda_stream, source=src) as sim:
+            sim.step(4)
+            torch.cuda.synchronize()
+            Ks = max(20, K // 4)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(Ks)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            gbs = bpl * n * n / (ms * 1e-3 / Ks) / 1e9
+            sp[form] = {"MLUPS": n * n * Ks / (ms * 1e-3) / 1e6, "GBps_algorithmic": gbs,
+                        "frac_hbm": gbs / hbm_peak, "bytes_per_lup": bpl, "steps": Ks}
+    out["source_flow"] = sp
+
     # end to end through the C ABI with host buffers: init from pinned host phi0,
     # each step one lbm_step whose kernels also reduce sum(phi), the kinetic energy
     # and max |u| (the per-step monitor), that record read to the host, the

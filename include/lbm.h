@@ -343,6 +343,49 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 /* Releases the context and all its device memory. NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 
+/* ---- single-phase model of Remark 3 (Sec. 2.3) ---------------------------
+ * The generalized model with rho~ = rho_0 and a constant density (rho = 1):
+ * incompressible Navier-Stokes flow with a mass source, div u = S(x), and a
+ * uniform body force F, on the D2Q9 lattice (x periodic; y periodic or halfway
+ * bounce-back walls). Equilibrium of Remark 3 (g_0 stored shifted by rho_0),
+ * force term w_i{S + c.F/c_s^2 + (cc - c_s^2 I):(uF + Fu + Q S I)/(2 c_s^4)}
+ * with Q = (2/d) c_s^2 - xi/(tau_g - 1/2), u by Eq. 27a (rho = 1), p by Eq. 28,
+ * BGK of Eq. 24 with tau_g = nu / c_s^2 + 1/2. One kernel a step. */
+typedef struct lbm_sp_params {
+    int32_t nx, ny;
+    int32_t bc_y;             /* LBM_BC_*                                                */
+    int32_t reserved;         /* must be 0                                                */
+    double nu;                /* kinematic viscosity (> 0)                               */
+    double xi;                /* bulk viscosity in Q (>= 0; 0 under Stokes' hypothesis)  */
+    double force_x, force_y;  /* uniform body force                                       */
+} lbm_sp_params;
+
+typedef struct lbm_sp_ctx lbm_sp_ctx;
+
+/* Creates one single-phase simulation; precision LBM_F64 or LBM_F32 (storage
+ * and arithmetic). nx, ny >= 3, 9 nx ny < 2^31. cuda_stream as lbm_create.
+ * Errors: LBM_EINVAL (no CUDA call made), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_stream,
+                         lbm_sp_ctx** out);
+
+/* Sets the source field S (host array of nx*ny doubles, copied; constant in
+ * time) and the state at rest (u = 0, p = 0). Resets the time. Synchronises. */
+lbm_status lbm_sp_init(lbm_sp_ctx* ctx, const double* source_host);
+
+/* Advances nsteps time steps (asynchronous). LBM_ESTATE before lbm_sp_init. */
+lbm_status lbm_sp_step(lbm_sp_ctx* ctx, int nsteps);
+
+/* u and p (Eq. 27a, Eq. 28) at the current time: mask of LBM_FIELD_UX,
+ * LBM_FIELD_UY, LBM_FIELD_P; host_out receives popcount(mask) * nx * ny doubles
+ * in that order. Synchronises. */
+lbm_status lbm_sp_get_fields(lbm_sp_ctx* ctx, unsigned mask, double* host_out);
+
+/* The 9 population planes in FP64 (g_0 shifted by rho_0). Synchronises. */
+lbm_status lbm_sp_get_populations(lbm_sp_ctx* ctx, double* host_g);
+
+const char* lbm_sp_last_error(const lbm_sp_ctx* ctx);
+void lbm_sp_destroy(lbm_sp_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

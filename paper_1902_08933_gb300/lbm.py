@@ -70,6 +70,12 @@ class lbm_monitor(ctypes.Structure):
                 ("device_status", ctypes.c_int32), ("time", ctypes.c_int64)]
 
 
+class lbm_sp_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("nu", ctypes.c_double), ("xi", ctypes.c_double),
+                ("force_x", ctypes.c_double), ("force_y", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 _VP = ctypes.c_void_p
@@ -105,6 +111,14 @@ SIGNATURES = [
     ("lbm_sync", ctypes.c_int, [_VP]),
     ("lbm_last_error", ctypes.c_char_p, [_VP]),
     ("lbm_destroy", None, [_VP]),
+    ("lbm_sp_create", ctypes.c_int, [ctypes.POINTER(lbm_sp_params), ctypes.c_int, _VP,
+                                     ctypes.POINTER(_VP)]),
+    ("lbm_sp_init", ctypes.c_int, [_VP, _DP]),
+    ("lbm_sp_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_sp_get_fields", ctypes.c_int, [_VP, ctypes.c_uint, _DP]),
+    ("lbm_sp_get_populations", ctypes.c_int, [_VP, _DP]),
+    ("lbm_sp_last_error", ctypes.c_char_p, [_VP]),
+    ("lbm_sp_destroy", None, [_VP]),
 ]
 
 
@@ -334,6 +348,70 @@ class Simulation:
     def close(self):
         if self.ctx:
             lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- single-phase model of Remark 3 (incompressible flow with a mass source) ----
+def _check_sp(st, ctx=None):
+    if st != LBM_OK:
+        msg = library().lbm_sp_last_error(ctx).decode() if ctx else ""
+        raise LbmError(st, msg)
+
+
+class SourceFlow:
+    """One single-phase simulation of Remark 3 (div u = S) on the GPU."""
+
+    def __init__(self, cfg: dict, precision="f64", stream=None, source=None):
+        p = lbm_sp_params()
+        p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
+        p.bc_y = int(cfg.get("walls_y", 0))
+        p.reserved = 0
+        p.nu, p.xi = float(cfg["nu"]), float(cfg.get("xi", 0.0))
+        p.force_x, p.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))
+        self.nx, self.ny = p.nx, p.ny
+        prec = FORMS[precision] if isinstance(precision, str) else int(precision)
+        out = _VP()
+        st = library().lbm_sp_create(ctypes.byref(p), prec, _VP(stream or 0), ctypes.byref(out))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_sp_create")
+        self.ctx = out
+        if source is not None:
+            self.init(source)
+
+    def init(self, source):
+        S = np.ascontiguousarray(source, dtype=np.float64)
+        assert S.shape == (self.ny, self.nx)
+        _check_sp(library().lbm_sp_init(self.ctx, S.ctypes.data_as(_DP)), self.ctx)
+
+    def step(self, n):
+        _check_sp(library().lbm_sp_step(self.ctx, int(n)), self.ctx)
+
+    def fields(self) -> dict:
+        out = np.zeros((3, self.ny, self.nx))
+        mask = FIELD_BITS["ux"] | FIELD_BITS["uy"] | FIELD_BITS["p"]
+        _check_sp(library().lbm_sp_get_fields(self.ctx, mask, out.ctypes.data_as(_DP)), self.ctx)
+        return {"ux": out[0], "uy": out[1], "p": out[2]}
+
+    def populations(self):
+        g = np.zeros((9, self.ny, self.nx))
+        _check_sp(library().lbm_sp_get_populations(self.ctx, g.ctypes.data_as(_DP)), self.ctx)
+        return g
+
+    def close(self):
+        if self.ctx:
+            library().lbm_sp_destroy(self.ctx)
             self.ctx = None
 
     def __enter__(self):

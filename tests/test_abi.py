@@ -78,6 +78,18 @@ def test_create_rejects_bad_input_without_touching_cuda(L):
     only3 = (L.lbm_params * 1)(p3)
     for form in (L.LBM_F32_G16, L.LBM_F32_H16):
         assert lib.lbm_create(only3, 1, form, None, ctypes.byref(out)) == L.LBM_EINVAL
+    # the single-phase model of Remark 3
+    sp = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
+    spo = ctypes.c_void_p(1234)
+    for field, value in (("nx", 2), ("bc_y", 5), ("reserved", 1), ("nu", 0.0), ("xi", -1.0),
+                         ("force_x", float("nan"))):
+        bad = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
+        setattr(bad, field, value)
+        assert lib.lbm_sp_create(ctypes.byref(bad), 0, None, ctypes.byref(spo)) == L.LBM_EINVAL
+        assert spo.value is None
+    assert lib.lbm_sp_create(ctypes.byref(sp), L.LBM_F32_C, None, ctypes.byref(spo)) == L.LBM_EINVAL
+    assert lib.lbm_sp_step(None, 1) == L.LBM_EINVAL and lib.lbm_sp_init(None, None) == L.LBM_EINVAL
+    lib.lbm_sp_destroy(None)
     big = _valid()
     big.nx, big.ny, big.nz = 2048, 2048, 512
     assert L.lbm_validate_params(big) == L.LBM_EINVAL     # 2^31 cells

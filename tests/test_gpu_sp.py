@@ -1,0 +1,69 @@
+"""GPU single-phase model of Remark 3 (div u = S) versus its FP64 oracle, and
+the closed-form checks of its oracle pins run on the GPU path."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+CS2 = 1.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_08933_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def rel(a, b):
+    den = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
+
+
+@pytest.mark.parametrize("walls,xi", [(0, 0.0), (1, 0.0), (0, 0.05), (1, 0.05)])
+def test_matches_oracle(L, orc, walls, xi):
+    cfg = dict(nx=37, ny=23, walls_y=walls, nu=0.07, xi=xi, force_x=2e-6, force_y=-1e-6)
+    S = 1e-4 * np.sin(2 * np.pi * np.arange(37) / 37)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
+    S = np.ascontiguousarray(S)
+    P = orc.sp_params(cfg)
+    g = orc.sp_init(P)
+    orc.sp_step(P, S, g, 40)
+    ref = orc.sp_fields(P, S, g)
+    with L.SourceFlow(cfg, "f64", source=S) as sim:
+        sim.step(40)
+        got, gg = sim.fields(), sim.populations()
+    assert rel(gg, g) < 1e-12
+    for k in ("ux", "uy", "p"):
+        assert rel(got[k], ref[k]) < 1e-12, k
+    with L.SourceFlow(cfg, "f32", source=S) as sim:
+        sim.step(40)
+        got = sim.fields()
+    for k in ("ux", "uy", "p"):
+        assert rel(got[k], ref[k]) < 1e-4, (k, rel(got[k], ref[k]))
+
+
+@pytest.mark.parametrize("form,bar", [("f64", 1e-3), ("f32", 1e-3)])
+def test_mass_source_flow_closed_form(L, report, form, bar):
+    nx, A = 64, 1e-4
+    k = 2 * np.pi / nx
+    S = np.ascontiguousarray(np.tile(A * np.sin(k * np.arange(nx)), (2, 1)))
+    with L.SourceFlow(dict(nx=nx, ny=3, nu=0.1), form, source=np.tile(S[0], (3, 1))) as sim:
+        sim.step(80000)
+        f = sim.fields()
+    ua = -(A / k) * np.cos(k * np.arange(nx))
+    err = np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua))
+    report(err=err)
+    assert err < bar
+
+
+def test_poiseuille_exact_at_the_magic_tau(L):
+    ny, F = 24, 1e-6
+    nu = CS2 * np.sqrt(3.0 / 16.0)
+    with L.SourceFlow(dict(nx=3, ny=ny, walls_y=1, nu=nu, force_x=F), "f64", source=np.zeros((ny, 3))) as sim:
+        sim.step(30000)
+        ux = sim.fields()["ux"][:, 0]
+    y = np.arange(ny)
+    ua = F / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux - ua)) / ua.max() < 1e-11
