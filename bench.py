@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--form", default="f32_c", choices=list(BYTES_PER_LUP))
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs"],
                     help="load path of the step kernel (lbm_set_pipeline)")
+    ap.add_argument("--kernel-run", default=None, choices=["bubble3d", "source_flow"],
+                    help="only time one step loop of another workload (for profiling): the "
+                         "128 x 256 x 128 D3Q15 bubble or the 4096 x 4096 Remark 3 source flow")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the side-by-side forms, e2e and CPU legs")
     return ap.parse_args()
@@ -261,10 +264,48 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------- GPU arm
+def kernel_run(args):
+    """Times args.steps steps of one secondary workload after args.warmup
+    warm-up steps and prints one line (used to profile those kernels)."""
+    import numpy as np
+    import torch
+    from paper_1902_08933_gb300 import build, lbm
+    from paper_1902_08933_gb300 import workloads as wl
+    build.build()
+    stream = torch.cuda.Stream()
+    if args.kernel_run == "bubble3d":
+        cfg = wl.rising_bubble3()
+        cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+        form = args.form if args.form in BYTES_PER_LUP_D3 else "f32_c"
+        sim = lbm.Simulation(cfg, form, stream=stream.cuda_stream, phi0=[wl.initial_phi(cfg)])
+        bpl = BYTES_PER_LUP_D3[form]
+    else:
+        n = 4096
+        cells = n * n
+        src = np.ascontiguousarray(1e-4 * np.sin(2 * np.pi * np.arange(n) / n)[None, :] * np.ones((n, 1)))
+        form = "f64" if args.form == "f64" else "f32"
+        sim = lbm.SourceFlow(dict(nx=n, ny=n, nu=0.1), form, stream=stream.cuda_stream, source=src)
+        bpl = 152 if form == "f64" else 76
+    sim.step(max(args.warmup, 2))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"kernel_run": args.kernel_run, "form": form, "ms_per_step": ms,
+                      "MLUPS": cells / ms / 1e3, "GBps_algorithmic": bpl * cells / ms / 1e6}))
+    sim.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_run:
+        return kernel_run(args)
     import numpy as np
     import torch
 
