@@ -153,6 +153,16 @@ int    orc_sp_init(const orc_sp_params* P, double* g);
 int    orc_sp_step(const orc_sp_params* P, const double* S, double* g, int nsteps);
 int    orc_sp_fields(const orc_sp_params* P, const double* S, const double* g, double* ux, double* uy,
                      double* p);
+/* Remark 1, the nearly incompressible form (rho~ = rho, p = rho c_s^2): */
+void   orc_sp1_moments(const orc_sp_params* P, const double* g, double S, double* rho, double* ux,
+                       double* uy);
+void   orc_sp1_force(const orc_sp_params* P, double S, double rho, double ux, double uy, double divu,
+                     double* G);
+void   orc_sp1_geq(double rho, double ux, double uy, double* geq);
+int    orc_sp1_init(const orc_sp_params* P, double rho_init, double* g);
+int    orc_sp1_step(const orc_sp_params* P, const double* S, double* g, int nsteps);
+int    orc_sp1_fields(const orc_sp_params* P, const double* S, const double* g, double* rho,
+                      double* ux, double* uy);
 
 /* Analytic layered Poiseuille profile, Eq. 37: y measured from the interface,
  * walls at y = -hh and y = +hh, dynamic viscosity mu_up for 0 < y <= hh and

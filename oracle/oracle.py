@@ -141,6 +141,12 @@ def lib():
         L.orc_sp_init.argtypes = [SP, _DP]
         L.orc_sp_step.argtypes = [SP, _DP, _DP, ctypes.c_int]
         L.orc_sp_fields.argtypes = [SP, _DP, _DP, _DP, _DP, _DP]
+        L.orc_sp1_moments.argtypes = [SP, _DP, ctypes.c_double, _DP, _DP, _DP]
+        L.orc_sp1_force.argtypes = [SP] + [ctypes.c_double] * 5 + [_DP]
+        L.orc_sp1_geq.argtypes = [ctypes.c_double] * 3 + [_DP]
+        L.orc_sp1_init.argtypes = [SP, ctypes.c_double, _DP]
+        L.orc_sp1_step.argtypes = [SP, _DP, _DP, ctypes.c_int]
+        L.orc_sp1_fields.argtypes = [SP, _DP, _DP, _DP, _DP, _DP]
         _lib = L
     return _lib
 
@@ -464,4 +470,38 @@ def sp_fields(P: SpParams, S, g) -> dict:
     S = np.ascontiguousarray(S, dtype=np.float64)
     out = {k: np.zeros((P.ny, P.nx)) for k in ("ux", "uy", "p")}
     lib().orc_sp_fields(ctypes.byref(P), _ptr(S), _ptr(g), _ptr(out["ux"]), _ptr(out["uy"]), _ptr(out["p"]))
+    return out
+
+
+# ------------------------------------------------- Remark 1 (nearly incompressible)
+def sp1_geq(rho, ux, uy):
+    out = np.zeros(9)
+    lib().orc_sp1_geq(rho, ux, uy, _ptr(out))
+    return out
+
+
+def sp1_force(P: SpParams, S, rho, ux, uy, divu):
+    out = np.zeros(9)
+    lib().orc_sp1_force(ctypes.byref(P), S, rho, ux, uy, divu, _ptr(out))
+    return out
+
+
+def sp1_init(P: SpParams, rho_init=1.0) -> np.ndarray:
+    g = np.zeros((9, P.ny, P.nx))
+    lib().orc_sp1_init(ctypes.byref(P), rho_init, _ptr(g))
+    return g
+
+
+def sp1_step(P: SpParams, S, g, n: int):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    rc = lib().orc_sp1_step(ctypes.byref(P), _ptr(S), _ptr(g), int(n))
+    if rc:
+        raise ValueError("orc_sp1_step failed (%d)" % rc)
+    return g
+
+
+def sp1_fields(P: SpParams, S, g) -> dict:
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    out = {k: np.zeros((P.ny, P.nx)) for k in ("rho", "ux", "uy")}
+    lib().orc_sp1_fields(ctypes.byref(P), _ptr(S), _ptr(g), _ptr(out["rho"]), _ptr(out["ux"]), _ptr(out["uy"]))
     return out

@@ -18,6 +18,16 @@
  *   g_i(x + c_i, t + 1) = g_i - (g_i - g_i^eq) / tau_g + (1 - 1/(2 tau_g)) G_i   (Eq. 24)
  * with tau_g = nu / c_s^2 + 1/2, a source field S(x) and a uniform force F;
  * x periodic, y periodic or halfway bounce-back walls. Layout as oracle.c.
+ *
+ * model = 1: the nearly incompressible form of Remark 1 (rho~ = rho, p = rho c_s^2):
+ *   rho = sum_i g_i + S/2                                     (Eq. 27aa)
+ *   u = (sum_i c_i g_i + F/2) / rho                           (Eq. 27a)
+ *   g_i^eq = rho (w_i + s_i(u))                               (Eq. 29bb)
+ *   G_i = w_i { S + c_i.F / c_s^2
+ *              + (c_i c_i - c_s^2 I) : (u F + F u - u u S + Q div(u) I) / (2 c_s^4) },
+ *   Q = (2/d) rho c_s^2 - xi / (tau_g - 1/2),
+ * div u by the isotropic gradient of Eq. 30a (mirror at walls, reading Q7);
+ * the u u S term is kept as printed.
  */
 #include "oracle.h"
 
@@ -84,6 +94,133 @@ void orc_sp_moments(const orc_sp_params* P, const double* g, double S, double* u
     orc_sp_force(P, S, P->force_x, P->force_y, *ux, *uy, G);
     const double tau = orc_sp_tau(P);
     *p = SCS2 / (1.0 - SW[0]) * (rest + 0.5 * S + sp_s(0, *ux, *uy) + (tau - 0.5) * G[0]);
+}
+
+/* ---- Remark 1 ---- */
+static double sp_at(const orc_sp_params* P, const double* f, int x, int y) {
+    const int nx = P->nx, ny = P->ny;
+    x = ((x % nx) + nx) % nx;
+    if (P->walls_y) {
+        if (y < 0) y = -1 - y;
+        if (y >= ny) y = 2 * ny - 1 - y;
+    } else {
+        y = ((y % ny) + ny) % ny;
+    }
+    return f[(long)y * nx + x];
+}
+
+/* rho (Eq. 27aa) and u (Eq. 27a) of one cell. */
+void orc_sp1_moments(const orc_sp_params* P, const double* g, double S, double* rho, double* ux, double* uy) {
+    double m0 = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < QS; ++i) {
+        m0 += g[i];
+        jx += SX[i] * g[i];
+        jy += SY[i] * g[i];
+    }
+    *rho = m0 + 0.5 * S;
+    *ux = (jx + 0.5 * P->force_x) / *rho;
+    *uy = (jy + 0.5 * P->force_y) / *rho;
+}
+
+/* Remark 1 force distribution with div u supplied. */
+void orc_sp1_force(const orc_sp_params* P, double S, double rho, double ux, double uy, double divu,
+                   double* G) {
+    const double tau = orc_sp_tau(P);
+    const double Qc = (2.0 / 2.0) * rho * SCS2 - P->xi / (tau - 0.5);
+    const double u[2] = {ux, uy}, F[2] = {P->force_x, P->force_y};
+    double A[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            A[a][b] = u[a] * F[b] + F[a] * u[b] - u[a] * u[b] * S + (a == b ? Qc * divu : 0.0);
+    for (int i = 0; i < QS; ++i) {
+        const double c[2] = {(double)SX[i], (double)SY[i]};
+        double contraction = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) contraction += (c[a] * c[b] - (a == b ? SCS2 : 0.0)) * A[a][b];
+        G[i] = SW[i] * (S + (c[0] * F[0] + c[1] * F[1]) / SCS2 + contraction / (2.0 * SCS2 * SCS2));
+    }
+}
+
+/* Eq. 29bb. */
+void orc_sp1_geq(double rho, double ux, double uy, double* geq) {
+    for (int i = 0; i < QS; ++i) geq[i] = rho * (SW[i] + sp_s(i, ux, uy));
+}
+
+int orc_sp1_init(const orc_sp_params* P, double rho_init, double* g) {
+    const long N = (long)P->nx * P->ny;
+    double geq[QS];
+    orc_sp1_geq(rho_init, 0.0, 0.0, geq);
+    for (int i = 0; i < QS; ++i)
+        for (long c = 0; c < N; ++c) g[i * N + c] = geq[i];
+    return 0;
+}
+
+int orc_sp1_step(const orc_sp_params* P, const double* S, double* g, int nsteps) {
+    const int nx = P->nx, ny = P->ny;
+    const long N = (long)nx * ny;
+    const double tau = orc_sp_tau(P);
+    double* post = (double*)malloc((size_t)(QS * N) * sizeof(double));
+    double* rho = (double*)malloc((size_t)N * sizeof(double));
+    double* ux = (double*)malloc((size_t)N * sizeof(double));
+    double* uy = (double*)malloc((size_t)N * sizeof(double));
+    if (!post || !rho || !ux || !uy) {
+        free(post); free(rho); free(ux); free(uy);
+        return 2;
+    }
+    for (int step = 0; step < nsteps; ++step) {
+        /* rho and u on the whole grid first (div u needs the neighbours') */
+        for (long c = 0; c < N; ++c) {
+            double gc[QS];
+            for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
+            orc_sp1_moments(P, gc, S[c], &rho[c], &ux[c], &uy[c]);
+        }
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < N; ++c) {
+            const int x = (int)(c % nx), y = (int)(c / nx);
+            double divu = 0.0;   /* Eq. 30a applied to u */
+            for (int i = 1; i < QS; ++i)
+                divu += SW[i] * (SX[i] * sp_at(P, ux, x + SX[i], y + SY[i]) +
+                                 SY[i] * sp_at(P, uy, x + SX[i], y + SY[i])) / SCS2;
+            double geq[QS], G[QS];
+            orc_sp1_geq(rho[c], ux[c], uy[c], geq);
+            orc_sp1_force(P, S[c], rho[c], ux[c], uy[c], divu, G);
+            for (int i = 0; i < QS; ++i) {
+                const double gi = g[i * N + c];
+                post[i * N + c] = gi - (gi - geq[i]) / tau + (1.0 - 1.0 / (2.0 * tau)) * G[i];
+            }
+        }
+        for (int i = 0; i < QS; ++i) {
+            const int oi = sp_opposite(i);
+#pragma omp parallel for schedule(static)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const long here = (long)y * nx + x;
+                    const int ys = y - SY[i];
+                    if (P->walls_y && (ys < 0 || ys >= ny)) {
+                        g[i * N + here] = post[oi * N + here];
+                    } else {
+                        const int xs = ((x - SX[i]) % nx + nx) % nx, yw = (ys % ny + ny) % ny;
+                        g[i * N + here] = post[i * N + (long)yw * nx + xs];
+                    }
+                }
+        }
+    }
+    free(post); free(rho); free(ux); free(uy);
+    return 0;
+}
+
+int orc_sp1_fields(const orc_sp_params* P, const double* S, const double* g, double* rho, double* ux,
+                   double* uy) {
+    const long N = (long)P->nx * P->ny;
+    for (long c = 0; c < N; ++c) {
+        double gc[QS], r, a, b;
+        for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
+        orc_sp1_moments(P, gc, S[c], &r, &a, &b);
+        if (rho) rho[c] = r;
+        if (ux) ux[c] = a;
+        if (uy) uy[c] = b;
+    }
+    return 0;
 }
 
 int orc_sp_init(const orc_sp_params* P, double* g) {

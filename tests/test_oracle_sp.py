@@ -102,3 +102,53 @@ def test_translation_equivariance_sp(orc):
     orc.sp_step(P, S, a, 20)
     orc.sp_step(P, np.roll(S, (3, 5), axis=(0, 1)), b, 20)
     assert np.array_equal(np.roll(a, (3, 5), axis=(1, 2)), b)
+
+
+# ---------------------------------------------------------------- Remark 1
+def test_remark1_equilibrium_and_force_moments(orc):
+    P = orc.sp_params(dict(nx=4, ny=4, nu=0.1, xi=0.02, force_x=3e-5, force_y=-1e-5))
+    tau = 0.1 / CS2 + 0.5
+    F = np.array([3e-5, -1e-5])
+    for _ in range(4):
+        rho = RNG.uniform(0.8, 1.2)
+        u = RNG.uniform(-0.05, 0.05, 2)
+        geq = orc.sp1_geq(rho, u[0], u[1])
+        assert np.isclose(geq.sum(), rho, atol=1e-15)                                   # Eq. 29bb moments
+        assert np.allclose(geq @ C, rho * u, atol=1e-16)
+        assert np.allclose(np.einsum("i,ia,ib->ab", geq, C, C), rho * CS2 * np.eye(2) + rho * np.outer(u, u),
+                           atol=1e-15)
+        S, divu = RNG.uniform(-1e-3, 1e-3), RNG.uniform(-1e-3, 1e-3)
+        G = orc.sp1_force(P, S, rho, u[0], u[1], divu)
+        Q = rho * CS2 - 0.02 / (tau - 0.5)
+        assert np.isclose(G.sum(), S, atol=1e-18)
+        assert np.allclose(G @ C, F, atol=1e-18)
+        M2 = np.einsum("i,ia,ib->ab", G, C, C)
+        expect = (CS2 * S * np.eye(2) + np.outer(u, F) + np.outer(F, u) - np.outer(u, u) * S
+                  + Q * divu * np.eye(2))
+        assert np.allclose(M2, expect, atol=1e-18)
+
+
+def test_remark1_mass_balance(orc):
+    # rho = sum g + S/2 (Eq. 27aa) and sum G = S: the total mass grows by sum S a step
+    P = orc.sp_params(dict(nx=16, ny=12, nu=0.08, walls_y=1, force_x=1e-6))
+    S = np.ascontiguousarray(RNG.uniform(0, 2e-5, (12, 16)))
+    g = orc.sp1_init(P, 1.0)
+    m0 = orc.sp1_fields(P, S, g)["rho"].sum()
+    orc.sp1_step(P, S, g, 50)
+    m1 = orc.sp1_fields(P, S, g)["rho"].sum()
+    assert abs(m1 - m0 - 50 * S.sum()) < 1e-12 * m0
+
+
+def test_remark1_mass_source_flow(orc):
+    errs = []
+    for nx in (32, 64):
+        P = orc.sp_params(dict(nx=nx, ny=2, nu=0.1))
+        k, A = 2 * np.pi / nx, 1e-4
+        x = np.arange(nx)
+        S = np.tile(A * np.sin(k * x), (2, 1))
+        g = orc.sp1_init(P, 1.0)
+        orc.sp1_step(P, S, g, 80000)
+        f = orc.sp1_fields(P, S, g)
+        ua = -(A / k) * np.cos(k * x)
+        errs.append(np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua)))
+    assert errs[1] < 1e-3 and 3.5 < errs[0] / errs[1] < 4.5
