@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--form", default="f32_c", choices=list(BYTES_PER_LUP))
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs"],
                     help="load path of the step kernel (lbm_set_pipeline)")
-    ap.add_argument("--kernel-run", default=None, choices=["bubble3d", "source_flow"],
+    ap.add_argument("--kernel-run", default=None, choices=["bubble3d", "source_flow", "source_flow_remark1"],
                     help="only time one step loop of another workload (for profiling): the "
                          "128 x 256 x 128 D3Q15 bubble or the 4096 x 4096 Remark 3 source flow")
     ap.add_argument("--headline-only", action="store_true",
@@ -284,8 +284,9 @@ def kernel_run(args):
         cells = n * n
         src = np.ascontiguousarray(1e-4 * np.sin(2 * np.pi * np.arange(n) / n)[None, :] * np.ones((n, 1)))
         form = "f64" if args.form == "f64" else "f32"
-        sim = lbm.SourceFlow(dict(nx=n, ny=n, nu=0.1), form, stream=stream.cuda_stream, source=src)
-        bpl = 152 if form == "f64" else 76
+        model = 1 if args.kernel_run == "source_flow_remark1" else 0
+        sim = lbm.SourceFlow(dict(nx=n, ny=n, nu=0.1, model=model), form, stream=stream.cuda_stream, source=src)
+        bpl = (264 if model else 152) if form == "f64" else (132 if model else 76)
     sim.step(max(args.warmup, 2))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -472,8 +473,12 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     n = 4096
     src = np.ascontiguousarray(1e-4 * np.sin(2 * np.pi * np.arange(n) / n)[None, :] * np.ones((n, 1)))
     sp = {"workload": "source_flow_4096x4096", "cells": n * n}
-    for form, bpl in (("f64", 152), ("f32", 76)):
-        with lbm.SourceFlow(dict(nx=n, ny=n, nu=0.1), form, stream=stream.cuda_stream, source=src) as sim:
+    # Remark 1 (two kernels a step): (9 + 1) reads + 2 writes of u, then
+    # 9 + 1 + 2 reads and 9 writes, so 264 / 132 bytes a cell
+    sp1 = {"workload": "source_flow_remark1_4096x4096", "cells": n * n}
+    for model, form, bpl in ((0, "f64", 152), (0, "f32", 76), (1, "f64", 264), (1, "f32", 132)):
+        with lbm.SourceFlow(dict(nx=n, ny=n, nu=0.1, model=model), form, stream=stream.cuda_stream,
+                            source=src) as sim:
             sim.step(4)
             torch.cuda.synchronize()
             Ks = max(20, K // 4)
@@ -485,9 +490,10 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             gbs = bpl * n * n / (ms * 1e-3 / Ks) / 1e9
-            sp[form] = {"MLUPS": n * n * Ks / (ms * 1e-3) / 1e6, "GBps_algorithmic": gbs,
-                        "frac_hbm": gbs / hbm_peak, "bytes_per_lup": bpl, "steps": Ks}
+            (sp1 if model else sp)[form] = {"MLUPS": n * n * Ks / (ms * 1e-3) / 1e6, "GBps_algorithmic": gbs,
+                                            "frac_hbm": gbs / hbm_peak, "bytes_per_lup": bpl, "steps": Ks}
     out["source_flow"] = sp
+    out["source_flow_remark1"] = sp1
 
     # end to end through the C ABI with host buffers: init from pinned host phi0,
     # each step one lbm_step whose kernels also reduce sum(phi), the kinetic energy

@@ -350,11 +350,17 @@ void lbm_destroy(lbm_ctx* ctx);
  * bounce-back walls). Equilibrium of Remark 3 (g_0 stored shifted by rho_0),
  * force term w_i{S + c.F/c_s^2 + (cc - c_s^2 I):(uF + Fu + Q S I)/(2 c_s^4)}
  * with Q = (2/d) c_s^2 - xi/(tau_g - 1/2), u by Eq. 27a (rho = 1), p by Eq. 28,
- * BGK of Eq. 24 with tau_g = nu / c_s^2 + 1/2. One kernel a step. */
+ * BGK of Eq. 24 with tau_g = nu / c_s^2 + 1/2. One kernel a step.
+ * model LBM_SP_NEARLY_INCOMPRESSIBLE is Remark 1 instead (rho~ = rho,
+ * p = rho c_s^2): rho = sum g + S/2 (Eq. 27aa), u = (sum c g + F/2)/rho,
+ * g^eq = rho (w_i + s_i(u)) (Eq. 29bb), force term with uF + Fu - uuS + Q div(u) I,
+ * Q = (2/d) rho c_s^2 - xi/(tau_g - 1/2), div u by Eq. 30a (mirror at walls);
+ * the total mass grows by sum S a step. Two kernels a step. */
+enum { LBM_SP_INCOMPRESSIBLE_SOURCE = 0, LBM_SP_NEARLY_INCOMPRESSIBLE = 1 };
 typedef struct lbm_sp_params {
     int32_t nx, ny;
     int32_t bc_y;             /* LBM_BC_*                                                */
-    int32_t reserved;         /* must be 0                                                */
+    int32_t model;            /* LBM_SP_* (Remark 3 or Remark 1)                          */
     double nu;                /* kinematic viscosity (> 0)                               */
     double xi;                /* bulk viscosity in Q (>= 0; 0 under Stokes' hypothesis)  */
     double force_x, force_y;  /* uniform body force                                       */
@@ -369,18 +375,21 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
                          lbm_sp_ctx** out);
 
 /* Sets the source field S (host array of nx*ny doubles, copied; constant in
- * time) and the state at rest (u = 0, p = 0). Resets the time. Synchronises. */
+ * time) and the state at rest (u = 0; p = 0 for Remark 3, rho = 1 for Remark
+ * 1). Resets the time. Synchronises. */
 lbm_status lbm_sp_init(lbm_sp_ctx* ctx, const double* source_host);
 
 /* Advances nsteps time steps (asynchronous). LBM_ESTATE before lbm_sp_init. */
 lbm_status lbm_sp_step(lbm_sp_ctx* ctx, int nsteps);
 
-/* u and p (Eq. 27a, Eq. 28) at the current time: mask of LBM_FIELD_UX,
- * LBM_FIELD_UY, LBM_FIELD_P; host_out receives popcount(mask) * nx * ny doubles
- * in that order. Synchronises. */
+/* u and p (Eq. 27a, Eq. 28; Remark 1: p = rho c_s^2) at the current time:
+ * mask of LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_P (and LBM_FIELD_RHO for Remark
+ * 1); host_out receives popcount(mask) * nx * ny doubles in bit order.
+ * Synchronises. */
 lbm_status lbm_sp_get_fields(lbm_sp_ctx* ctx, unsigned mask, double* host_out);
 
-/* The 9 population planes in FP64 (g_0 shifted by rho_0). Synchronises. */
+/* The 9 population planes in FP64 (Remark 3: g_0 shifted by rho_0; Remark 1:
+ * as they are). Synchronises. */
 lbm_status lbm_sp_get_populations(lbm_sp_ctx* ctx, double* host_g);
 
 const char* lbm_sp_last_error(const lbm_sp_ctx* ctx);

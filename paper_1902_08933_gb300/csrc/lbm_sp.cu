@@ -10,6 +10,14 @@
 //   Q = (2/d) c_s^2 - xi / (tau_g - 1/2),
 // then BGK (Eq. 24) and push-streaming (x periodic; y periodic or halfway
 // bounce-back walls). Storage and arithmetic in FP64 or FP32.
+//
+// model LBM_SP_NEARLY_INCOMPRESSIBLE: Remark 1 (rho~ = rho, p = rho c_s^2): rho =
+// sum g + S/2 (Eq. 27aa), u = (sum c g + F/2) / rho, g^eq = rho (w_i + s_i(u))
+// (Eq. 29bb), G_i with (u F + F u - u u S + Q div(u) I) and Q = (2/d) rho c_s^2 -
+// xi / (tau_g - 1/2); div u by Eq. 30a from a plane of u (mirror at walls), so
+// a step is two kernels (rho and u, then the collision). The populations are
+// stored as g_i - w_i (their rest state at rho = 1), so that FP32 storage keeps
+// the small deviations that carry the flow: rho = 1 + sum(g - w) + S/2.
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -96,6 +104,119 @@ __global__ void __launch_bounds__(256) sp_step_kernel(const R* __restrict__ gin,
     }
 }
 
+// ---- Remark 1 ----
+// g holds g_i - w_i; drho = rho - 1
+template <typename R>
+__device__ __forceinline__ void sp1_moments(const SpConst& K, const R g[kQ], R S, R& drho, R& rho, R& ux, R& uy) {
+    R m0 = g[0], jx = R(0), jy = R(0);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        m0 += g[i];
+        if (sx(i)) jx += sx(i) > 0 ? g[i] : -g[i];
+        if (sy(i)) jy += sy(i) > 0 ? g[i] : -g[i];
+    }
+    drho = m0 + R(0.5) * S;
+    rho = R(1) + drho;
+    const R ir = R(1) / rho;
+    ux = (jx + R(0.5) * R(K.fx)) * ir;
+    uy = (jy + R(0.5) * R(K.fy)) * ir;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) sp1_moments_kernel(const R* __restrict__ gin, const R* __restrict__ src,
+                                                          long long N, SpConst K, R* __restrict__ ufield) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    R g[kQ], drho, rho, ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = gin[i * N + c];
+    sp1_moments(K, g, src[c], drho, rho, ux, uy);
+    ufield[c] = ux;
+    ufield[N + c] = uy;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin, R* __restrict__ gout,
+                                                       const R* __restrict__ src, const R* __restrict__ ufield,
+                                                       long long N, SpConst K) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+    R g[kQ], drho, rho, ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = gin[i * N + c];
+    const R S = src[c];
+    sp1_moments(K, g, S, drho, rho, ux, uy);
+    const int xs[3] = {x == 0 ? K.nx - 1 : x - 1, x, x == K.nx - 1 ? 0 : x + 1};
+    // stencil rows: mirror at walls (reading Q7), wrap when periodic
+    const int yst[3] = {y == 0 ? (K.walls ? 0 : K.ny - 1) : y - 1, y,
+                        y == K.ny - 1 ? (K.walls ? K.ny - 1 : 0) : y + 1};
+    R divu = R(0);   // Eq. 30a applied to u
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const long long n = (long long)yst[sy(i) + 1] * K.nx + xs[sx(i) + 1];
+        R cu = R(0);
+        if (sx(i)) cu += sx(i) > 0 ? ufield[n] : -ufield[n];
+        if (sy(i)) cu += sy(i) > 0 ? ufield[N + n] : -ufield[N + n];
+        divu += R(sw(i)) * cu;
+    }
+    divu *= R(3);
+    const R fx = R(K.fx), fy = R(K.fy);
+    const R uF = ux * fx + uy * fy, uu = ux * ux + uy * uy;
+    // Q = (2/d) rho c_s^2 - xi / (tau_g - 1/2); K.Qc holds the value at rho = 1
+    const R Qd = (rho * R(1.0 / 3.0) + R(K.Qc - 1.0 / 3.0)) * divu;
+    const R ig = R(K.inv_tau), sg = R(K.src);
+    const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
+    const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
+                       K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const R cu = R(sx(i)) * ux + R(sy(i)) * uy, cF = R(sx(i)) * fx + R(sy(i)) * fy;
+        const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
+        const R si = R(sw(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        const R geq = drho * R(sw(i)) + rho * si;                              // Eq. 29bb, minus w_i
+        // (cc - c_s^2 I):(uF + Fu - uu S + Q div u I) / (2 c_s^4)
+        //   = 9 (c.u)(c.F) - 3 u.F - 4.5 ((c.u)^2 - u.u / 3) S + 4.5 (|c|^2 - 2/3) Q div u
+        const R Gi = R(sw(i)) * (S + R(3) * cF + R(9) * cu * cF - R(3) * uF -
+                                 R(4.5) * (cu * cu - uu * R(1.0 / 3.0)) * S + R(4.5) * (c2 - R(2.0 / 3.0)) * Qd);
+        const R post = g[i] - (g[i] - geq) * ig + sg * Gi;
+        long long dst;
+        int k = i;
+        if ((sy(i) > 0 && top) || (sy(i) < 0 && bot)) {
+            dst = c;
+            k = sopp(i);
+        } else {
+            dst = (long long)ys[sy(i) + 1] * K.nx + xs[sx(i) + 1];
+        }
+        gout[k * N + dst] = post;
+    }
+}
+
+template <typename R>
+__global__ void sp1_fields_kernel(const R* __restrict__ g, const R* __restrict__ src, long long N, SpConst K,
+                                  unsigned mask, double* __restrict__ out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    R gc[kQ], drho, rho, ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) gc[i] = g[i * N + c];
+    sp1_moments(K, gc, src[c], drho, rho, ux, uy);
+    int slot = 0;
+    if (mask & LBM_FIELD_UX) out[(slot++) * N + c] = double(ux);
+    if (mask & LBM_FIELD_UY) out[(slot++) * N + c] = double(uy);
+    if (mask & LBM_FIELD_P) out[(slot++) * N + c] = (1.0 + double(drho)) / 3.0;   // p = rho c_s^2
+    if (mask & LBM_FIELD_RHO) out[(slot++) * N + c] = 1.0 + double(drho);
+}
+
+// populations g_i = stored + w_i, widened to FP64
+template <typename R>
+__global__ void sp1_widen_kernel(const R* __restrict__ in, double* __restrict__ out, long long N) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) out[i * N + c] = double(in[i * N + c]) + sw(i);
+}
+
 template <typename R>
 __global__ void sp_fields_kernel(const R* __restrict__ g, const R* __restrict__ src, long long N, SpConst K,
                                  unsigned mask, double* __restrict__ out) {
@@ -131,6 +252,7 @@ struct lbm_sp_ctx {
     long long N = 0;
     void* g[2] = {nullptr, nullptr};
     void* src = nullptr;
+    void* ufield = nullptr;            // Remark 1: u of the current step (2 planes)
     double* d_tmp = nullptr;           // staging for inputs and outputs
     int cur = 0;
     bool ready = false;
@@ -157,6 +279,7 @@ void sp_release(lbm_sp_ctx* c) {
     cudaFree(c->g[0]);
     cudaFree(c->g[1]);
     cudaFree(c->src);
+    cudaFree(c->ufield);
     cudaFree(c->d_tmp);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -172,7 +295,7 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
     const lbm_sp_params& p = *params;
     if (p.nx < 3 || p.ny < 3 || (long long)p.nx * p.ny >= (1LL << 31) / 9) return LBM_EINVAL;
     if (p.bc_y != LBM_BC_PERIODIC && p.bc_y != LBM_BC_BOUNCEBACK) return LBM_EINVAL;
-    if (p.reserved != 0) return LBM_EINVAL;
+    if (p.model != LBM_SP_INCOMPRESSIBLE_SOURCE && p.model != LBM_SP_NEARLY_INCOMPRESSIBLE) return LBM_EINVAL;
     if (!(std::isfinite(p.nu) && p.nu > 0) || !(std::isfinite(p.xi) && p.xi >= 0) || !std::isfinite(p.force_x) ||
         !std::isfinite(p.force_y))
         return LBM_EINVAL;
@@ -189,6 +312,7 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
     if ((r = cudaMalloc(&c->g[0], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->g[1], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->src, c->N * e)) != cudaSuccess ||
+        (p.model == LBM_SP_NEARLY_INCOMPRESSIBLE && (r = cudaMalloc(&c->ufield, 2 * c->N * e)) != cudaSuccess) ||
         (r = cudaMalloc((void**)&c->d_tmp, kQ * c->N * sizeof(double))) != cudaSuccess) {
         sp_release(c);
         delete c;
@@ -219,8 +343,9 @@ lbm_status lbm_sp_init(lbm_sp_ctx* c, const double* source_host) {
     } else {
         sp_convert_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(c->d_tmp, static_cast<float*>(c->src), c->N);
     }
-    // at rest: p = 0, u = 0, g^eq = rho_0 delta_i0 -- zero with g_0 stored shifted by rho_0
     c->cur = 0;
+    // at rest: Remark 3 g^eq = rho_0 delta_i0 (g_0 stored shifted by rho_0);
+    // Remark 1 g^eq = w_i at rho = 1 (stored shifted by w_i) -- zero either way
     if ((r = cudaMemsetAsync(c->g[0], 0, kQ * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
         return sp_cuda(c, r, "state reset");
     if ((r = cudaStreamSynchronize(c->stream)) != cudaSuccess) return sp_cuda(c, r, "init");
@@ -234,8 +359,25 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
     if (!c) return LBM_EINVAL;
     if (nsteps < 0) return sp_fail(c, LBM_EINVAL, "nsteps < 0");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
+    const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE;
     for (int s = 0; s < nsteps; ++s) {
-        if (c->form == LBM_F64)
+        if (m1) {
+            if (c->form == LBM_F64) {
+                const double* gi = static_cast<const double*>(c->g[c->cur]);
+                sp1_moments_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
+                    gi, static_cast<const double*>(c->src), c->N, c->K, static_cast<double*>(c->ufield));
+                sp1_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
+                    gi, static_cast<double*>(c->g[1 - c->cur]), static_cast<const double*>(c->src),
+                    static_cast<const double*>(c->ufield), c->N, c->K);
+            } else {
+                const float* gi = static_cast<const float*>(c->g[c->cur]);
+                sp1_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                    gi, static_cast<const float*>(c->src), c->N, c->K, static_cast<float*>(c->ufield));
+                sp1_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                    gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src),
+                    static_cast<const float*>(c->ufield), c->N, c->K);
+            }
+        } else if (c->form == LBM_F64)
             sp_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
                 static_cast<const double*>(c->g[c->cur]), static_cast<double*>(c->g[1 - c->cur]),
                 static_cast<const double*>(c->src), c->N, c->K);
@@ -252,11 +394,19 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
 
 lbm_status lbm_sp_get_fields(lbm_sp_ctx* c, unsigned mask, double* host_out) {
     if (!c) return LBM_EINVAL;
-    const unsigned ok = LBM_FIELD_UX | LBM_FIELD_UY | LBM_FIELD_P;
+    const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE;
+    const unsigned ok = LBM_FIELD_UX | LBM_FIELD_UY | LBM_FIELD_P | (m1 ? LBM_FIELD_RHO : 0u);
     if (!host_out || mask == 0 || (mask & ~ok)) return sp_fail(c, LBM_EINVAL, "bad mask or output");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
-    const int nf = ((mask & LBM_FIELD_UX) ? 1 : 0) + ((mask & LBM_FIELD_UY) ? 1 : 0) + ((mask & LBM_FIELD_P) ? 1 : 0);
-    if (c->form == LBM_F64)
+    const int nf = ((mask & LBM_FIELD_UX) ? 1 : 0) + ((mask & LBM_FIELD_UY) ? 1 : 0) + ((mask & LBM_FIELD_P) ? 1 : 0) +
+                   ((mask & LBM_FIELD_RHO) ? 1 : 0);
+    if (m1 && c->form == LBM_F64)
+        sp1_fields_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
+            static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
+    else if (m1)
+        sp1_fields_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+            static_cast<const float*>(c->g[c->cur]), static_cast<const float*>(c->src), c->N, c->K, mask, c->d_tmp);
+    else if (c->form == LBM_F64)
         sp_fields_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
             static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
     else
@@ -275,7 +425,11 @@ lbm_status lbm_sp_get_populations(lbm_sp_ctx* c, double* host_g) {
     if (!host_g) return sp_fail(c, LBM_EINVAL, "output is NULL");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
     const long long n = kQ * c->N;
-    if (c->form == LBM_F64)
+    if (c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE && c->form == LBM_F64)
+        sp1_widen_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(static_cast<const double*>(c->g[c->cur]), c->d_tmp, c->N);
+    else if (c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE)
+        sp1_widen_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(static_cast<const float*>(c->g[c->cur]), c->d_tmp, c->N);
+    else if (c->form == LBM_F64)
         sp_widen_kernel<double><<<blocks(n), 256, 0, c->stream>>>(static_cast<const double*>(c->g[c->cur]), c->d_tmp, n);
     else
         sp_widen_kernel<float><<<blocks(n), 256, 0, c->stream>>>(static_cast<const float*>(c->g[c->cur]), c->d_tmp, n);

@@ -72,7 +72,7 @@ class lbm_monitor(ctypes.Structure):
 
 class lbm_sp_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("nu", ctypes.c_double), ("xi", ctypes.c_double),
+                ("model", ctypes.c_int32), ("nu", ctypes.c_double), ("xi", ctypes.c_double),
                 ("force_x", ctypes.c_double), ("force_y", ctypes.c_double)]
 
 
@@ -377,7 +377,8 @@ class SourceFlow:
         p = lbm_sp_params()
         p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
         p.bc_y = int(cfg.get("walls_y", 0))
-        p.reserved = 0
+        p.model = int(cfg.get("model", 0))   # 0: Remark 3, 1: Remark 1
+        self.model = p.model
         p.nu, p.xi = float(cfg["nu"]), float(cfg.get("xi", 0.0))
         p.force_x, p.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))
         self.nx, self.ny = p.nx, p.ny
@@ -399,10 +400,14 @@ class SourceFlow:
         _check_sp(library().lbm_sp_step(self.ctx, int(n)), self.ctx)
 
     def fields(self) -> dict:
-        out = np.zeros((3, self.ny, self.nx))
-        mask = FIELD_BITS["ux"] | FIELD_BITS["uy"] | FIELD_BITS["p"]
+        names = ["ux", "uy", "p"] + (["rho"] if self.model == 1 else [])
+        out = np.zeros((len(names), self.ny, self.nx))
+        mask = 0
+        for n in names:
+            mask |= FIELD_BITS[n]
         _check_sp(library().lbm_sp_get_fields(self.ctx, mask, out.ctypes.data_as(_DP)), self.ctx)
-        return {"ux": out[0], "uy": out[1], "p": out[2]}
+        order = [n for n in FIELDS3 if n in names]
+        return {n: out[i] for i, n in enumerate(order)}
 
     def populations(self):
         g = np.zeros((9, self.ny, self.nx))

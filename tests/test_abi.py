@@ -81,7 +81,7 @@ def test_create_rejects_bad_input_without_touching_cuda(L):
     # the single-phase model of Remark 3
     sp = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
     spo = ctypes.c_void_p(1234)
-    for field, value in (("nx", 2), ("bc_y", 5), ("reserved", 1), ("nu", 0.0), ("xi", -1.0),
+    for field, value in (("nx", 2), ("bc_y", 5), ("model", 2), ("nu", 0.0), ("xi", -1.0),
                          ("force_x", float("nan"))):
         bad = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
         setattr(bad, field, value)
