@@ -140,6 +140,9 @@ typedef struct {
     double xi;            /* bulk viscosity in Q = (2/d) rho c_s^2 - xi/(tau_g - 1/2) */
     double force_x, force_y;
     double rho0;          /* rho~ = rho_0 of the equilibrium                     */
+    /* velocity-dependent force of the Remark 4 scheme:
+     * F(u) = (force_x, force_y) - (drag_lin + drag_quad |u|) u                   */
+    double drag_lin, drag_quad;
 } orc_sp_params;
 
 double orc_sp_tau(const orc_sp_params* P);
@@ -163,6 +166,17 @@ int    orc_sp1_init(const orc_sp_params* P, double rho_init, double* g);
 int    orc_sp1_step(const orc_sp_params* P, const double* S, double* g, int nsteps);
 int    orc_sp1_fields(const orc_sp_params* P, const double* S, const double* g, double* rho,
                       double* ux, double* uy);
+
+/* Remark 4: the Remark 3 model evolved with the explicit discretization of
+ * D_i G_i (f_bar not shifted by G/2, u = sum c f_bar explicit even when F
+ * depends on u). Gprev: the 9 planes of G_i at t - 1. */
+void   orc_sp4_force_of_u(const orc_sp_params* P, double ux, double uy, double* Fx, double* Fy);
+void   orc_sp4_moments(const orc_sp_params* P, const double* f, double S, double* ux, double* uy,
+                       double* p);
+int    orc_sp4_init(const orc_sp_params* P, const double* S, double* f, double* Gprev);
+int    orc_sp4_step(const orc_sp_params* P, const double* S, double* f, double* Gprev, int nsteps);
+int    orc_sp4_fields(const orc_sp_params* P, const double* S, const double* f, double* ux,
+                      double* uy, double* p);
 
 /* Analytic layered Poiseuille profile, Eq. 37: y measured from the interface,
  * walls at y = -hh and y = +hh, dynamic viscosity mu_up for 0 < y <= hh and

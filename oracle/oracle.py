@@ -63,7 +63,8 @@ class Diag(ctypes.Structure):
 class SpParams(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls_y", ctypes.c_int),
                 ("nu", ctypes.c_double), ("xi", ctypes.c_double), ("force_x", ctypes.c_double),
-                ("force_y", ctypes.c_double), ("rho0", ctypes.c_double)]
+                ("force_y", ctypes.c_double), ("rho0", ctypes.c_double), ("drag_lin", ctypes.c_double),
+                ("drag_quad", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -146,6 +147,10 @@ def lib():
         L.orc_sp1_geq.argtypes = [ctypes.c_double] * 3 + [_DP]
         L.orc_sp1_init.argtypes = [SP, ctypes.c_double, _DP]
         L.orc_sp1_step.argtypes = [SP, _DP, _DP, ctypes.c_int]
+        L.orc_sp4_moments.argtypes = [SP, _DP, ctypes.c_double, _DP, _DP, _DP]
+        L.orc_sp4_init.argtypes = [SP, _DP, _DP, _DP]
+        L.orc_sp4_step.argtypes = [SP, _DP, _DP, _DP, ctypes.c_int]
+        L.orc_sp4_fields.argtypes = [SP, _DP, _DP, _DP, _DP, _DP]
         L.orc_sp1_fields.argtypes = [SP, _DP, _DP, _DP, _DP, _DP]
         _lib = L
     return _lib
@@ -429,6 +434,7 @@ def sp_params(cfg: dict) -> SpParams:
     P.nu, P.xi = float(cfg["nu"]), float(cfg.get("xi", 0.0))
     P.force_x, P.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))
     P.rho0 = float(cfg.get("rho0", 0.0))
+    P.drag_lin, P.drag_quad = float(cfg.get("drag_lin", 0.0)), float(cfg.get("drag_quad", 0.0))
     return P
 
 
@@ -504,4 +510,36 @@ def sp1_fields(P: SpParams, S, g) -> dict:
     S = np.ascontiguousarray(S, dtype=np.float64)
     out = {k: np.zeros((P.ny, P.nx)) for k in ("rho", "ux", "uy")}
     lib().orc_sp1_fields(ctypes.byref(P), _ptr(S), _ptr(g), _ptr(out["rho"]), _ptr(out["ux"]), _ptr(out["uy"]))
+    return out
+
+
+# ------------------------------------------------- Remark 4 (explicit D_i G_i)
+def sp4_moments(P: SpParams, f, S):
+    ux, uy, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().orc_sp4_moments(ctypes.byref(P), _ptr(np.ascontiguousarray(f, dtype=np.float64)), S,
+                          ctypes.cast(ctypes.byref(ux), _DP), ctypes.cast(ctypes.byref(uy), _DP),
+                          ctypes.cast(ctypes.byref(p), _DP))
+    return ux.value, uy.value, p.value
+
+
+def sp4_init(P: SpParams, S):
+    """(f, Gprev): f at rest, Gprev = G of that state (standing in for t = -1)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    f, G = np.zeros((9, P.ny, P.nx)), np.zeros((9, P.ny, P.nx))
+    lib().orc_sp4_init(ctypes.byref(P), _ptr(S), _ptr(f), _ptr(G))
+    return f, G
+
+
+def sp4_step(P: SpParams, S, f, Gprev, n: int):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    rc = lib().orc_sp4_step(ctypes.byref(P), _ptr(S), _ptr(f), _ptr(Gprev), int(n))
+    if rc:
+        raise ValueError("orc_sp4_step failed (%d)" % rc)
+    return f
+
+
+def sp4_fields(P: SpParams, S, f) -> dict:
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    out = {k: np.zeros((P.ny, P.nx)) for k in ("ux", "uy", "p")}
+    lib().orc_sp4_fields(ctypes.byref(P), _ptr(S), _ptr(f), _ptr(out["ux"]), _ptr(out["uy"]), _ptr(out["p"]))
     return out

@@ -28,6 +28,23 @@
  *   Q = (2/d) rho c_s^2 - xi / (tau_g - 1/2),
  * div u by the isotropic gradient of Eq. 30a (mirror at walls, reading Q7);
  * the u u S term is kept as printed.
+ *
+ * Remark 4 (orc_sp4_*): the Remark 3 model with a velocity-dependent force
+ * F(u) = F_0 - (lambda + beta |u|) u, evolved without the shift of Eq. 23a and
+ * with the explicit discretization of D_i G_i the remark gives:
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq) / tau_g
+ *                        + G_i(x, t) + [G_i(x + c_i, t) - G_i(x, t - 1)] / 2,
+ * u = sum_i c_i f_i (rho = 1; explicit: the moments of the unshifted f are the
+ * equilibrium's, sum f = rho_0, sum c f = u), G_i of Remark 3 with F = F(u), and
+ * the pressure of Eq. 28 rewritten for the unshifted f (f_0 - f_0^eq = tau G_0
+ * to first order, the argument of App. B):
+ *   p = c_s^2 / (1 - w_0) [ sum_{i != 0} f_i + s_0(u) + tau_g G_0 ].
+ * G_i(x + c_i, t) across a wall is taken at the mirrored cell (as the stencils
+ * of the phase-field model), and G_i(x, -1) = G_i(x, 0). G at t - 1 is kept as
+ * the remark says (nine planes). Halfway bounce-back acts on g = f - G/2 of
+ * Eq. 23a (the variable the rule is stated for): the population i that left x
+ * towards the wall returns as f_opp = f_i^post - G_i(x + c_i, t)/2 + G_opp(x, t)/2,
+ * so a fluid at rest under a uniform force stays at rest.
  */
 #include "oracle.h"
 
@@ -277,6 +294,129 @@ int orc_sp_fields(const orc_sp_params* P, const double* S, const double* g, doub
         double gc[QS], a, b, q;
         for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
         orc_sp_moments(P, gc, S[c], &a, &b, &q);
+        if (ux) ux[c] = a;
+        if (uy) uy[c] = b;
+        if (p) p[c] = q;
+    }
+    return 0;
+}
+
+/* ---- Remark 4 ---- */
+void orc_sp4_force_of_u(const orc_sp_params* P, double ux, double uy, double* Fx, double* Fy) {
+    const double k = P->drag_lin + P->drag_quad * sqrt(ux * ux + uy * uy);
+    *Fx = P->force_x - k * ux;
+    *Fy = P->force_y - k * uy;
+}
+
+/* u = sum c f, F(u), G_i(x, t) (Remark 3 with F(u)) and p of one cell. */
+static void sp4_cell(const orc_sp_params* P, const double* f, double S, double* ux, double* uy,
+                     double* p, double* G) {
+    double jx = 0.0, jy = 0.0, rest = 0.0;
+    for (int i = 0; i < QS; ++i) {
+        jx += SX[i] * f[i];
+        jy += SY[i] * f[i];
+        if (i) rest += f[i];
+    }
+    *ux = jx;
+    *uy = jy;
+    double Fx, Fy;
+    orc_sp4_force_of_u(P, jx, jy, &Fx, &Fy);
+    orc_sp_force(P, S, Fx, Fy, jx, jy, G);
+    *p = SCS2 / (1.0 - SW[0]) * (rest + sp_s(0, jx, jy) + orc_sp_tau(P) * G[0]);
+}
+
+void orc_sp4_moments(const orc_sp_params* P, const double* f, double S, double* ux, double* uy,
+                     double* p) {
+    double G[QS];
+    sp4_cell(P, f, S, ux, uy, p, G);
+}
+
+int orc_sp4_init(const orc_sp_params* P, const double* S, double* f, double* Gprev) {
+    const long N = (long)P->nx * P->ny;
+    double geq[QS];
+    orc_sp_geq(0.0, 0.0, 0.0, P->rho0, geq);
+    for (int i = 0; i < QS; ++i)
+        for (long c = 0; c < N; ++c) f[i * N + c] = geq[i];
+    for (long c = 0; c < N; ++c) {   /* G at the initial state stands in for G at t = -1 */
+        double G[QS], ux, uy, p, fc[QS];
+        for (int i = 0; i < QS; ++i) fc[i] = f[i * N + c];
+        sp4_cell(P, fc, S[c], &ux, &uy, &p, G);
+        for (int i = 0; i < QS; ++i) Gprev[i * N + c] = G[i];
+    }
+    return 0;
+}
+
+int orc_sp4_step(const orc_sp_params* P, const double* S, double* f, double* Gprev, int nsteps) {
+    const int nx = P->nx, ny = P->ny;
+    const long N = (long)nx * ny;
+    const double tau = orc_sp_tau(P);
+    double* post = (double*)malloc((size_t)(QS * N) * sizeof(double));
+    double* Gnow = (double*)malloc((size_t)(QS * N) * sizeof(double));
+    double* pc = (double*)malloc((size_t)N * sizeof(double));
+    double* uxc = (double*)malloc((size_t)N * sizeof(double));
+    double* uyc = (double*)malloc((size_t)N * sizeof(double));
+    if (!post || !Gnow || !pc || !uxc || !uyc) {
+        free(post); free(Gnow); free(pc); free(uxc); free(uyc);
+        return 2;
+    }
+    for (int step = 0; step < nsteps; ++step) {
+        /* G_i(x, t) everywhere first: the update at x needs it at x + c_i */
+        for (long c = 0; c < N; ++c) {
+            double fc[QS], G[QS];
+            for (int i = 0; i < QS; ++i) fc[i] = f[i * N + c];
+            sp4_cell(P, fc, S[c], &uxc[c], &uyc[c], &pc[c], G);
+            for (int i = 0; i < QS; ++i) Gnow[i * N + c] = G[i];
+        }
+        for (long c = 0; c < N; ++c) {
+            const int x = (int)(c % nx), y = (int)(c / nx);
+            double geq[QS];
+            orc_sp_geq(pc[c], uxc[c], uyc[c], P->rho0, geq);
+            for (int i = 0; i < QS; ++i) {
+                const int xn = ((x + SX[i]) % nx + nx) % nx;
+                int yn = y + SY[i];
+                if (P->walls_y) {
+                    if (yn < 0 || yn >= ny) yn = y;   /* mirror about the wall */
+                } else {
+                    yn = (yn % ny + ny) % ny;
+                }
+                const double Gdst = Gnow[i * N + (long)yn * nx + xn];
+                const double fi = f[i * N + c];
+                post[i * N + c] = fi - (fi - geq[i]) / tau + Gnow[i * N + c] +
+                                  0.5 * (Gdst - Gprev[i * N + c]);
+            }
+        }
+        for (int i = 0; i < QS; ++i) {
+            const int oi = sp_opposite(i);
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const long here = (long)y * nx + x;
+                    const int ys = y - SY[i];
+                    if (P->walls_y && (ys < 0 || ys >= ny)) {
+                        /* halfway bounce-back of g = f - G/2 (Eq. 23a): the
+                         * population oi left here towards the wall, whose
+                         * G_oi(x + c_oi) is at the mirrored cell (x + c_oi,x, y) */
+                        const int xm = ((x + SX[oi]) % nx + nx) % nx;
+                        f[i * N + here] = post[oi * N + here] - 0.5 * Gnow[oi * N + (long)y * nx + xm] +
+                                          0.5 * Gnow[i * N + here];
+                    } else {
+                        const int xs = ((x - SX[i]) % nx + nx) % nx, yw = (ys % ny + ny) % ny;
+                        f[i * N + here] = post[i * N + (long)yw * nx + xs];
+                    }
+                }
+        }
+        memcpy(Gprev, Gnow, (size_t)(QS * N) * sizeof(double));
+    }
+    free(post); free(Gnow); free(pc); free(uxc); free(uyc);
+    return 0;
+}
+
+int orc_sp4_fields(const orc_sp_params* P, const double* S, const double* f, double* ux, double* uy,
+                   double* p) {
+    const long N = (long)P->nx * P->ny;
+    for (long c = 0; c < N; ++c) {
+        double fc[QS], a, b, q;
+        for (int i = 0; i < QS; ++i) fc[i] = f[i * N + c];
+        orc_sp4_moments(P, fc, S[c], &a, &b, &q);
         if (ux) ux[c] = a;
         if (uy) uy[c] = b;
         if (p) p[c] = q;

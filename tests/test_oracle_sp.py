@@ -1,4 +1,4 @@
-"""Pins of the oracle of Remark 3 (Sec. 2.3): the generalized model with
+"""Pins of the oracles of Remarks 3, 1 and 4 (Sec. 2.3). Remark 3: the generalized model with
 rho~ = rho_0 and constant density, the incompressible Navier-Stokes equations
 with a mass source (div u = S).
 
@@ -152,3 +152,110 @@ def test_remark1_mass_source_flow(orc):
         ua = -(A / k) * np.cos(k * x)
         errs.append(np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua)))
     assert errs[1] < 1e-3 and 3.5 < errs[0] / errs[1] < 4.5
+
+
+# ---------------------------------------------------------------- Remark 4
+def _drag(F0, lam, beta, u):
+    return F0 - (lam + beta * np.linalg.norm(u)) * u
+
+
+def test_remark4_uniform_state_is_adams_bashforth(orc):
+    # a uniform state under F(u) = F0 - (lambda + beta|u|) u: sum c f_eq = u and
+    # sum c G = F, so the Remark 4 update of the momentum is u + F(u_n) +
+    # [F(u_n) - F(u_{n-1})]/2, the two-step Adams-Bashforth rule for du/dt = F(u)
+    # (first step Euler: G at t = -1 is G at t = 0)
+    lam, beta, F0 = 0.01, 0.5, np.array([1e-4, -5e-5])
+    P = orc.sp_params(dict(nx=4, ny=3, nu=0.1, force_x=F0[0], force_y=F0[1], drag_lin=lam, drag_quad=beta))
+    S = np.zeros((3, 4))
+    f, G = orc.sp4_init(P, S)
+    u, up = np.zeros(2), np.zeros(2)
+    for _ in range(60):
+        orc.sp4_step(P, S, f, G, 1)
+        u, up = u + 1.5 * _drag(F0, lam, beta, u) - 0.5 * _drag(F0, lam, beta, up), u
+        r = orc.sp4_fields(P, S, f)
+        assert np.allclose(r["ux"], u[0], rtol=0, atol=1e-17) and np.allclose(r["uy"], u[1], rtol=0, atol=1e-17)
+
+
+def test_remark4_uniform_drag_steady_state(orc):
+    # steady: F(u) = 0, |u| = (-lambda + sqrt(lambda^2 + 4 beta |F0|)) / (2 beta) along F0
+    lam, beta, F0 = 0.02, 2.0, np.array([3e-5, 4e-5])
+    P = orc.sp_params(dict(nx=3, ny=2, nu=0.1, force_x=F0[0], force_y=F0[1], drag_lin=lam, drag_quad=beta))
+    S = np.zeros((2, 3))
+    f, G = orc.sp4_init(P, S)
+    orc.sp4_step(P, S, f, G, 5000)
+    r = orc.sp4_fields(P, S, f)
+    mag = (-lam + np.sqrt(lam * lam + 4 * beta * np.linalg.norm(F0))) / (2 * beta)
+    ue = mag * F0 / np.linalg.norm(F0)
+    assert np.allclose(r["ux"], ue[0], rtol=1e-12) and np.allclose(r["uy"], ue[1], rtol=1e-12)
+
+
+def test_remark4_hydrostatic_rest(orc):
+    # walls in y, a uniform force towards a wall: the fluid stays at rest and
+    # grad p = F exactly (bounce-back acts on g = f - G/2)
+    ny, Fy = 16, -1e-5
+    P = orc.sp_params(dict(nx=2, ny=ny, walls_y=1, nu=0.1, force_y=Fy))
+    S = np.zeros((ny, 2))
+    f, G = orc.sp4_init(P, S)
+    orc.sp4_step(P, S, f, G, 20000)
+    r = orc.sp4_fields(P, S, f)
+    assert np.abs(r["uy"]).max() < 1e-15 and np.abs(r["ux"]).max() < 1e-15
+    assert np.allclose(np.diff(r["p"][:, 0]), Fy, rtol=1e-9, atol=0)
+
+
+def test_remark4_poiseuille_exact_at_the_magic_tau(orc):
+    ny, F = 24, 1e-6
+    nu = CS2 * np.sqrt(3.0 / 16.0)
+    P = orc.sp_params(dict(nx=2, ny=ny, walls_y=1, nu=nu, force_x=F))
+    S = np.zeros((ny, 2))
+    f, G = orc.sp4_init(P, S)
+    orc.sp4_step(P, S, f, G, 30000)
+    ux = orc.sp4_fields(P, S, f)["ux"][:, 0]
+    y = np.arange(ny)
+    ua = F / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux - ua)) / ua.max() < 1e-11
+
+
+def test_remark4_brinkman_second_order(orc):
+    # -nu u'' + lambda u = F between walls at y = +-H: u = (F/lambda)(1 - cosh(ky)/cosh(kH)),
+    # k = sqrt(lambda/nu); lambda scaled with 1/ny^2 keeps kH fixed while refining
+    def err(ny, steps):
+        nu, F, lam = 0.1, 1e-5, 1.6 / ny ** 2
+        P = orc.sp_params(dict(nx=2, ny=ny, walls_y=1, nu=nu, force_x=F, drag_lin=lam))
+        S = np.zeros((ny, 2))
+        f, G = orc.sp4_init(P, S)
+        orc.sp4_step(P, S, f, G, steps)
+        ux = orc.sp4_fields(P, S, f)["ux"][:, 0]
+        y = np.arange(ny) + 0.5 - ny / 2
+        k = np.sqrt(lam / nu)
+        ua = F / lam * (1 - np.cosh(k * y) / np.cosh(k * ny / 2))
+        return np.abs(ux - ua).max() / ua.max()
+    e16, e32 = err(16, 40000), err(32, 80000)
+    assert e32 < 2e-3 and 3.0 < e16 / e32 < 5.0
+
+
+def test_remark4_source_flow_with_drag(orc):
+    # div u = S fixes u = -(A/k) cos kx; the linear drag removes the mean momentum
+    errs = []
+    for nx in (32, 64):
+        P = orc.sp_params(dict(nx=nx, ny=2, nu=0.1, drag_lin=0.002))
+        k, A = 2 * np.pi / nx, 1e-4
+        x = np.arange(nx)
+        S = np.tile(A * np.sin(k * x), (2, 1))
+        f, G = orc.sp4_init(P, S)
+        orc.sp4_step(P, S, f, G, 80000)
+        r = orc.sp4_fields(P, S, f)
+        assert np.abs(r["uy"]).max() == 0.0
+        ua = -(A / k) * np.cos(k * x)
+        errs.append(np.max(np.abs(r["ux"][0] - ua)) / np.max(np.abs(ua)))
+    assert errs[1] < 1e-3 and 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_remark4_translation_equivariance(orc):
+    P = orc.sp_params(dict(nx=12, ny=10, nu=0.05, force_x=1e-5, force_y=-2e-5, drag_lin=0.01, drag_quad=0.3))
+    S = RNG.uniform(-1e-3, 1e-3, (10, 12))
+    a, Ga = orc.sp4_init(P, S)
+    Sb = np.roll(S, (3, 5), axis=(0, 1))
+    b, Gb = orc.sp4_init(P, Sb)
+    orc.sp4_step(P, S, a, Ga, 20)
+    orc.sp4_step(P, Sb, b, Gb, 20)
+    assert np.array_equal(np.roll(a, (3, 5), axis=(1, 2)), b)
