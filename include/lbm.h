@@ -357,13 +357,29 @@ void lbm_destroy(lbm_ctx* ctx);
  * Q = (2/d) rho c_s^2 - xi/(tau_g - 1/2), div u by Eq. 30a (mirror at walls);
  * the total mass grows by sum S a step. Two kernels a step. */
 enum { LBM_SP_INCOMPRESSIBLE_SOURCE = 0, LBM_SP_NEARLY_INCOMPRESSIBLE = 1 };
+/* scheme LBM_SP_SCHEME_REMARK4 (with model LBM_SP_INCOMPRESSIBLE_SOURCE only)
+ * evolves the Remark 3 model with the explicit discretization of D_i G_i of
+ * Remark 4, for a velocity-dependent force F(u) = F_0 - (drag_lin + drag_quad
+ * |u|) u (F_0 = (force_x, force_y)): the populations f are not shifted by G/2,
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq)/tau_g + G_i(x, t)
+ *                         + [G_i(x + c_i, t) - G_i(x, t - 1)] / 2,
+ * u = sum c f (explicit), p = c_s^2/(1 - w_0) [sum_{i != 0} f_i + s_0(u) +
+ * tau_g G_0]. G_i(x + c_i, t) across a wall is taken at the mirrored cell;
+ * bounce-back acts on f - G/2; G at t = -1 is G at t = 0. G at t - 1 is
+ * recomputed from u at t - 1 (kept, two planes) and S. Two kernels a step.
+ * The scheme of Eq. 24 (LBM_SP_SCHEME_EQ24) needs drag_lin = drag_quad = 0. */
+enum { LBM_SP_SCHEME_EQ24 = 0, LBM_SP_SCHEME_REMARK4 = 1 };
 typedef struct lbm_sp_params {
     int32_t nx, ny;
     int32_t bc_y;             /* LBM_BC_*                                                */
     int32_t model;            /* LBM_SP_* (Remark 3 or Remark 1)                          */
     double nu;                /* kinematic viscosity (> 0)                               */
     double xi;                /* bulk viscosity in Q (>= 0; 0 under Stokes' hypothesis)  */
-    double force_x, force_y;  /* uniform body force                                       */
+    double force_x, force_y;  /* uniform body force F_0                                   */
+    int32_t scheme;           /* LBM_SP_SCHEME_*                                          */
+    int32_t reserved;         /* must be 0                                                */
+    double drag_lin;          /* lambda >= 0 of F(u) (Remark 4 scheme only)               */
+    double drag_quad;         /* beta >= 0 of F(u) (Remark 4 scheme only)                 */
 } lbm_sp_params;
 
 typedef struct lbm_sp_ctx lbm_sp_ctx;
@@ -388,8 +404,8 @@ lbm_status lbm_sp_step(lbm_sp_ctx* ctx, int nsteps);
  * Synchronises. */
 lbm_status lbm_sp_get_fields(lbm_sp_ctx* ctx, unsigned mask, double* host_out);
 
-/* The 9 population planes in FP64 (Remark 3: g_0 shifted by rho_0; Remark 1:
- * as they are). Synchronises. */
+/* The 9 population planes in FP64 (Remark 3: g_0 shifted by rho_0 = 0;
+ * Remark 1: as they are; Remark 4 scheme: the unshifted f). Synchronises. */
 lbm_status lbm_sp_get_populations(lbm_sp_ctx* ctx, double* host_g);
 
 const char* lbm_sp_last_error(const lbm_sp_ctx* ctx);

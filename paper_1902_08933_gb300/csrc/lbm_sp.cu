@@ -18,6 +18,12 @@
 // a step is two kernels (rho and u, then the collision). The populations are
 // stored as g_i - w_i (their rest state at rho = 1), so that FP32 storage keeps
 // the small deviations that carry the flow: rho = 1 + sum(g - w) + S/2.
+//
+// scheme LBM_SP_SCHEME_REMARK4: the Remark 3 model with a velocity-dependent
+// force F(u) = F_0 - (lambda + beta |u|) u, evolved with the explicit D_i G_i of
+// Remark 4 (unshifted f, u = sum c f). A first kernel writes u; the second
+// rebuilds G_i at the destination x + c_i from its u and S, and G_i(x, t - 1)
+// from u at t - 1 (two planes kept instead of the nine planes of G).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -36,6 +42,7 @@ static_assert(sopp(1) == 3 && sopp(2) == 4 && sopp(5) == 7 && sopp(6) == 8 && so
 struct SpConst {
     int nx, ny, walls;
     double inv_tau, src, tgm, Qc, fx, fy;   // 1/tau_g, 1 - 1/(2 tau_g), tau_g - 1/2, Q, F
+    double dl, dq;                          // drag of the Remark 4 scheme: F(u) = F - (dl + dq |u|) u
 };
 
 template <typename R>
@@ -208,6 +215,123 @@ __global__ void sp1_fields_kernel(const R* __restrict__ g, const R* __restrict__
     if (mask & LBM_FIELD_RHO) out[(slot++) * N + c] = 1.0 + double(drho);
 }
 
+// ---- Remark 4 scheme (on the Remark 3 model) ----
+template <typename R>
+__device__ __forceinline__ void sp4_u(const R f[kQ], R& ux, R& uy) {
+    R jx = R(0), jy = R(0);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        if (sx(i)) jx += sx(i) > 0 ? f[i] : -f[i];
+        if (sy(i)) jy += sy(i) > 0 ? f[i] : -f[i];
+    }
+    ux = jx;
+    uy = jy;
+}
+
+template <typename R>
+__device__ __forceinline__ void sp4_force(const SpConst& K, R ux, R uy, R& Fx, R& Fy) {
+    const R k = R(K.dl) + R(K.dq) * sqrt(ux * ux + uy * uy);
+    Fx = R(K.fx) - k * ux;
+    Fy = R(K.fy) - k * uy;
+}
+
+// G_i of Remark 3 with force F at velocity u, direction i
+template <typename R>
+__device__ __forceinline__ R sp4_G(const SpConst& K, int i, R S, R ux, R uy, R Fx, R Fy) {
+    const R cu = R(sx(i)) * ux + R(sy(i)) * uy, cF = R(sx(i)) * Fx + R(sy(i)) * Fy;
+    const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
+    return R(sw(i)) * (S + R(3) * cF + R(9) * cu * cF - R(3) * (ux * Fx + uy * Fy) +
+                       R(4.5) * (c2 - R(2.0 / 3.0)) * R(K.Qc) * S);
+}
+
+// u = sum c f of every cell (the update at x needs G at x + c_i, so u first)
+template <typename R>
+__global__ void __launch_bounds__(256) sp4_moments_kernel(const R* __restrict__ fin, long long N,
+                                                          R* __restrict__ unow) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    R f[kQ], ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[i] = fin[i * N + c];
+    sp4_u(f, ux, uy);
+    unow[c] = ux;
+    unow[N + c] = uy;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin, R* __restrict__ fout,
+                                                       const R* __restrict__ src, const R* __restrict__ unow,
+                                                       const R* __restrict__ uprev, long long N, SpConst K) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+    R f[kQ], G[kQ], ux, uy, Fx, Fy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[i] = fin[i * N + c];
+    const R S = src[c];
+    sp4_u(f, ux, uy);
+    sp4_force(K, ux, uy, Fx, Fy);
+    R rest = R(0);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        G[i] = sp4_G(K, i, S, ux, uy, Fx, Fy);
+        if (i) rest += f[i];
+    }
+    const R uu = ux * ux + uy * uy;
+    // Eq. 28 for the unshifted f: c_s^2 / (1 - w_0) = 3/5, s_0(u) = -(2/3) u.u, tau_g G_0
+    const R p = R(0.6) * (rest - R(2.0 / 3.0) * uu + R(K.tgm + 0.5) * G[0]);
+    const R upx = uprev[c], upy = uprev[N + c];
+    R Fpx, Fpy;
+    sp4_force(K, upx, upy, Fpx, Fpy);
+    const R ig = R(K.inv_tau);
+    const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
+    const int xs[3] = {x == 0 ? K.nx - 1 : x - 1, x, x == K.nx - 1 ? 0 : x + 1};
+    const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
+                       K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool wall = (sy(i) > 0 && top) || (sy(i) < 0 && bot);
+        // G_i(x + c_i, t): the destination cell, mirrored about a wall
+        const long long n = (long long)(wall ? y : ys[sy(i) + 1]) * K.nx + xs[sx(i) + 1];
+        const R nux = unow[n], nuy = unow[N + n];
+        R nFx, nFy;
+        sp4_force(K, nux, nuy, nFx, nFy);
+        const R Gn = sp4_G(K, i, src[n], nux, nuy, nFx, nFy);
+        const R Gp = sp4_G(K, i, S, upx, upy, Fpx, Fpy);   // G_i(x, t - 1)
+        const R cu = R(sx(i)) * ux + R(sy(i)) * uy;
+        const R si = R(sw(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        const R geq = i == 0 ? R(3) * p * (R(sw(0)) - R(1)) + si : R(3) * p * R(sw(i)) + si;
+        const R post = f[i] - (f[i] - geq) * ig + G[i] + R(0.5) * (Gn - Gp);
+        if (wall) {
+            // bounce-back of g = f - G/2: leaves as i with G_i(x + c_i), returns as opp(i)
+            fout[sopp(i) * N + c] = post - R(0.5) * Gn + R(0.5) * G[sopp(i)];
+        } else {
+            fout[i * N + (long long)ys[sy(i) + 1] * K.nx + xs[sx(i) + 1]] = post;
+        }
+    }
+}
+
+template <typename R>
+__global__ void sp4_fields_kernel(const R* __restrict__ f, const R* __restrict__ src, long long N, SpConst K,
+                                  unsigned mask, double* __restrict__ out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    R fc[kQ], ux, uy, Fx, Fy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) fc[i] = f[i * N + c];
+    sp4_u(fc, ux, uy);
+    sp4_force(K, ux, uy, Fx, Fy);
+    R rest = R(0);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) rest += fc[i];
+    const R G0 = sp4_G(K, 0, src[c], ux, uy, Fx, Fy);
+    const R p = R(0.6) * (rest - R(2.0 / 3.0) * (ux * ux + uy * uy) + R(K.tgm + 0.5) * G0);
+    int slot = 0;
+    if (mask & LBM_FIELD_UX) out[(slot++) * N + c] = double(ux);
+    if (mask & LBM_FIELD_UY) out[(slot++) * N + c] = double(uy);
+    if (mask & LBM_FIELD_P) out[(slot++) * N + c] = double(p);
+}
+
 // populations g_i = stored + w_i, widened to FP64
 template <typename R>
 __global__ void sp1_widen_kernel(const R* __restrict__ in, double* __restrict__ out, long long N) {
@@ -252,7 +376,9 @@ struct lbm_sp_ctx {
     long long N = 0;
     void* g[2] = {nullptr, nullptr};
     void* src = nullptr;
-    void* ufield = nullptr;            // Remark 1: u of the current step (2 planes)
+    void* ufield = nullptr;            // Remark 1: u of the current step (2 planes);
+                                       // Remark 4 scheme: u at t and t - 1 (2 x 2 planes)
+    int uprev = 0;                     // Remark 4 scheme: which half of ufield holds u at t - 1
     double* d_tmp = nullptr;           // staging for inputs and outputs
     int cur = 0;
     bool ready = false;
@@ -296,6 +422,13 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
     if (p.nx < 3 || p.ny < 3 || (long long)p.nx * p.ny >= (1LL << 31) / 9) return LBM_EINVAL;
     if (p.bc_y != LBM_BC_PERIODIC && p.bc_y != LBM_BC_BOUNCEBACK) return LBM_EINVAL;
     if (p.model != LBM_SP_INCOMPRESSIBLE_SOURCE && p.model != LBM_SP_NEARLY_INCOMPRESSIBLE) return LBM_EINVAL;
+    if ((p.scheme != LBM_SP_SCHEME_EQ24 && p.scheme != LBM_SP_SCHEME_REMARK4) || p.reserved != 0) return LBM_EINVAL;
+    if (!(std::isfinite(p.drag_lin) && p.drag_lin >= 0) || !(std::isfinite(p.drag_quad) && p.drag_quad >= 0))
+        return LBM_EINVAL;
+    // a velocity-dependent force makes Eq. 27a implicit: it needs the Remark 4 scheme,
+    // which is built on the Remark 3 model
+    if (p.scheme == LBM_SP_SCHEME_EQ24 && (p.drag_lin != 0 || p.drag_quad != 0)) return LBM_EINVAL;
+    if (p.scheme == LBM_SP_SCHEME_REMARK4 && p.model != LBM_SP_INCOMPRESSIBLE_SOURCE) return LBM_EINVAL;
     if (!(std::isfinite(p.nu) && p.nu > 0) || !(std::isfinite(p.xi) && p.xi >= 0) || !std::isfinite(p.force_x) ||
         !std::isfinite(p.force_y))
         return LBM_EINVAL;
@@ -306,13 +439,14 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
     c->N = (long long)p.nx * p.ny;
     const double tau = 3.0 * p.nu + 0.5;
     c->K = SpConst{p.nx, p.ny, p.bc_y == LBM_BC_BOUNCEBACK ? 1 : 0, 1.0 / tau, 1.0 - 0.5 / tau, tau - 0.5,
-                   1.0 / 3.0 - p.xi / (tau - 0.5), p.force_x, p.force_y};
+                   1.0 / 3.0 - p.xi / (tau - 0.5), p.force_x, p.force_y, p.drag_lin, p.drag_quad};
     const size_t e = sp_elem(precision);
     cudaError_t r;
     if ((r = cudaMalloc(&c->g[0], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->g[1], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->src, c->N * e)) != cudaSuccess ||
         (p.model == LBM_SP_NEARLY_INCOMPRESSIBLE && (r = cudaMalloc(&c->ufield, 2 * c->N * e)) != cudaSuccess) ||
+        (p.scheme == LBM_SP_SCHEME_REMARK4 && (r = cudaMalloc(&c->ufield, 4 * c->N * e)) != cudaSuccess) ||
         (r = cudaMalloc((void**)&c->d_tmp, kQ * c->N * sizeof(double))) != cudaSuccess) {
         sp_release(c);
         delete c;
@@ -348,6 +482,11 @@ lbm_status lbm_sp_init(lbm_sp_ctx* c, const double* source_host) {
     // Remark 1 g^eq = w_i at rho = 1 (stored shifted by w_i) -- zero either way
     if ((r = cudaMemsetAsync(c->g[0], 0, kQ * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
         return sp_cuda(c, r, "state reset");
+    // Remark 4 scheme: u at t = -1 is u at t = 0 = 0
+    c->uprev = 0;
+    if (c->p.scheme == LBM_SP_SCHEME_REMARK4 &&
+        (r = cudaMemsetAsync(c->ufield, 0, 4 * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
+        return sp_cuda(c, r, "state reset");
     if ((r = cudaStreamSynchronize(c->stream)) != cudaSuccess) return sp_cuda(c, r, "init");
     if ((r = cudaGetLastError()) != cudaSuccess) return sp_cuda(c, r, "init kernel");
     c->ready = true;
@@ -360,8 +499,28 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
     if (nsteps < 0) return sp_fail(c, LBM_EINVAL, "nsteps < 0");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
     const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE;
+    const bool r4 = c->p.scheme == LBM_SP_SCHEME_REMARK4;
     for (int s = 0; s < nsteps; ++s) {
-        if (m1) {
+        if (r4) {
+            const long long h = 2 * c->N;
+            const int un = 1 - c->uprev;
+            if (c->form == LBM_F64) {
+                const double* fi = static_cast<const double*>(c->g[c->cur]);
+                double* u = static_cast<double*>(c->ufield);
+                sp4_moments_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, u + un * h);
+                sp4_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
+                    fi, static_cast<double*>(c->g[1 - c->cur]), static_cast<const double*>(c->src), u + un * h,
+                    u + c->uprev * h, c->N, c->K);
+            } else {
+                const float* fi = static_cast<const float*>(c->g[c->cur]);
+                float* u = static_cast<float*>(c->ufield);
+                sp4_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, u + un * h);
+                sp4_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                    fi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), u + un * h,
+                    u + c->uprev * h, c->N, c->K);
+            }
+            c->uprev = un;
+        } else if (m1) {
             if (c->form == LBM_F64) {
                 const double* gi = static_cast<const double*>(c->g[c->cur]);
                 sp1_moments_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
@@ -400,7 +559,13 @@ lbm_status lbm_sp_get_fields(lbm_sp_ctx* c, unsigned mask, double* host_out) {
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
     const int nf = ((mask & LBM_FIELD_UX) ? 1 : 0) + ((mask & LBM_FIELD_UY) ? 1 : 0) + ((mask & LBM_FIELD_P) ? 1 : 0) +
                    ((mask & LBM_FIELD_RHO) ? 1 : 0);
-    if (m1 && c->form == LBM_F64)
+    if (c->p.scheme == LBM_SP_SCHEME_REMARK4 && c->form == LBM_F64)
+        sp4_fields_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
+            static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
+    else if (c->p.scheme == LBM_SP_SCHEME_REMARK4)
+        sp4_fields_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+            static_cast<const float*>(c->g[c->cur]), static_cast<const float*>(c->src), c->N, c->K, mask, c->d_tmp);
+    else if (m1 && c->form == LBM_F64)
         sp1_fields_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
             static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
     else if (m1)

@@ -73,7 +73,8 @@ class lbm_monitor(ctypes.Structure):
 class lbm_sp_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
                 ("model", ctypes.c_int32), ("nu", ctypes.c_double), ("xi", ctypes.c_double),
-                ("force_x", ctypes.c_double), ("force_y", ctypes.c_double)]
+                ("force_x", ctypes.c_double), ("force_y", ctypes.c_double), ("scheme", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("drag_lin", ctypes.c_double), ("drag_quad", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -371,7 +372,10 @@ def _check_sp(st, ctx=None):
 
 
 class SourceFlow:
-    """One single-phase simulation of Remark 3 (div u = S) on the GPU."""
+    """One single-phase simulation with a mass source on the GPU: Remark 3
+    (div u = S; cfg "model": 0) or Remark 1 ("model": 1); cfg "scheme": 1 runs
+    Remark 3 with the explicit D_i G_i of Remark 4 and the velocity-dependent
+    force F_0 - (drag_lin + drag_quad |u|) u."""
 
     def __init__(self, cfg: dict, precision="f64", stream=None, source=None):
         p = lbm_sp_params()
@@ -381,6 +385,8 @@ class SourceFlow:
         self.model = p.model
         p.nu, p.xi = float(cfg["nu"]), float(cfg.get("xi", 0.0))
         p.force_x, p.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))
+        p.scheme, p.reserved = int(cfg.get("scheme", 0)), 0
+        p.drag_lin, p.drag_quad = float(cfg.get("drag_lin", 0.0)), float(cfg.get("drag_quad", 0.0))
         self.nx, self.ny = p.nx, p.ny
         prec = FORMS[precision] if isinstance(precision, str) else int(precision)
         out = _VP()

@@ -82,8 +82,14 @@ def test_create_rejects_bad_input_without_touching_cuda(L):
     sp = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
     spo = ctypes.c_void_p(1234)
     for field, value in (("nx", 2), ("bc_y", 5), ("model", 2), ("nu", 0.0), ("xi", -1.0),
-                         ("force_x", float("nan"))):
+                         ("force_x", float("nan")), ("scheme", 2), ("reserved", 1),
+                         ("drag_lin", 0.1), ("drag_quad", 0.1)):   # drag needs the Remark 4 scheme
         bad = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
+        setattr(bad, field, value)
+        assert lib.lbm_sp_create(ctypes.byref(bad), 0, None, ctypes.byref(spo)) == L.LBM_EINVAL
+        assert spo.value is None
+    for field, value in (("drag_lin", -1.0), ("drag_quad", float("inf")), ("model", 1)):
+        bad = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0, 1)   # Remark 4 scheme
         setattr(bad, field, value)
         assert lib.lbm_sp_create(ctypes.byref(bad), 0, None, ctypes.byref(spo)) == L.LBM_EINVAL
         assert spo.value is None

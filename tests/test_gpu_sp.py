@@ -1,5 +1,6 @@
 """GPU single-phase models of Remark 3 (div u = S) and Remark 1 (nearly
-incompressible, mass source) versus their FP64 oracles, and
+incompressible, mass source), and Remark 3 under the explicit D_iG_i scheme of
+Remark 4 with a drag force, versus their FP64 oracles, and
 the closed-form checks of its oracle pins run on the GPU path."""
 import numpy as np
 import pytest
@@ -119,3 +120,76 @@ def test_remark1_mass_source_flow(L, report, form, bar):
     err = np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua))
     report(err=err)
     assert err < bar
+
+
+# ---------------------------------------------------------------- Remark 4
+@pytest.mark.parametrize("walls,drag", [(0, (0.0, 0.0)), (1, (0.0, 0.0)), (0, (0.01, 0.4)), (1, (0.01, 0.4))])
+def test_remark4_matches_oracle(L, orc, walls, drag):
+    cfg = dict(nx=37, ny=23, walls_y=walls, nu=0.07, xi=0.02, force_x=2e-5, force_y=-1e-5,
+               drag_lin=drag[0], drag_quad=drag[1])
+    S = 1e-4 * np.sin(2 * np.pi * np.arange(37) / 37)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
+    S = np.ascontiguousarray(S)
+    P = orc.sp_params(cfg)
+    f, G = orc.sp4_init(P, S)
+    orc.sp4_step(P, S, f, G, 40)
+    ref = orc.sp4_fields(P, S, f)
+    with L.SourceFlow(dict(cfg, scheme=1), "f64", source=S) as sim:
+        sim.step(40)
+        got, ff = sim.fields(), sim.populations()
+    assert rel(ff, f) < 1e-12
+    for k in ("ux", "uy", "p"):
+        assert rel(got[k], ref[k]) < 1e-12, (k, rel(got[k], ref[k]))
+    with L.SourceFlow(dict(cfg, scheme=1), "f32", source=S) as sim:
+        sim.step(40)
+        got = sim.fields()
+    for k in ("ux", "uy", "p"):
+        assert rel(got[k], ref[k]) < 1e-4, (k, rel(got[k], ref[k]))
+
+
+def test_remark4_uniform_state_is_adams_bashforth(L):
+    lam, beta, F0 = 0.01, 0.5, np.array([1e-4, -5e-5])
+    cfg = dict(nx=4, ny=3, nu=0.1, force_x=F0[0], force_y=F0[1], drag_lin=lam, drag_quad=beta, scheme=1)
+
+    def Fu(u):
+        return F0 - (lam + beta * np.linalg.norm(u)) * u
+    u, up = np.zeros(2), np.zeros(2)
+    with L.SourceFlow(cfg, "f64", source=np.zeros((3, 4))) as sim:
+        for _ in range(30):
+            sim.step(1)
+            u, up = u + 1.5 * Fu(u) - 0.5 * Fu(up), u
+            r = sim.fields()
+            assert np.allclose(r["ux"], u[0], rtol=0, atol=1e-17) and np.allclose(r["uy"], u[1], rtol=0, atol=1e-17)
+
+
+def test_remark4_walls_rest_and_poiseuille(L):
+    ny, Fy = 16, -1e-5
+    with L.SourceFlow(dict(nx=3, ny=ny, walls_y=1, nu=0.1, force_y=Fy, scheme=1), "f64",
+                      source=np.zeros((ny, 3))) as sim:
+        sim.step(20000)
+        r = sim.fields()
+    assert np.abs(r["uy"]).max() < 1e-15 and np.allclose(np.diff(r["p"][:, 0]), Fy, rtol=1e-9, atol=0)
+    ny, F = 24, 1e-6
+    nu = CS2 * np.sqrt(3.0 / 16.0)
+    with L.SourceFlow(dict(nx=3, ny=ny, walls_y=1, nu=nu, force_x=F, scheme=1), "f64",
+                      source=np.zeros((ny, 3))) as sim:
+        sim.step(30000)
+        ux = sim.fields()["ux"][:, 0]
+    y = np.arange(ny)
+    ua = F / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux - ua)) / ua.max() < 1e-11
+
+
+@pytest.mark.parametrize("form", ["f64", "f32"])
+def test_remark4_brinkman(L, report, form):
+    ny, nu, F = 32, 0.1, 1e-5
+    lam = 1.6 / ny ** 2
+    with L.SourceFlow(dict(nx=3, ny=ny, walls_y=1, nu=nu, force_x=F, drag_lin=lam, scheme=1), form,
+                      source=np.zeros((ny, 3))) as sim:
+        sim.step(80000)
+        ux = sim.fields()["ux"][:, 0]
+    y = np.arange(ny) + 0.5 - ny / 2
+    k = np.sqrt(lam / nu)
+    ua = F / lam * (1 - np.cosh(k * y) / np.cosh(k * ny / 2))
+    err = np.abs(ux - ua).max() / ua.max()
+    report(err=err)
+    assert err < 2e-3
