@@ -291,7 +291,7 @@ def kernel_run(args):
         if model == 4:
             cfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
         sim = lbm.SourceFlow(cfg, form, stream=stream.cuda_stream, source=src)
-        bpl = {0: 76, 1: 132, 4: 136}[model] * (2 if form == "f64" else 1)
+        bpl = {0: 76, 1: 132, 4: 160}[model] * (2 if form == "f64" else 1)
     sim.step(max(args.warmup, 2))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -481,12 +481,12 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     # Remark 1 (two kernels a step): (9 + 1) reads + 2 writes of u, then
     # 9 + 1 + 2 reads and 9 writes, so 264 / 132 bytes a cell
     sp1 = {"workload": "source_flow_remark1_4096x4096", "cells": n * n}
-    # Remark 4 scheme with a drag force (two kernels): 9 reads and 2 writes of u,
-    # then 9 + 1 + 2 + 2 reads (f, S, u at t and t - 1) and 9 writes: 272 / 136
+    # Remark 4 scheme with a drag force (two kernels): 9 reads and 4 writes (u, F),
+    # then 9 + 1 + 4 + 4 reads (f, S, u and F at t and t - 1) and 9 writes: 320 / 160
     sp4 = {"workload": "source_flow_remark4_drag_4096x4096", "cells": n * n}
     legs = {0: sp, 1: sp1, 4: sp4}
     for model, form, bpl in ((0, "f64", 152), (0, "f32", 76), (1, "f64", 264), (1, "f32", 132),
-                             (4, "f64", 272), (4, "f32", 136)):
+                             (4, "f64", 320), (4, "f32", 160)):
         cfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
         if model == 4:
             cfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)

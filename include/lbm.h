@@ -366,7 +366,8 @@ enum { LBM_SP_INCOMPRESSIBLE_SOURCE = 0, LBM_SP_NEARLY_INCOMPRESSIBLE = 1 };
  * u = sum c f (explicit), p = c_s^2/(1 - w_0) [sum_{i != 0} f_i + s_0(u) +
  * tau_g G_0]. G_i(x + c_i, t) across a wall is taken at the mirrored cell;
  * bounce-back acts on f - G/2; G at t = -1 is G at t = 0. G at t - 1 is
- * recomputed from u at t - 1 (kept, two planes) and S. Two kernels a step.
+ * recomputed from u and F(u) at t - 1 (kept, four planes) and S. Two kernels
+ * a step.
  * The scheme of Eq. 24 (LBM_SP_SCHEME_EQ24) needs drag_lin = drag_quad = 0. */
 enum { LBM_SP_SCHEME_EQ24 = 0, LBM_SP_SCHEME_REMARK4 = 1 };
 typedef struct lbm_sp_params {

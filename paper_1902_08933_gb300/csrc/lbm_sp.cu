@@ -22,8 +22,8 @@
 // scheme LBM_SP_SCHEME_REMARK4: the Remark 3 model with a velocity-dependent
 // force F(u) = F_0 - (lambda + beta |u|) u, evolved with the explicit D_i G_i of
 // Remark 4 (unshifted f, u = sum c f). A first kernel writes u; the second
-// rebuilds G_i at the destination x + c_i from its u and S, and G_i(x, t - 1)
-// from u at t - 1 (two planes kept instead of the nine planes of G).
+// rebuilds G_i at the destination x + c_i from its u, F(u) and S, and G_i(x, t - 1)
+// from u and F at t - 1 (four planes kept instead of the nine planes of G).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -244,18 +244,22 @@ __device__ __forceinline__ R sp4_G(const SpConst& K, int i, R S, R ux, R uy, R F
                        R(4.5) * (c2 - R(2.0 / 3.0)) * R(K.Qc) * S);
 }
 
-// u = sum c f of every cell (the update at x needs G at x + c_i, so u first)
+// u = sum c f and F(u) of every cell, four planes (the update at x needs G at
+// x + c_i, so these first; F is kept so that no neighbour evaluates the drag)
 template <typename R>
 __global__ void __launch_bounds__(256) sp4_moments_kernel(const R* __restrict__ fin, long long N,
-                                                          R* __restrict__ unow) {
+                                                          SpConst K, R* __restrict__ unow) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    R f[kQ], ux, uy;
+    R f[kQ], ux, uy, Fx, Fy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[i] = fin[i * N + c];
     sp4_u(f, ux, uy);
+    sp4_force(K, ux, uy, Fx, Fy);
     unow[c] = ux;
     unow[N + c] = uy;
+    unow[2 * N + c] = Fx;
+    unow[3 * N + c] = Fy;
 }
 
 template <typename R>
@@ -265,12 +269,12 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
-    R f[kQ], G[kQ], ux, uy, Fx, Fy;
+    R f[kQ], G[kQ], ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[i] = fin[i * N + c];
     const R S = src[c];
     sp4_u(f, ux, uy);
-    sp4_force(K, ux, uy, Fx, Fy);
+    const R Fx = unow[2 * N + c], Fy = unow[3 * N + c];
     R rest = R(0);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -280,9 +284,7 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
     const R uu = ux * ux + uy * uy;
     // Eq. 28 for the unshifted f: c_s^2 / (1 - w_0) = 3/5, s_0(u) = -(2/3) u.u, tau_g G_0
     const R p = R(0.6) * (rest - R(2.0 / 3.0) * uu + R(K.tgm + 0.5) * G[0]);
-    const R upx = uprev[c], upy = uprev[N + c];
-    R Fpx, Fpy;
-    sp4_force(K, upx, upy, Fpx, Fpy);
+    const R upx = uprev[c], upy = uprev[N + c], Fpx = uprev[2 * N + c], Fpy = uprev[3 * N + c];
     const R ig = R(K.inv_tau);
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
     const int xs[3] = {x == 0 ? K.nx - 1 : x - 1, x, x == K.nx - 1 ? 0 : x + 1};
@@ -293,10 +295,7 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
         const bool wall = (sy(i) > 0 && top) || (sy(i) < 0 && bot);
         // G_i(x + c_i, t): the destination cell, mirrored about a wall
         const long long n = (long long)(wall ? y : ys[sy(i) + 1]) * K.nx + xs[sx(i) + 1];
-        const R nux = unow[n], nuy = unow[N + n];
-        R nFx, nFy;
-        sp4_force(K, nux, nuy, nFx, nFy);
-        const R Gn = sp4_G(K, i, src[n], nux, nuy, nFx, nFy);
+        const R Gn = sp4_G(K, i, src[n], unow[n], unow[N + n], unow[2 * N + n], unow[3 * N + n]);
         const R Gp = sp4_G(K, i, S, upx, upy, Fpx, Fpy);   // G_i(x, t - 1)
         const R cu = R(sx(i)) * ux + R(sy(i)) * uy;
         const R si = R(sw(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
@@ -363,6 +362,12 @@ __global__ void sp_convert_kernel(const double* __restrict__ in, R* __restrict__
 }
 
 template <typename R>
+__global__ void sp_fill_kernel(R* __restrict__ out, double v, long long n) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[c] = R(v);
+}
+
+template <typename R>
 __global__ void sp_widen_kernel(const R* __restrict__ in, double* __restrict__ out, long long n) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) out[c] = double(in[c]);
@@ -377,7 +382,7 @@ struct lbm_sp_ctx {
     void* g[2] = {nullptr, nullptr};
     void* src = nullptr;
     void* ufield = nullptr;            // Remark 1: u of the current step (2 planes);
-                                       // Remark 4 scheme: u at t and t - 1 (2 x 2 planes)
+                                       // Remark 4 scheme: u, F(u) at t and t - 1 (2 x 4 planes)
     int uprev = 0;                     // Remark 4 scheme: which half of ufield holds u at t - 1
     double* d_tmp = nullptr;           // staging for inputs and outputs
     int cur = 0;
@@ -446,7 +451,7 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
         (r = cudaMalloc(&c->g[1], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->src, c->N * e)) != cudaSuccess ||
         (p.model == LBM_SP_NEARLY_INCOMPRESSIBLE && (r = cudaMalloc(&c->ufield, 2 * c->N * e)) != cudaSuccess) ||
-        (p.scheme == LBM_SP_SCHEME_REMARK4 && (r = cudaMalloc(&c->ufield, 4 * c->N * e)) != cudaSuccess) ||
+        (p.scheme == LBM_SP_SCHEME_REMARK4 && (r = cudaMalloc(&c->ufield, 8 * c->N * e)) != cudaSuccess) ||
         (r = cudaMalloc((void**)&c->d_tmp, kQ * c->N * sizeof(double))) != cudaSuccess) {
         sp_release(c);
         delete c;
@@ -485,8 +490,19 @@ lbm_status lbm_sp_init(lbm_sp_ctx* c, const double* source_host) {
     // Remark 4 scheme: u at t = -1 is u at t = 0 = 0
     c->uprev = 0;
     if (c->p.scheme == LBM_SP_SCHEME_REMARK4 &&
-        (r = cudaMemsetAsync(c->ufield, 0, 4 * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
+        (r = cudaMemsetAsync(c->ufield, 0, 8 * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
         return sp_cuda(c, r, "state reset");
+    if (c->p.scheme == LBM_SP_SCHEME_REMARK4) {   // F(u = 0) = F_0 at t = -1
+        const double* F0 = &c->p.force_x;
+        for (int a = 0; a < 2; ++a) {
+            if (c->form == LBM_F64)
+                sp_fill_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
+                    static_cast<double*>(c->ufield) + (2 + a) * c->N, F0[a], c->N);
+            else
+                sp_fill_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                    static_cast<float*>(c->ufield) + (2 + a) * c->N, F0[a], c->N);
+        }
+    }
     if ((r = cudaStreamSynchronize(c->stream)) != cudaSuccess) return sp_cuda(c, r, "init");
     if ((r = cudaGetLastError()) != cudaSuccess) return sp_cuda(c, r, "init kernel");
     c->ready = true;
@@ -502,19 +518,19 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
     const bool r4 = c->p.scheme == LBM_SP_SCHEME_REMARK4;
     for (int s = 0; s < nsteps; ++s) {
         if (r4) {
-            const long long h = 2 * c->N;
+            const long long h = 4 * c->N;
             const int un = 1 - c->uprev;
             if (c->form == LBM_F64) {
                 const double* fi = static_cast<const double*>(c->g[c->cur]);
                 double* u = static_cast<double*>(c->ufield);
-                sp4_moments_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, u + un * h);
+                sp4_moments_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, c->K, u + un * h);
                 sp4_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
                     fi, static_cast<double*>(c->g[1 - c->cur]), static_cast<const double*>(c->src), u + un * h,
                     u + c->uprev * h, c->N, c->K);
             } else {
                 const float* fi = static_cast<const float*>(c->g[c->cur]);
                 float* u = static_cast<float*>(c->ufield);
-                sp4_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, u + un * h);
+                sp4_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, c->K, u + un * h);
                 sp4_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
                     fi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), u + un * h,
                     u + c->uprev * h, c->N, c->K);
