@@ -287,10 +287,10 @@ def kernel_run(args):
         src = np.ascontiguousarray(1e-4 * np.sin(2 * np.pi * np.arange(n) / n)[None, :] * np.ones((n, 1)))
         form = "f64" if args.form == "f64" else "f32"
         model = {"source_flow": 0, "source_flow_remark1": 1, "source_flow_remark4": 4}[args.kernel_run]
-        cfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
+        spcfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
         if model == 4:
-            cfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
-        sim = lbm.SourceFlow(cfg, form, stream=stream.cuda_stream, source=src)
+            spcfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
+        sim = lbm.SourceFlow(spcfg, form, stream=stream.cuda_stream, source=src)
         bpl = {0: 76, 1: 132, 4: 160}[model] * (2 if form == "f64" else 1)
     sim.step(max(args.warmup, 2))
     torch.cuda.synchronize()
@@ -487,10 +487,10 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     legs = {0: sp, 1: sp1, 4: sp4}
     for model, form, bpl in ((0, "f64", 152), (0, "f32", 76), (1, "f64", 264), (1, "f32", 132),
                              (4, "f64", 320), (4, "f32", 160)):
-        cfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
+        spcfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
         if model == 4:
-            cfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
-        with lbm.SourceFlow(cfg, form, stream=stream.cuda_stream, source=src) as sim:
+            spcfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
+        with lbm.SourceFlow(spcfg, form, stream=stream.cuda_stream, source=src) as sim:
             sim.step(4)
             torch.cuda.synchronize()
             Ks = max(20, K // 4)
