@@ -29,8 +29,12 @@
 #include <string>
 
 #include "lbm.h"
+#include "lbm_device.cuh"   // lbm::F2, two cells' FP32 values in packed instructions
 
 namespace {
+
+using lbm::F2;
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
 
 constexpr int kQ = 9;
 __host__ __device__ constexpr int sx(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
@@ -108,6 +112,46 @@ __global__ void __launch_bounds__(256) sp_step_kernel(const R* __restrict__ gin,
             dst = (long long)ys[sy(i) + 1] * K.nx + xs[sx(i) + 1];
         }
         gout[k * N + dst] = post;
+    }
+}
+
+// FP32 step of Remark 3 with two horizontally adjacent cells (x, x + 1), x
+// even, per thread, computed together in packed FP32 instructions (F2): the
+// loads, the S read and the stores of directions with c_x = 0 are 8-byte
+// pairs; directions with c_x != 0 split into two 4-byte stores. nx even.
+__global__ void __launch_bounds__(256) sp_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
+                                                         const float* __restrict__ src, long long N, SpConst K) {
+    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+    F2 g[kQ], G[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = F2(*reinterpret_cast<const float2*>(gin + i * N + c));
+    const F2 S(*reinterpret_cast<const float2*>(src + c));
+    const SpCell<F2> m = sp_moments(K, g, S, G);
+    const F2 uu = m.ux * m.ux + m.uy * m.uy;
+    const F2 ig = F2(float(K.inv_tau)), sg = F2(float(K.src));
+    const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
+    // destination columns of the left cell for c_x = -1, 0, +1 (the right cell is +1)
+    const int xl[3] = {x == 0 ? K.nx - 1 : x - 1, x, x + 1};
+    const int xr[3] = {x, x + 1, x + 2 == K.nx ? 0 : x + 2};
+    const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
+                       K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const F2 cu = float(sx(i)) * m.ux + float(sy(i)) * m.uy;
+        const F2 si = float(sw(i)) * (F2(3.f) * cu + F2(4.5f) * cu * cu - F2(1.5f) * uu);
+        const F2 geq = i == 0 ? F2(3.f) * m.p * F2(float(sw(0) - 1.0)) + si : F2(3.f) * m.p * F2(float(sw(i))) + si;
+        const F2 post = g[i] - (g[i] - geq) * ig + sg * G[i];
+        if ((sy(i) > 0 && top) || (sy(i) < 0 && bot)) {
+            *reinterpret_cast<float2*>(gout + sopp(i) * N + c) = post.v;
+        } else if (sx(i) == 0) {
+            *reinterpret_cast<float2*>(gout + i * N + (long long)ys[sy(i) + 1] * K.nx + x) = post.v;
+        } else {
+            const long long row = i * N + (long long)ys[sy(i) + 1] * K.nx;
+            gout[row + xl[sx(i) + 1]] = post.v.x;
+            gout[row + xr[sx(i) + 1]] = post.v.y;
+        }
     }
 }
 
@@ -556,6 +600,10 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
             sp_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
                 static_cast<const double*>(c->g[c->cur]), static_cast<double*>(c->g[1 - c->cur]),
                 static_cast<const double*>(c->src), c->N, c->K);
+        else if (c->p.nx % 2 == 0)   // two cells a thread
+            sp_step_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(
+                static_cast<const float*>(c->g[c->cur]), static_cast<float*>(c->g[1 - c->cur]),
+                static_cast<const float*>(c->src), c->N, c->K);
         else
             sp_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
                 static_cast<const float*>(c->g[c->cur]), static_cast<float*>(c->g[1 - c->cur]),

@@ -24,10 +24,12 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
 
 
+# nx odd runs the one-cell FP32 kernel, nx even the two-cell one
+@pytest.mark.parametrize("nx", [37, 38])
 @pytest.mark.parametrize("walls,xi", [(0, 0.0), (1, 0.0), (0, 0.05), (1, 0.05)])
-def test_matches_oracle(L, orc, walls, xi):
-    cfg = dict(nx=37, ny=23, walls_y=walls, nu=0.07, xi=xi, force_x=2e-6, force_y=-1e-6)
-    S = 1e-4 * np.sin(2 * np.pi * np.arange(37) / 37)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
+def test_matches_oracle(L, orc, walls, xi, nx):
+    cfg = dict(nx=nx, ny=23, walls_y=walls, nu=0.07, xi=xi, force_x=2e-6, force_y=-1e-6)
+    S = 1e-4 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
     S = np.ascontiguousarray(S)
     P = orc.sp_params(cfg)
     g = orc.sp_init(P)
