@@ -35,6 +35,29 @@ namespace {
 
 using lbm::F2;
 __device__ __forceinline__ F2& operator+=(F2& a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2& operator*=(F2& a, F2 b) { return a = a * b; }
+// 1/x and sqrt(x), correctly rounded per lane, so one-cell and two-cell kernels agree
+template <typename R> __device__ __forceinline__ R sp_inv(R x) { return R(1) / x; }
+__device__ __forceinline__ F2 sp_inv(F2 x) { return F2(1.f / x.v.x, 1.f / x.v.y); }
+template <typename R> __device__ __forceinline__ R sp_sqrt(R x) { return sqrt(x); }
+__device__ __forceinline__ F2 sp_sqrt(F2 x) { return F2(sqrtf(x.v.x), sqrtf(x.v.y)); }
+
+// Loads and stores of cell pairs (x, x + 1), x even: one 8-byte access.
+__device__ __forceinline__ F2 ld2(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ void st2(float* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+// A row of a plane around the pair: columns x - 2 .. x + 3 as three pairs
+// (wrapping in x; nx even). at(dx) is the pair of columns (x + dx, x + 1 + dx).
+struct Row2 {
+    float2 l, m, r;
+    __device__ __forceinline__ Row2(const float* row, int x, int nx) {
+        l = *reinterpret_cast<const float2*>(row + (x == 0 ? nx - 2 : x - 2));
+        m = *reinterpret_cast<const float2*>(row + x);
+        r = *reinterpret_cast<const float2*>(row + (x + 2 == nx ? 0 : x + 2));
+    }
+    __device__ __forceinline__ F2 at(int dx) const {
+        return dx < 0 ? F2(l.y, m.x) : (dx > 0 ? F2(m.y, r.x) : F2(m));
+    }
+};
 
 constexpr int kQ = 9;
 __host__ __device__ constexpr int sx(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
@@ -42,6 +65,22 @@ __host__ __device__ constexpr int sy(int i) { return i == 2 || i == 5 || i == 6 
 __host__ __device__ constexpr double sw(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
 __host__ __device__ constexpr int sopp(int i) { return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 5 + 2) % 4 + 5); }
 static_assert(sopp(1) == 3 && sopp(2) == 4 && sopp(5) == 7 && sopp(6) == 8 && sopp(8) == 6, "D2Q9 opposites");
+
+// Push-streaming of direction i of a pair (x, x + 1), x even: with bounce, back
+// into the pair as the opposite direction (halfway wall); else to row yrow,
+// columns x + c_x and x + 1 + c_x (wrapped). c_x = 0 keeps the pair together.
+__device__ __forceinline__ void sp_store2(float* __restrict__ gout, long long N, long long c, int x, int yrow,
+                                          int nx, bool bounce, int i, F2 v) {
+    if (bounce) {
+        st2(gout + sopp(i) * N + c, v);
+    } else if (sx(i) == 0) {
+        st2(gout + i * N + (long long)yrow * nx + x, v);
+    } else {
+        const long long row = i * N + (long long)yrow * nx;
+        gout[row + (sx(i) < 0 ? (x == 0 ? nx - 1 : x - 1) : x + 1)] = v.v.x;
+        gout[row + (sx(i) < 0 ? x : (x + 2 == nx ? 0 : x + 2))] = v.v.y;
+    }
+}
 
 struct SpConst {
     int nx, ny, walls;
@@ -132,9 +171,6 @@ __global__ void __launch_bounds__(256) sp_step_x2_kernel(const float* __restrict
     const F2 uu = m.ux * m.ux + m.uy * m.uy;
     const F2 ig = F2(float(K.inv_tau)), sg = F2(float(K.src));
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
-    // destination columns of the left cell for c_x = -1, 0, +1 (the right cell is +1)
-    const int xl[3] = {x == 0 ? K.nx - 1 : x - 1, x, x + 1};
-    const int xr[3] = {x, x + 1, x + 2 == K.nx ? 0 : x + 2};
     const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
                        K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
 #pragma unroll
@@ -143,15 +179,7 @@ __global__ void __launch_bounds__(256) sp_step_x2_kernel(const float* __restrict
         const F2 si = float(sw(i)) * (F2(3.f) * cu + F2(4.5f) * cu * cu - F2(1.5f) * uu);
         const F2 geq = i == 0 ? F2(3.f) * m.p * F2(float(sw(0) - 1.0)) + si : F2(3.f) * m.p * F2(float(sw(i))) + si;
         const F2 post = g[i] - (g[i] - geq) * ig + sg * G[i];
-        if ((sy(i) > 0 && top) || (sy(i) < 0 && bot)) {
-            *reinterpret_cast<float2*>(gout + sopp(i) * N + c) = post.v;
-        } else if (sx(i) == 0) {
-            *reinterpret_cast<float2*>(gout + i * N + (long long)ys[sy(i) + 1] * K.nx + x) = post.v;
-        } else {
-            const long long row = i * N + (long long)ys[sy(i) + 1] * K.nx;
-            gout[row + xl[sx(i) + 1]] = post.v.x;
-            gout[row + xr[sx(i) + 1]] = post.v.y;
-        }
+        sp_store2(gout, N, c, x, ys[sy(i) + 1], K.nx, (sy(i) > 0 && top) || (sy(i) < 0 && bot), i, post);
     }
 }
 
@@ -168,7 +196,7 @@ __device__ __forceinline__ void sp1_moments(const SpConst& K, const R g[kQ], R S
     }
     drho = m0 + R(0.5) * S;
     rho = R(1) + drho;
-    const R ir = R(1) / rho;
+    const R ir = sp_inv(rho);
     ux = (jx + R(0.5) * R(K.fx)) * ir;
     uy = (jy + R(0.5) * R(K.fy)) * ir;
 }
@@ -243,6 +271,70 @@ __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin
     }
 }
 
+// Remark 1, FP32, two cells a thread (nx even): rho - 1 and u of the pair
+__global__ void __launch_bounds__(256) sp1_moments_x2_kernel(const float* __restrict__ gin,
+                                                             const float* __restrict__ src, long long N, SpConst K,
+                                                             float* __restrict__ ufield) {
+    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    F2 g[kQ], drho, rho, ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = ld2(gin + i * N + c);
+    sp1_moments(K, g, ld2(src + c), drho, rho, ux, uy);
+    st2(ufield + c, ux);
+    st2(ufield + N + c, uy);
+}
+
+__global__ void __launch_bounds__(256) sp1_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
+                                                          const float* __restrict__ src,
+                                                          const float* __restrict__ ufield, long long N, SpConst K) {
+    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+    F2 g[kQ], drho, rho, ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] = ld2(gin + i * N + c);
+    const F2 S = ld2(src + c);
+    sp1_moments(K, g, S, drho, rho, ux, uy);
+    // stencil rows: mirror at walls (reading Q7), wrap when periodic
+    const int yst[3] = {y == 0 ? (K.walls ? 0 : K.ny - 1) : y - 1, y,
+                        y == K.ny - 1 ? (K.walls ? K.ny - 1 : 0) : y + 1};
+    F2 divu(0.f);   // Eq. 30a applied to u
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const long long row = (long long)yst[r] * K.nx;
+        const Row2 UX(ufield + row, x, K.nx), UY(ufield + N + row, x, K.nx);
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            if (sy(i) + 1 != r) continue;
+            F2 cu(0.f);
+            if (sx(i)) cu += sx(i) > 0 ? UX.at(sx(i)) : -UX.at(sx(i));
+            if (sy(i)) cu += sy(i) > 0 ? UY.at(sx(i)) : -UY.at(sx(i));
+            divu += F2(float(sw(i))) * cu;
+        }
+    }
+    divu *= F2(3.f);
+    const F2 fx(float(K.fx)), fy(float(K.fy));
+    const F2 uF = ux * fx + uy * fy, uu = ux * ux + uy * uy;
+    const F2 Qd = (rho * F2(float(1.0 / 3.0)) + F2(float(K.Qc - 1.0 / 3.0))) * divu;
+    const F2 ig(float(K.inv_tau)), sg(float(K.src));
+    const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
+    const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
+                       K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const F2 cu = float(sx(i)) * ux + float(sy(i)) * uy, cF = float(sx(i)) * fx + float(sy(i)) * fy;
+        const float c2 = float(sx(i) * sx(i) + sy(i) * sy(i));
+        const F2 si = float(sw(i)) * (F2(3.f) * cu + F2(4.5f) * cu * cu - F2(1.5f) * uu);
+        const F2 geq = drho * F2(float(sw(i))) + rho * si;
+        const F2 Gi = float(sw(i)) * (S + F2(3.f) * cF + F2(9.f) * cu * cF - F2(3.f) * uF -
+                                      F2(4.5f) * (cu * cu - uu * F2(float(1.0 / 3.0))) * S +
+                                      F2(4.5f) * F2(c2 - float(2.0 / 3.0)) * Qd);
+        const F2 post = g[i] - (g[i] - geq) * ig + sg * Gi;
+        sp_store2(gout, N, c, x, ys[sy(i) + 1], K.nx, (sy(i) > 0 && top) || (sy(i) < 0 && bot), i, post);
+    }
+}
+
 template <typename R>
 __global__ void sp1_fields_kernel(const R* __restrict__ g, const R* __restrict__ src, long long N, SpConst K,
                                   unsigned mask, double* __restrict__ out) {
@@ -274,7 +366,7 @@ __device__ __forceinline__ void sp4_u(const R f[kQ], R& ux, R& uy) {
 
 template <typename R>
 __device__ __forceinline__ void sp4_force(const SpConst& K, R ux, R uy, R& Fx, R& Fy) {
-    const R k = R(K.dl) + R(K.dq) * sqrt(ux * ux + uy * uy);
+    const R k = R(K.dl) + R(K.dq) * sp_sqrt(ux * ux + uy * uy);
     Fx = R(K.fx) - k * ux;
     Fy = R(K.fy) - k * uy;
 }
@@ -351,6 +443,74 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
         } else {
             fout[i * N + (long long)ys[sy(i) + 1] * K.nx + xs[sx(i) + 1]] = post;
         }
+    }
+}
+
+// Remark 4 scheme, FP32, two cells a thread (nx even)
+__global__ void __launch_bounds__(256) sp4_moments_x2_kernel(const float* __restrict__ fin, long long N,
+                                                             SpConst K, float* __restrict__ unow) {
+    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    F2 f[kQ], ux, uy, Fx, Fy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[i] = ld2(fin + i * N + c);
+    sp4_u(f, ux, uy);
+    sp4_force(K, ux, uy, Fx, Fy);
+    st2(unow + c, ux);
+    st2(unow + N + c, uy);
+    st2(unow + 2 * N + c, Fx);
+    st2(unow + 3 * N + c, Fy);
+}
+
+__global__ void __launch_bounds__(256) sp4_step_x2_kernel(const float* __restrict__ fin, float* __restrict__ fout,
+                                                          const float* __restrict__ src,
+                                                          const float* __restrict__ unow,
+                                                          const float* __restrict__ uprev, long long N, SpConst K) {
+    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+    F2 f[kQ], ux, uy;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[i] = ld2(fin + i * N + c);
+    const F2 S = ld2(src + c);
+    sp4_u(f, ux, uy);
+    const F2 Fx = ld2(unow + 2 * N + c), Fy = ld2(unow + 3 * N + c);
+    F2 rest(0.f);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) rest += f[i];
+    const F2 uu = ux * ux + uy * uy;
+    const F2 G0 = sp4_G(K, 0, S, ux, uy, Fx, Fy);
+    const F2 p = F2(0.6f) * (rest - F2(float(2.0 / 3.0)) * uu + F2(float(K.tgm + 0.5)) * G0);
+    const F2 upx = ld2(uprev + c), upy = ld2(uprev + N + c), Fpx = ld2(uprev + 2 * N + c),
+             Fpy = ld2(uprev + 3 * N + c);
+    const F2 ig(float(K.inv_tau));
+    const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
+    const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
+                       K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
+    // rows of the destinations x + c_i for G_i(x + c_i, t): mirrored about a wall
+    const int yst[3] = {y == 0 ? (K.walls ? 0 : K.ny - 1) : y - 1, y,
+                        y == K.ny - 1 ? (K.walls ? K.ny - 1 : 0) : y + 1};
+    const int xl[3] = {x == 0 ? K.nx - 1 : x - 1, x, x + 1};   // left lane's x + c_x
+    const int xr[3] = {x, x + 1, x + 2 == K.nx ? 0 : x + 2};   // right lane's
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool wall = (sy(i) > 0 && top) || (sy(i) < 0 && bot);
+        const F2 Gi = i == 0 ? G0 : sp4_G(K, i, S, ux, uy, Fx, Fy);
+        F2 Gn = G0;
+        if (i != 0) {
+            const long long row = (long long)yst[sy(i) + 1] * K.nx;
+            const long long a = row + xl[sx(i) + 1], b = row + xr[sx(i) + 1];
+            auto nb = [&](const float* pl) { return sx(i) == 0 ? ld2(pl + a) : F2(pl[a], pl[b]); };
+            Gn = sp4_G(K, i, nb(src), nb(unow), nb(unow + N), nb(unow + 2 * N), nb(unow + 3 * N));
+        }
+        const F2 Gp = sp4_G(K, i, S, upx, upy, Fpx, Fpy);   // G_i(x, t - 1)
+        const F2 cu = float(sx(i)) * ux + float(sy(i)) * uy;
+        const F2 si = float(sw(i)) * (F2(3.f) * cu + F2(4.5f) * cu * cu - F2(1.5f) * uu);
+        const F2 geq = i == 0 ? F2(3.f) * p * F2(float(sw(0) - 1.0)) + si : F2(3.f) * p * F2(float(sw(i))) + si;
+        const F2 post = f[i] - (f[i] - geq) * ig + Gi + F2(0.5f) * (Gn - Gp);
+        // bounce-back of g = f - G/2: leaves as i with G_i(x + c_i), returns as opp(i)
+        sp_store2(fout, N, c, x, ys[sy(i) + 1], K.nx, wall, i,
+                  wall ? post - F2(0.5f) * Gn + F2(0.5f) * sp4_G(K, sopp(i), S, ux, uy, Fx, Fy) : post);
     }
 }
 
@@ -574,10 +734,17 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
             } else {
                 const float* fi = static_cast<const float*>(c->g[c->cur]);
                 float* u = static_cast<float*>(c->ufield);
-                sp4_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, c->K, u + un * h);
-                sp4_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
-                    fi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), u + un * h,
-                    u + c->uprev * h, c->N, c->K);
+                if (c->p.nx % 2 == 0) {   // two cells a thread
+                    sp4_moments_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(fi, c->N, c->K, u + un * h);
+                    sp4_step_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(
+                        fi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), u + un * h,
+                        u + c->uprev * h, c->N, c->K);
+                } else {
+                    sp4_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(fi, c->N, c->K, u + un * h);
+                    sp4_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                        fi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), u + un * h,
+                        u + c->uprev * h, c->N, c->K);
+                }
             }
             c->uprev = un;
         } else if (m1) {
@@ -590,11 +757,20 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
                     static_cast<const double*>(c->ufield), c->N, c->K);
             } else {
                 const float* gi = static_cast<const float*>(c->g[c->cur]);
-                sp1_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
-                    gi, static_cast<const float*>(c->src), c->N, c->K, static_cast<float*>(c->ufield));
-                sp1_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
-                    gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src),
-                    static_cast<const float*>(c->ufield), c->N, c->K);
+                float* uf = static_cast<float*>(c->ufield);
+                if (c->p.nx % 2 == 0) {   // two cells a thread
+                    sp1_moments_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(
+                        gi, static_cast<const float*>(c->src), c->N, c->K, uf);
+                    sp1_step_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(
+                        gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), uf, c->N,
+                        c->K);
+                } else {
+                    sp1_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                        gi, static_cast<const float*>(c->src), c->N, c->K, uf);
+                    sp1_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
+                        gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), uf, c->N,
+                        c->K);
+                }
             }
         } else if (c->form == LBM_F64)
             sp_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(

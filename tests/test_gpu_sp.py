@@ -74,10 +74,11 @@ def test_poiseuille_exact_at_the_magic_tau(L):
 
 
 # ---------------------------------------------------------------- Remark 1
+@pytest.mark.parametrize("nx", [37, 38])
 @pytest.mark.parametrize("walls,xi", [(0, 0.0), (1, 0.0), (0, 0.03), (1, 0.03)])
-def test_remark1_matches_oracle(L, orc, walls, xi):
-    cfg = dict(nx=37, ny=23, walls_y=walls, nu=0.07, xi=xi, force_x=2e-6, force_y=-1e-6)
-    S = 1e-4 * np.sin(2 * np.pi * np.arange(37) / 37)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
+def test_remark1_matches_oracle(L, orc, walls, xi, nx):
+    cfg = dict(nx=nx, ny=23, walls_y=walls, nu=0.07, xi=xi, force_x=2e-6, force_y=-1e-6)
+    S = 1e-4 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
     S = np.ascontiguousarray(S + 2e-5)
     P = orc.sp_params(cfg)
     g = orc.sp1_init(P, 1.0)
@@ -125,11 +126,12 @@ def test_remark1_mass_source_flow(L, report, form, bar):
 
 
 # ---------------------------------------------------------------- Remark 4
+@pytest.mark.parametrize("nx", [37, 38])
 @pytest.mark.parametrize("walls,drag", [(0, (0.0, 0.0)), (1, (0.0, 0.0)), (0, (0.01, 0.4)), (1, (0.01, 0.4))])
-def test_remark4_matches_oracle(L, orc, walls, drag):
-    cfg = dict(nx=37, ny=23, walls_y=walls, nu=0.07, xi=0.02, force_x=2e-5, force_y=-1e-5,
+def test_remark4_matches_oracle(L, orc, walls, drag, nx):
+    cfg = dict(nx=nx, ny=23, walls_y=walls, nu=0.07, xi=0.02, force_x=2e-5, force_y=-1e-5,
                drag_lin=drag[0], drag_quad=drag[1])
-    S = 1e-4 * np.sin(2 * np.pi * np.arange(37) / 37)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
+    S = 1e-4 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
     S = np.ascontiguousarray(S)
     P = orc.sp_params(cfg)
     f, G = orc.sp4_init(P, S)
