@@ -512,15 +512,17 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     # each step one lbm_step whose kernels also reduce sum(phi), the kinetic energy
     # and max |u| (the per-step monitor), that record read to the host, the
     # fields read back to the host at the end.
-    # The record of step t is copied asynchronously into one of two pinned slots
-    # and checked on the host once step t has finished, while step t + 1 runs.
+    # The record of step t is copied asynchronously into one of NSLOT pinned
+    # slots and checked on the host once step t has finished, NSLOT - 1 steps
+    # later, so the host never waits on the step it has just queued.
     Ke = max(20, args.steps // 4)
     pinned = torch.from_numpy(phi0).pin_memory()
     host_phi0 = pinned.numpy()
     fields_out = torch.zeros((4, cfg["ny"], cfg["nx"]), dtype=torch.float64).pin_memory().numpy()
-    slots = [torch.zeros(ctypes.sizeof(lbm.lbm_monitor), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    NSLOT = 8
+    slots = [torch.zeros(ctypes.sizeof(lbm.lbm_monitor), dtype=torch.uint8).pin_memory() for _ in range(NSLOT)]
     recs = [lbm.lbm_monitor.from_address(b.data_ptr()) for b in slots]
-    done = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(NSLOT)]
 
     def check(r, t):
         if r.nonfinite or r.device_status or r.time != t:
@@ -535,14 +537,16 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
         lbm.lbm_init(sim.ctx, 0, host_phi0)
         for t in range(Ke):
             lbm.lbm_step(sim.ctx, 1)
-            lbm.lbm_read_monitor_async(sim.ctx, 0, slots[t % 2].data_ptr())
-            done[t % 2].record(stream)
-            if t > 0:
-                done[(t - 1) % 2].synchronize()
-                check(recs[(t - 1) % 2], t - 1)
-        done[(Ke - 1) % 2].synchronize()
-        check(recs[(Ke - 1) % 2], Ke - 1)
-        mon = {"sum_phi": recs[(Ke - 1) % 2].sum_phi}
+            lbm.lbm_read_monitor_async(sim.ctx, 0, slots[t % NSLOT].data_ptr())
+            done[t % NSLOT].record(stream)
+            if t >= NSLOT - 1:
+                tc = t - NSLOT + 1
+                done[tc % NSLOT].synchronize()
+                check(recs[tc % NSLOT], tc)
+        for tc in range(max(0, Ke - NSLOT + 1), Ke):
+            done[tc % NSLOT].synchronize()
+            check(recs[tc % NSLOT], tc)
+        mon = {"sum_phi": recs[(Ke - 1) % NSLOT].sum_phi}
         lbm.lbm_get_fields(sim.ctx, 0, 0xF, fields_out)
         dt = time.perf_counter() - t0
     d2h = ctypes.sizeof(lbm.lbm_monitor) + 8 * 4 * cells / Ke
