@@ -261,7 +261,8 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
  * D3Q15 contexts: PLAIN runs the unfused step (phi, mu and the collision as
  * three kernels over each instance, phi and mu through global scratch planes);
  * every other mode runs the fused step, which marches tiles of 32 x 8 columns
- * in z with phi, mu and p in shared-memory rings. Both give the same result. */
+ * in z with phi, mu and p in shared-memory rings -- except AUTO in LBM_F64,
+ * which runs the unfused step (faster there). Both give the same result. */
 enum {
     LBM_PIPELINE_AUTO = 0, LBM_PIPELINE_PLAIN = 1, LBM_PIPELINE_ASYNC = 2, LBM_PIPELINE_TMA = 3,
     LBM_PIPELINE_PAIRS = 4

@@ -746,12 +746,20 @@ cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStre
     });
 }
 
+// D3Q15: the unfused three-kernel step runs under LBM_PIPELINE_PLAIN, and by
+// default in FP64, where the fused march is bound by the FP64 pipe and its
+// recomputed halo costs more than the scratch planes (647 against 714 MLUPS on
+// the 128 x 256 x 128 bubble).
+bool d3_unfused(const lbm_ctx* c) {
+    return c->pipeline == LBM_PIPELINE_PLAIN || (c->pipeline == LBM_PIPELINE_AUTO && c->form == LBM_F64);
+}
+
 // Queues one time step (all launches of the plan) reading buffer set `in`; with
 // `monitor` the step kernels also write their monitor slots, reduced per instance.
 cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
     if (c->d3) {
         const StepArgs a = step_args(c, in);
-        if (c->pipeline == LBM_PIPELINE_PLAIN) {   // the unfused three-kernel step
+        if (d3_unfused(c)) {   // the unfused three-kernel step
             for (int k = 0; k < c->n; ++k) {
                 cudaError_t e = lbm::launch_step3(c->form, a, c->sc, k, (int)cells_of(c->params[k]), c->stream);
                 if (e != cudaSuccess) return e;
@@ -1249,7 +1257,7 @@ int lbm_launches_per_step(const lbm_ctx* c) {
         lbm_ctx* m = const_cast<lbm_ctx*>(c);
         if (cudaSetDevice(m->device) != cudaSuccess || plan(m) != LBM_OK) return 0;
     }
-    return (c->d3 && c->pipeline == LBM_PIPELINE_PLAIN) ? 3 * c->n : (int)c->launches.size();
+    return (c->d3 && d3_unfused(c)) ? 3 * c->n : (int)c->launches.size();
 }
 
 int64_t lbm_time(const lbm_ctx* c, int instance) {

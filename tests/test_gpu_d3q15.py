@@ -75,9 +75,12 @@ def test_tiny_grids_all_flags_fp64(L, orc, walls, qim, pressure, sforce, visc):
     cfg["init"] = dict(kind="droplet", cx=3.5, cy=3.0, cz=2.5, R=2.0)
     phi0 = noisy(cfg, 11 + walls + 2 * qim + 4 * pressure + 12 * sforce + 24 * visc)
     ref, st = oracle_run(orc, cfg, phi0, 8)
-    with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
-        sim.step(8)
-        compare(sim, 0, ref, st, 1e-12)
+    # FP64 runs the unfused step by default (AUTO) and the fused march under ASYNC
+    for mode in (L.LBM_PIPELINE_AUTO, L.LBM_PIPELINE_ASYNC):
+        with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
+            L.lbm_set_pipeline(sim.ctx, mode)
+            sim.step(8)
+            compare(sim, 0, ref, st, 1e-12)
 
 
 def test_initial_state_matches_oracle(L, orc):
@@ -131,13 +134,17 @@ def test_several_instances_in_one_context(L, orc):
     cfgs = [wl.static_droplet3(10, R=3.0), wl.rising_bubble3(nx=9, ny=12, nz=7, R=3.0, cy=4.5, Re=5.0),
             wl.static_droplet3(8, R=2.5, rho_ratio=2.0, qim=0)]
     phis = [noisy(c, 40 + k) for k, c in enumerate(cfgs)]
-    with L.Simulation(cfgs, "f64", phi0=phis) as sim:
-        sim.step(1)
-        sim.step(23)        # graph replays from here on
-        for k, c in enumerate(cfgs):
-            ref, st = oracle_run(orc, c, phis[k], 24)
-            compare(sim, k, ref, st, 1e-12)
-        assert L.lbm_launches_per_step(sim.ctx) == 1     # one fused launch for all instances
+    refs = [oracle_run(orc, c, phis[k], 24) for k, c in enumerate(cfgs)]
+    # the fused march (ASYNC): one launch for all instances; the default FP64
+    # step (AUTO): the three unfused kernels an instance
+    for mode, launches in ((L.LBM_PIPELINE_ASYNC, 1), (L.LBM_PIPELINE_AUTO, 3 * len(cfgs))):
+        with L.Simulation(cfgs, "f64", phi0=phis) as sim:
+            L.lbm_set_pipeline(sim.ctx, mode)
+            sim.step(1)
+            sim.step(23)        # graph replays from here on
+            for k, c in enumerate(cfgs):
+                compare(sim, k, refs[k][0], refs[k][1], 1e-12)
+            assert L.lbm_launches_per_step(sim.ctx) == launches
 
 
 def test_diagnostics_match_oracle(L, orc):
@@ -231,7 +238,7 @@ def test_fused_march_equals_unfused_step(L, form):
     # (FP64: to round-off; FP32: the compiler may contract a product into an FMA in
     # one kernel and not in the other, so the FP32 bars of the parity tests apply)
     out = []
-    for mode in (L.LBM_PIPELINE_AUTO, L.LBM_PIPELINE_PLAIN):
+    for mode in (L.LBM_PIPELINE_ASYNC, L.LBM_PIPELINE_PLAIN):   # fused, unfused
         with L.Simulation(cfgs, form, phi0=phis) as sim:
             L.lbm_set_pipeline(sim.ctx, mode)
             for rows in (0, 3):
