@@ -143,6 +143,7 @@ typedef struct {
     /* velocity-dependent force of the Remark 4 scheme:
      * F(u) = (force_x, force_y) - (drag_lin + drag_quad |u|) u                   */
     double drag_lin, drag_quad;
+    double p0;            /* Remark 2: the constant p_0 (> 0)                    */
 } orc_sp_params;
 
 double orc_sp_tau(const orc_sp_params* P);
@@ -177,6 +178,18 @@ int    orc_sp4_init(const orc_sp_params* P, const double* S, double* f, double* 
 int    orc_sp4_step(const orc_sp_params* P, const double* S, double* f, double* Gprev, int nsteps);
 int    orc_sp4_fields(const orc_sp_params* P, const double* S, const double* f, double* ux,
                       double* uy, double* p);
+
+/* Remark 2 (He-type incompressible form with a source S_1): g in units of
+ * pressure, p = sum g + p_0 S_1 / 2, p_0 u = sum c g + p_0 F_1 / 2 (force_x,
+ * force_y are F_1; the source field is S_1). */
+void   orc_sp2_moments(const orc_sp_params* P, const double* g, double S1, double* p, double* ux,
+                       double* uy);
+void   orc_sp2_force(const orc_sp_params* P, double S1, double ux, double uy, double divu, double* G);
+void   orc_sp2_geq(double p, double p0, double ux, double uy, double* geq);
+int    orc_sp2_init(const orc_sp_params* P, double* g);
+int    orc_sp2_step(const orc_sp_params* P, const double* S1, double* g, int nsteps);
+int    orc_sp2_fields(const orc_sp_params* P, const double* S1, const double* g, double* p, double* ux,
+                      double* uy);
 
 /* Analytic layered Poiseuille profile, Eq. 37: y measured from the interface,
  * walls at y = -hh and y = +hh, dynamic viscosity mu_up for 0 < y <= hh and

@@ -64,7 +64,7 @@ class SpParams(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls_y", ctypes.c_int),
                 ("nu", ctypes.c_double), ("xi", ctypes.c_double), ("force_x", ctypes.c_double),
                 ("force_y", ctypes.c_double), ("rho0", ctypes.c_double), ("drag_lin", ctypes.c_double),
-                ("drag_quad", ctypes.c_double)]
+                ("drag_quad", ctypes.c_double), ("p0", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -147,6 +147,12 @@ def lib():
         L.orc_sp1_geq.argtypes = [ctypes.c_double] * 3 + [_DP]
         L.orc_sp1_init.argtypes = [SP, ctypes.c_double, _DP]
         L.orc_sp1_step.argtypes = [SP, _DP, _DP, ctypes.c_int]
+        L.orc_sp2_moments.argtypes = [SP, _DP, ctypes.c_double, _DP, _DP, _DP]
+        L.orc_sp2_force.argtypes = [SP] + [ctypes.c_double] * 4 + [_DP]
+        L.orc_sp2_geq.argtypes = [ctypes.c_double] * 4 + [_DP]
+        L.orc_sp2_init.argtypes = [SP, _DP]
+        L.orc_sp2_step.argtypes = [SP, _DP, _DP, ctypes.c_int]
+        L.orc_sp2_fields.argtypes = [SP, _DP, _DP, _DP, _DP, _DP]
         L.orc_sp4_moments.argtypes = [SP, _DP, ctypes.c_double, _DP, _DP, _DP]
         L.orc_sp4_init.argtypes = [SP, _DP, _DP, _DP]
         L.orc_sp4_step.argtypes = [SP, _DP, _DP, _DP, ctypes.c_int]
@@ -435,6 +441,7 @@ def sp_params(cfg: dict) -> SpParams:
     P.force_x, P.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))
     P.rho0 = float(cfg.get("rho0", 0.0))
     P.drag_lin, P.drag_quad = float(cfg.get("drag_lin", 0.0)), float(cfg.get("drag_quad", 0.0))
+    P.p0 = float(cfg.get("p0", 1.0 / 3.0))
     return P
 
 
@@ -542,4 +549,38 @@ def sp4_fields(P: SpParams, S, f) -> dict:
     S = np.ascontiguousarray(S, dtype=np.float64)
     out = {k: np.zeros((P.ny, P.nx)) for k in ("ux", "uy", "p")}
     lib().orc_sp4_fields(ctypes.byref(P), _ptr(S), _ptr(f), _ptr(out["ux"]), _ptr(out["uy"]), _ptr(out["p"]))
+    return out
+
+
+# ------------------------------------------------- Remark 2 (He-type, source S_1)
+def sp2_geq(p, p0, ux, uy):
+    out = np.zeros(9)
+    lib().orc_sp2_geq(p, p0, ux, uy, _ptr(out))
+    return out
+
+
+def sp2_force(P: SpParams, S1, ux, uy, divu):
+    out = np.zeros(9)
+    lib().orc_sp2_force(ctypes.byref(P), S1, ux, uy, divu, _ptr(out))
+    return out
+
+
+def sp2_init(P: SpParams) -> np.ndarray:
+    g = np.zeros((9, P.ny, P.nx))
+    lib().orc_sp2_init(ctypes.byref(P), _ptr(g))
+    return g
+
+
+def sp2_step(P: SpParams, S1, g, n: int):
+    S1 = np.ascontiguousarray(S1, dtype=np.float64)
+    rc = lib().orc_sp2_step(ctypes.byref(P), _ptr(S1), _ptr(g), int(n))
+    if rc:
+        raise ValueError("orc_sp2_step failed (%d)" % rc)
+    return g
+
+
+def sp2_fields(P: SpParams, S1, g) -> dict:
+    S1 = np.ascontiguousarray(S1, dtype=np.float64)
+    out = {k: np.zeros((P.ny, P.nx)) for k in ("p", "ux", "uy")}
+    lib().orc_sp2_fields(ctypes.byref(P), _ptr(S1), _ptr(g), _ptr(out["p"]), _ptr(out["ux"]), _ptr(out["uy"]))
     return out

@@ -29,6 +29,16 @@
  * div u by the isotropic gradient of Eq. 30a (mirror at walls, reading Q7);
  * the u u S term is kept as printed.
  *
+ * Remark 2 (orc_sp2_*): Eq. 29bb multiplied by c_s^2 with the O(Ma^2) part of
+ * the density in front of s_i dropped, g in units of pressure:
+ *   g_i^eq = w_i p + p_0 s_i(u)                                (Eq. 29bd)
+ *   G_i = w_i { p_0 S_1 + p_0 c_i.F_1 / c_s^2
+ *              + (c_i c_i - c_s^2 I) : [p_0 (u F_1 + F_1 u) + Q_2 div(u) I] / (2 c_s^4) },
+ *   Q_2 = (2/d) p_0 c_s^2 - xi / (tau_g - 1/2)  (as printed),
+ *   p = sum_i g_i + p_0 S_1 / 2,   p_0 u = sum_i c_i g_i + p_0 F_1 / 2,
+ * with the constant p_0, the source S_1 and the force F_1 (S = p_0 S_1 and
+ * F = p_0 F_1 in the notation of the other remarks); div u as for Remark 1.
+ *
  * Remark 4 (orc_sp4_*): the Remark 3 model with a velocity-dependent force
  * F(u) = F_0 - (lambda + beta |u|) u, evolved without the shift of Eq. 23a and
  * with the explicit discretization of D_i G_i the remark gives:
@@ -420,6 +430,115 @@ int orc_sp4_fields(const orc_sp_params* P, const double* S, const double* f, dou
         if (ux) ux[c] = a;
         if (uy) uy[c] = b;
         if (p) p[c] = q;
+    }
+    return 0;
+}
+
+/* ---- Remark 2 ---- */
+void orc_sp2_moments(const orc_sp_params* P, const double* g, double S1, double* p, double* ux,
+                     double* uy) {
+    double m0 = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < QS; ++i) {
+        m0 += g[i];
+        jx += SX[i] * g[i];
+        jy += SY[i] * g[i];
+    }
+    *p = m0 + 0.5 * P->p0 * S1;
+    *ux = (jx + 0.5 * P->p0 * P->force_x) / P->p0;
+    *uy = (jy + 0.5 * P->p0 * P->force_y) / P->p0;
+}
+
+void orc_sp2_force(const orc_sp_params* P, double S1, double ux, double uy, double divu, double* G) {
+    const double tau = orc_sp_tau(P), p0 = P->p0;
+    const double Q2 = (2.0 / 2.0) * p0 * SCS2 - P->xi / (tau - 0.5);
+    const double u[2] = {ux, uy}, F[2] = {P->force_x, P->force_y};
+    double A[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) A[a][b] = p0 * (u[a] * F[b] + F[a] * u[b]) + (a == b ? Q2 * divu : 0.0);
+    for (int i = 0; i < QS; ++i) {
+        const double c[2] = {(double)SX[i], (double)SY[i]};
+        double contraction = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) contraction += (c[a] * c[b] - (a == b ? SCS2 : 0.0)) * A[a][b];
+        G[i] = SW[i] * (p0 * S1 + p0 * (c[0] * F[0] + c[1] * F[1]) / SCS2 + contraction / (2.0 * SCS2 * SCS2));
+    }
+}
+
+void orc_sp2_geq(double p, double p0, double ux, double uy, double* geq) {
+    for (int i = 0; i < QS; ++i) geq[i] = SW[i] * p + p0 * sp_s(i, ux, uy);
+}
+
+int orc_sp2_init(const orc_sp_params* P, double* g) {   /* p = p_0, u = 0 */
+    const long N = (long)P->nx * P->ny;
+    double geq[QS];
+    orc_sp2_geq(P->p0, P->p0, 0.0, 0.0, geq);
+    for (int i = 0; i < QS; ++i)
+        for (long c = 0; c < N; ++c) g[i * N + c] = geq[i];
+    return 0;
+}
+
+int orc_sp2_step(const orc_sp_params* P, const double* S1, double* g, int nsteps) {
+    const int nx = P->nx, ny = P->ny;
+    const long N = (long)nx * ny;
+    const double tau = orc_sp_tau(P);
+    if (!(P->p0 > 0.0)) return 1;
+    double* post = (double*)malloc((size_t)(QS * N) * sizeof(double));
+    double* pc = (double*)malloc((size_t)N * sizeof(double));
+    double* ux = (double*)malloc((size_t)N * sizeof(double));
+    double* uy = (double*)malloc((size_t)N * sizeof(double));
+    if (!post || !pc || !ux || !uy) {
+        free(post); free(pc); free(ux); free(uy);
+        return 2;
+    }
+    for (int step = 0; step < nsteps; ++step) {
+        for (long c = 0; c < N; ++c) {   /* p and u everywhere first (div u) */
+            double gc[QS];
+            for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
+            orc_sp2_moments(P, gc, S1[c], &pc[c], &ux[c], &uy[c]);
+        }
+        for (long c = 0; c < N; ++c) {
+            const int x = (int)(c % nx), y = (int)(c / nx);
+            double divu = 0.0;   /* Eq. 30a applied to u */
+            for (int i = 1; i < QS; ++i)
+                divu += SW[i] * (SX[i] * sp_at(P, ux, x + SX[i], y + SY[i]) +
+                                 SY[i] * sp_at(P, uy, x + SX[i], y + SY[i])) / SCS2;
+            double geq[QS], G[QS];
+            orc_sp2_geq(pc[c], P->p0, ux[c], uy[c], geq);
+            orc_sp2_force(P, S1[c], ux[c], uy[c], divu, G);
+            for (int i = 0; i < QS; ++i) {
+                const double gi = g[i * N + c];
+                post[i * N + c] = gi - (gi - geq[i]) / tau + (1.0 - 1.0 / (2.0 * tau)) * G[i];
+            }
+        }
+        for (int i = 0; i < QS; ++i) {
+            const int oi = sp_opposite(i);
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const long here = (long)y * nx + x;
+                    const int ys = y - SY[i];
+                    if (P->walls_y && (ys < 0 || ys >= ny)) {
+                        g[i * N + here] = post[oi * N + here];
+                    } else {
+                        const int xs = ((x - SX[i]) % nx + nx) % nx, yw = (ys % ny + ny) % ny;
+                        g[i * N + here] = post[i * N + (long)yw * nx + xs];
+                    }
+                }
+        }
+    }
+    free(post); free(pc); free(ux); free(uy);
+    return 0;
+}
+
+int orc_sp2_fields(const orc_sp_params* P, const double* S1, const double* g, double* p, double* ux,
+                   double* uy) {
+    const long N = (long)P->nx * P->ny;
+    for (long c = 0; c < N; ++c) {
+        double gc[QS], a, b, q;
+        for (int i = 0; i < QS; ++i) gc[i] = g[i * N + c];
+        orc_sp2_moments(P, gc, S1[c], &q, &a, &b);
+        if (p) p[c] = q;
+        if (ux) ux[c] = a;
+        if (uy) uy[c] = b;
     }
     return 0;
 }

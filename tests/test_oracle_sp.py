@@ -1,4 +1,4 @@
-"""Pins of the oracles of Remarks 3, 1 and 4 (Sec. 2.3). Remark 3: the generalized model with
+"""Pins of the oracles of Remarks 3, 1, 2 and 4 (Sec. 2.3). Remark 3: the generalized model with
 rho~ = rho_0 and constant density, the incompressible Navier-Stokes equations
 with a mass source (div u = S).
 
@@ -259,3 +259,75 @@ def test_remark4_translation_equivariance(orc):
     orc.sp4_step(P, S, a, Ga, 20)
     orc.sp4_step(P, Sb, b, Gb, 20)
     assert np.array_equal(np.roll(a, (3, 5), axis=(1, 2)), b)
+
+
+# ---------------------------------------------------------------- Remark 2
+def test_remark2_equilibrium_and_force_moments(orc):
+    p0, xi, nu = 0.4, 0.02, 0.1
+    F1 = np.array([3e-5, -1e-5])
+    P = orc.sp_params(dict(nx=4, ny=4, nu=nu, xi=xi, force_x=F1[0], force_y=F1[1], p0=p0))
+    tau = nu / CS2 + 0.5
+    for _ in range(4):
+        p = p0 + RNG.uniform(-1e-3, 1e-3)
+        u = RNG.uniform(-0.05, 0.05, 2)
+        geq = orc.sp2_geq(p, p0, u[0], u[1])                                           # Eq. 29bd
+        assert np.isclose(geq.sum(), p, atol=1e-15)
+        assert np.allclose(geq @ C, p0 * u, atol=1e-16)
+        assert np.allclose(np.einsum("i,ia,ib->ab", geq, C, C), p * CS2 * np.eye(2) + p0 * np.outer(u, u),
+                           atol=1e-15)
+        S1, divu = RNG.uniform(-1e-3, 1e-3), RNG.uniform(-1e-3, 1e-3)
+        G = orc.sp2_force(P, S1, u[0], u[1], divu)
+        Q2 = p0 * CS2 - xi / (tau - 0.5)
+        assert np.isclose(G.sum(), p0 * S1, atol=1e-18)
+        assert np.allclose(G @ C, p0 * F1, atol=1e-18)
+        expect = CS2 * p0 * S1 * np.eye(2) + p0 * (np.outer(u, F1) + np.outer(F1, u)) + Q2 * divu * np.eye(2)
+        assert np.allclose(np.einsum("i,ia,ib->ab", G, C, C), expect, atol=1e-18)
+
+
+def test_remark2_pressure_balance(orc):
+    # p = sum g + p0 S1 / 2 and sum G = p0 S1: the sum of p grows by p0 sum S1 a step
+    P = orc.sp_params(dict(nx=16, ny=12, nu=0.08, walls_y=1, force_x=1e-6, p0=0.5))
+    S1 = np.ascontiguousarray(RNG.uniform(0, 2e-5, (12, 16)))
+    g = orc.sp2_init(P)
+    m0 = orc.sp2_fields(P, S1, g)["p"].sum()
+    orc.sp2_step(P, S1, g, 50)
+    m1 = orc.sp2_fields(P, S1, g)["p"].sum()
+    assert abs(m1 - m0 - 50 * 0.5 * S1.sum()) < 1e-12 * m0
+
+
+def test_remark2_source_flow_and_p0_invariance(orc):
+    # div u = S1 fixes u = -(A/k) cos kx, second order; u does not depend on p0 (xi = 0)
+    errs = []
+    for nx in (32, 64):
+        k, A = 2 * np.pi / nx, 1e-4
+        x = np.arange(nx)
+        S1 = np.tile(A * np.sin(k * x), (2, 1))
+        P = orc.sp_params(dict(nx=nx, ny=2, nu=0.1, p0=1.0 / 3.0))
+        g = orc.sp2_init(P)
+        orc.sp2_step(P, S1, g, 80000)
+        f = orc.sp2_fields(P, S1, g)
+        ua = -(A / k) * np.cos(k * x)
+        errs.append(np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua)))
+        if nx == 32:
+            P2 = orc.sp_params(dict(nx=nx, ny=2, nu=0.1, p0=2.0))
+            g2 = orc.sp2_init(P2)
+            orc.sp2_step(P2, S1, g2, 2000)
+            g1 = orc.sp2_init(P)
+            orc.sp2_step(P, S1, g1, 2000)
+            a, b = orc.sp2_fields(P2, S1, g2)["ux"], orc.sp2_fields(P, S1, g1)["ux"]
+            assert np.abs(a - b).max() < 1e-10 * np.abs(b).max()   # rounding only
+    assert errs[1] < 1e-3 and 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_remark2_poiseuille_exact_at_the_magic_tau(orc):
+    # S1 = 0: the incompressible model of He et al.; halfway bounce-back exact at tau = 1/2 + sqrt(3/16)
+    ny, F = 24, 1e-6
+    nu = CS2 * np.sqrt(3.0 / 16.0)
+    P = orc.sp_params(dict(nx=2, ny=ny, walls_y=1, nu=nu, force_x=F, p0=1.0))
+    S1 = np.zeros((ny, 2))
+    g = orc.sp2_init(P)
+    orc.sp2_step(P, S1, g, 30000)
+    ux = orc.sp2_fields(P, S1, g)["ux"][:, 0]
+    y = np.arange(ny)
+    ua = F / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux - ua)) / ua.max() < 1e-11
