@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs"],
                     help="load path of the step kernel (lbm_set_pipeline)")
     ap.add_argument("--kernel-run", default=None,
-                    choices=["bubble3d", "source_flow", "source_flow_remark1", "source_flow_remark4"],
+                    choices=["bubble3d", "source_flow", "source_flow_remark1", "source_flow_remark2",
+                             "source_flow_remark4"],
                     help="only time one step loop of another workload (for profiling): the "
                          "128 x 256 x 128 D3Q15 bubble or the 4096 x 4096 single-phase source "
                          "flow of Remark 3, Remark 1 or the Remark 4 scheme with drag")
@@ -286,12 +287,13 @@ def kernel_run(args):
         cells = n * n
         src = np.ascontiguousarray(1e-4 * np.sin(2 * np.pi * np.arange(n) / n)[None, :] * np.ones((n, 1)))
         form = "f64" if args.form == "f64" else "f32"
-        model = {"source_flow": 0, "source_flow_remark1": 1, "source_flow_remark4": 4}[args.kernel_run]
-        spcfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
+        model = {"source_flow": 0, "source_flow_remark1": 1, "source_flow_remark2": 2,
+                 "source_flow_remark4": 4}[args.kernel_run]
+        spcfg = dict(nx=n, ny=n, nu=0.1, model=model if model in (1, 2) else 0)
         if model == 4:
             spcfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
         sim = lbm.SourceFlow(spcfg, form, stream=stream.cuda_stream, source=src)
-        bpl = {0: 76, 1: 132, 4: 160}[model] * (2 if form == "f64" else 1)
+        bpl = {0: 76, 1: 132, 2: 132, 4: 160}[model] * (2 if form == "f64" else 1)
     sim.step(max(args.warmup, 2))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -481,13 +483,14 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     # Remark 1 (two kernels a step): (9 + 1) reads + 2 writes of u, then
     # 9 + 1 + 2 reads and 9 writes, so 264 / 132 bytes a cell
     sp1 = {"workload": "source_flow_remark1_4096x4096", "cells": n * n}
+    sp2 = {"workload": "source_flow_remark2_4096x4096", "cells": n * n}   # Remark 2: as Remark 1
     # Remark 4 scheme with a drag force (two kernels): 9 reads and 4 writes (u, F),
     # then 9 + 1 + 4 + 4 reads (f, S, u and F at t and t - 1) and 9 writes: 320 / 160
     sp4 = {"workload": "source_flow_remark4_drag_4096x4096", "cells": n * n}
-    legs = {0: sp, 1: sp1, 4: sp4}
+    legs = {0: sp, 1: sp1, 2: sp2, 4: sp4}
     for model, form, bpl in ((0, "f64", 152), (0, "f32", 76), (1, "f64", 264), (1, "f32", 132),
-                             (4, "f64", 320), (4, "f32", 160)):
-        spcfg = dict(nx=n, ny=n, nu=0.1, model=1 if model == 1 else 0)
+                             (2, "f64", 264), (2, "f32", 132), (4, "f64", 320), (4, "f32", 160)):
+        spcfg = dict(nx=n, ny=n, nu=0.1, model=model if model in (1, 2) else 0)
         if model == 4:
             spcfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
         with lbm.SourceFlow(spcfg, form, stream=stream.cuda_stream, source=src) as sim:
@@ -503,9 +506,10 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
             ms = e0.elapsed_time(e1)
             gbs = bpl * n * n / (ms * 1e-3 / Ks) / 1e9
             legs[model][form] = {"MLUPS": n * n * Ks / (ms * 1e-3) / 1e6, "GBps_algorithmic": gbs,
-                                            "frac_hbm": gbs / hbm_peak, "bytes_per_lup": bpl, "steps": Ks}
+                                 "frac_hbm": gbs / hbm_peak, "bytes_per_lup": bpl, "steps": Ks}
     out["source_flow"] = sp
     out["source_flow_remark1"] = sp1
+    out["source_flow_remark2"] = sp2
     out["source_flow_remark4"] = sp4
 
     # end to end through the C ABI with host buffers: init from pinned host phi0,

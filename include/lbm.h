@@ -356,8 +356,13 @@ void lbm_destroy(lbm_ctx* ctx);
  * p = rho c_s^2): rho = sum g + S/2 (Eq. 27aa), u = (sum c g + F/2)/rho,
  * g^eq = rho (w_i + s_i(u)) (Eq. 29bb), force term with uF + Fu - uuS + Q div(u) I,
  * Q = (2/d) rho c_s^2 - xi/(tau_g - 1/2), div u by Eq. 30a (mirror at walls);
- * the total mass grows by sum S a step. Two kernels a step. */
-enum { LBM_SP_INCOMPRESSIBLE_SOURCE = 0, LBM_SP_NEARLY_INCOMPRESSIBLE = 1 };
+ * the total mass grows by sum S a step. Two kernels a step.
+ * model LBM_SP_HE_INCOMPRESSIBLE is Remark 2: g in units of pressure,
+ * g^eq = w_i p + p_0 s_i(u) (Eq. 29bd), p = sum g + p_0 S_1/2, p_0 u = sum c g +
+ * p_0 F_1/2, G_i with p_0 S_1, p_0 F_1 and ((2/d) p_0 c_s^2 - xi/(tau_g - 1/2))
+ * div u (as printed); the source field is S_1, (force_x, force_y) is F_1, p0 > 0.
+ * Two kernels a step, like Remark 1. */
+enum { LBM_SP_INCOMPRESSIBLE_SOURCE = 0, LBM_SP_NEARLY_INCOMPRESSIBLE = 1, LBM_SP_HE_INCOMPRESSIBLE = 2 };
 /* scheme LBM_SP_SCHEME_REMARK4 (with model LBM_SP_INCOMPRESSIBLE_SOURCE only)
  * evolves the Remark 3 model with the explicit discretization of D_i G_i of
  * Remark 4, for a velocity-dependent force F(u) = F_0 - (drag_lin + drag_quad
@@ -374,7 +379,7 @@ enum { LBM_SP_SCHEME_EQ24 = 0, LBM_SP_SCHEME_REMARK4 = 1 };
 typedef struct lbm_sp_params {
     int32_t nx, ny;
     int32_t bc_y;             /* LBM_BC_*                                                */
-    int32_t model;            /* LBM_SP_* (Remark 3 or Remark 1)                          */
+    int32_t model;            /* LBM_SP_* (Remark 3, 1 or 2)                              */
     double nu;                /* kinematic viscosity (> 0)                               */
     double xi;                /* bulk viscosity in Q (>= 0; 0 under Stokes' hypothesis)  */
     double force_x, force_y;  /* uniform body force F_0                                   */
@@ -382,6 +387,7 @@ typedef struct lbm_sp_params {
     int32_t reserved;         /* must be 0                                                */
     double drag_lin;          /* lambda >= 0 of F(u) (Remark 4 scheme only)               */
     double drag_quad;         /* beta >= 0 of F(u) (Remark 4 scheme only)                 */
+    double p0;                /* p_0 > 0 of Remark 2 (ignored by the other models)        */
 } lbm_sp_params;
 
 typedef struct lbm_sp_ctx lbm_sp_ctx;
@@ -394,20 +400,20 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
 
 /* Sets the source field S (host array of nx*ny doubles, copied; constant in
  * time) and the state at rest (u = 0; p = 0 for Remark 3, rho = 1 for Remark
- * 1). Resets the time. Synchronises. */
+ * 1, p = p_0 for Remark 2). Resets the time. Synchronises. */
 lbm_status lbm_sp_init(lbm_sp_ctx* ctx, const double* source_host);
 
 /* Advances nsteps time steps (asynchronous). LBM_ESTATE before lbm_sp_init. */
 lbm_status lbm_sp_step(lbm_sp_ctx* ctx, int nsteps);
 
-/* u and p (Eq. 27a, Eq. 28; Remark 1: p = rho c_s^2) at the current time:
+/* u and p (Eq. 27a, Eq. 28; Remark 1: p = rho c_s^2; Remark 2: p) at the current time:
  * mask of LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_P (and LBM_FIELD_RHO for Remark
  * 1); host_out receives popcount(mask) * nx * ny doubles in bit order.
  * Synchronises. */
 lbm_status lbm_sp_get_fields(lbm_sp_ctx* ctx, unsigned mask, double* host_out);
 
 /* The 9 population planes in FP64 (Remark 3: g_0 shifted by rho_0 = 0;
- * Remark 1: as they are; Remark 4 scheme: the unshifted f). Synchronises. */
+ * Remarks 1 and 2: as they are; Remark 4 scheme: the unshifted f). Synchronises. */
 lbm_status lbm_sp_get_populations(lbm_sp_ctx* ctx, double* host_g);
 
 const char* lbm_sp_last_error(const lbm_sp_ctx* ctx);

@@ -11,6 +11,9 @@
 // then BGK (Eq. 24) and push-streaming (x periodic; y periodic or halfway
 // bounce-back walls). Storage and arithmetic in FP64 or FP32.
 //
+// model LBM_SP_HE_INCOMPRESSIBLE: Remark 2, the same two kernels with g in
+// units of pressure (g^eq = w_i p + p_0 s_i(u), Eq. 29bd; p_0 S_1 and p_0 F_1).
+//
 // model LBM_SP_NEARLY_INCOMPRESSIBLE: Remark 1 (rho~ = rho, p = rho c_s^2): rho =
 // sum g + S/2 (Eq. 27aa), u = (sum c g + F/2) / rho, g^eq = rho (w_i + s_i(u))
 // (Eq. 29bb), G_i with (u F + F u - u u S + Q div(u) I) and Q = (2/d) rho c_s^2 -
@@ -86,6 +89,10 @@ struct SpConst {
     int nx, ny, walls;
     double inv_tau, src, tgm, Qc, fx, fy;   // 1/tau_g, 1 - 1/(2 tau_g), tau_g - 1/2, Q, F
     double dl, dq;                          // drag of the Remark 4 scheme: F(u) = F - (dl + dq |u|) u
+    double p0;                              // Remark 2: the constant p_0
+    // derived on the host, so that FP32 kernels do no FP64 arithmetic on them
+    double tau, Qd0;                        // tau_g; Q - (2/d) c_s^2 (the part of Q without the density)
+    double hp0, ip0, hp0fx, hp0fy;          // p_0 / 2, 1 / p_0, p_0 F_1 / 2
 };
 
 template <typename R>
@@ -183,10 +190,14 @@ __global__ void __launch_bounds__(256) sp_step_x2_kernel(const float* __restrict
     }
 }
 
-// ---- Remark 1 ----
-// g holds g_i - w_i; drho = rho - 1
-template <typename R>
-__device__ __forceinline__ void sp1_moments(const SpConst& K, const R g[kQ], R S, R& drho, R& rho, R& ux, R& uy) {
+// ---- Remarks 1 and 2 (M = 1, 2) ----
+// g holds g_i - w_i a0 (a0 = 1 for Remark 1, p_0 for Remark 2: the rest state).
+// d = rho - 1 (Remark 1) or p - p_0 (Remark 2); a = rho or p_0, the factor of
+// s_i(u) in g^eq (Eq. 29bb, Eq. 29bd); both equilibria are d w_i + a s_i(u)
+// after the shift. Sg and the force Fg are in the units of g (Remark 2: p_0 S_1,
+// p_0 F_1).
+template <int M, typename R>
+__device__ __forceinline__ void sp1_moments(const SpConst& K, const R g[kQ], R S, R& d, R& a, R& ux, R& uy) {
     R m0 = g[0], jx = R(0), jy = R(0);
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
@@ -194,38 +205,62 @@ __device__ __forceinline__ void sp1_moments(const SpConst& K, const R g[kQ], R S
         if (sx(i)) jx += sx(i) > 0 ? g[i] : -g[i];
         if (sy(i)) jy += sy(i) > 0 ? g[i] : -g[i];
     }
-    drho = m0 + R(0.5) * S;
-    rho = R(1) + drho;
-    const R ir = sp_inv(rho);
-    ux = (jx + R(0.5) * R(K.fx)) * ir;
-    uy = (jy + R(0.5) * R(K.fy)) * ir;
+    if constexpr (M == 1) {
+        d = m0 + R(0.5) * S;                       // Eq. 27aa
+        a = R(1) + d;
+        const R ir = sp_inv(a);
+        ux = (jx + R(0.5) * R(K.fx)) * ir;         // Eq. 27a
+        uy = (jy + R(0.5) * R(K.fy)) * ir;
+    } else {
+        d = m0 + R(K.hp0) * S;                     // p = sum g + p_0 S_1 / 2
+        a = R(K.p0);
+        ux = (jx + R(K.hp0fx)) * R(K.ip0);         // p_0 u = sum c g + p_0 F_1 / 2
+        uy = (jy + R(K.hp0fy)) * R(K.ip0);
+    }
 }
 
-template <typename R>
+// post-collision value of direction i (Eq. 24 with the force term of the remark)
+template <int M, typename R>
+__device__ __forceinline__ R sp1_post(const SpConst& K, int i, R gi, R d, R a, R ux, R uy, R S, R Qd) {
+    const R sc = M == 1 ? R(1) : R(K.p0);          // S and F in the units of g
+    const R fx = R(K.fx) * sc, fy = R(K.fy) * sc, Sg = S * sc;
+    const R cu = R(sx(i)) * ux + R(sy(i)) * uy, cF = R(sx(i)) * fx + R(sy(i)) * fy;
+    const R uF = ux * fx + uy * fy, uu = ux * ux + uy * uy;
+    const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
+    const R si = R(sw(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+    const R geq = d * R(sw(i)) + a * si;
+    // (cc - c_s^2 I):(uF + Fu [- uu S] + Q div u I) / (2 c_s^4)
+    //   = 9 (c.u)(c.F) - 3 u.F [- 4.5 ((c.u)^2 - u.u / 3) S] + 4.5 (|c|^2 - 2/3) Q div u
+    R Gi = Sg + R(3) * cF + R(9) * cu * cF - R(3) * uF + R(4.5) * (c2 - R(2.0 / 3.0)) * Qd;
+    if constexpr (M == 1) Gi = Gi - R(4.5) * (cu * cu - uu * R(1.0 / 3.0)) * Sg;   // the u u S of Remark 1
+    return gi - (gi - geq) * R(K.inv_tau) + R(K.src) * (R(sw(i)) * Gi);
+}
+
+template <int M, typename R>
 __global__ void __launch_bounds__(256) sp1_moments_kernel(const R* __restrict__ gin, const R* __restrict__ src,
                                                           long long N, SpConst K, R* __restrict__ ufield) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    R g[kQ], drho, rho, ux, uy;
+    R g[kQ], d, a, ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] = gin[i * N + c];
-    sp1_moments(K, g, src[c], drho, rho, ux, uy);
+    sp1_moments<M>(K, g, src[c], d, a, ux, uy);
     ufield[c] = ux;
     ufield[N + c] = uy;
 }
 
-template <typename R>
+template <int M, typename R>
 __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin, R* __restrict__ gout,
                                                        const R* __restrict__ src, const R* __restrict__ ufield,
                                                        long long N, SpConst K) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
-    R g[kQ], drho, rho, ux, uy;
+    R g[kQ], d, a, ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] = gin[i * N + c];
     const R S = src[c];
-    sp1_moments(K, g, S, drho, rho, ux, uy);
+    sp1_moments<M>(K, g, S, d, a, ux, uy);
     const int xs[3] = {x == 0 ? K.nx - 1 : x - 1, x, x == K.nx - 1 ? 0 : x + 1};
     // stencil rows: mirror at walls (reading Q7), wrap when periodic
     const int yst[3] = {y == 0 ? (K.walls ? 0 : K.ny - 1) : y - 1, y,
@@ -240,25 +275,14 @@ __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin
         divu += R(sw(i)) * cu;
     }
     divu *= R(3);
-    const R fx = R(K.fx), fy = R(K.fy);
-    const R uF = ux * fx + uy * fy, uu = ux * ux + uy * uy;
-    // Q = (2/d) rho c_s^2 - xi / (tau_g - 1/2); K.Qc holds the value at rho = 1
-    const R Qd = (rho * R(1.0 / 3.0) + R(K.Qc - 1.0 / 3.0)) * divu;
-    const R ig = R(K.inv_tau), sg = R(K.src);
+    // Q = (2/d) a c_s^2 - xi / (tau_g - 1/2); K.Qd0 = -xi / (tau_g - 1/2)
+    const R Qd = (a * R(1.0 / 3.0) + R(K.Qd0)) * divu;
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
     const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
                        K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-        const R cu = R(sx(i)) * ux + R(sy(i)) * uy, cF = R(sx(i)) * fx + R(sy(i)) * fy;
-        const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
-        const R si = R(sw(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-        const R geq = drho * R(sw(i)) + rho * si;                              // Eq. 29bb, minus w_i
-        // (cc - c_s^2 I):(uF + Fu - uu S + Q div u I) / (2 c_s^4)
-        //   = 9 (c.u)(c.F) - 3 u.F - 4.5 ((c.u)^2 - u.u / 3) S + 4.5 (|c|^2 - 2/3) Q div u
-        const R Gi = R(sw(i)) * (S + R(3) * cF + R(9) * cu * cF - R(3) * uF -
-                                 R(4.5) * (cu * cu - uu * R(1.0 / 3.0)) * S + R(4.5) * (c2 - R(2.0 / 3.0)) * Qd);
-        const R post = g[i] - (g[i] - geq) * ig + sg * Gi;
+        const R post = sp1_post<M>(K, i, g[i], d, a, ux, uy, S, Qd);
         long long dst;
         int k = i;
         if ((sy(i) > 0 && top) || (sy(i) < 0 && bot)) {
@@ -271,31 +295,33 @@ __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin
     }
 }
 
-// Remark 1, FP32, two cells a thread (nx even): rho - 1 and u of the pair
+// FP32, two cells a thread (nx even)
+template <int M>
 __global__ void __launch_bounds__(256) sp1_moments_x2_kernel(const float* __restrict__ gin,
                                                              const float* __restrict__ src, long long N, SpConst K,
                                                              float* __restrict__ ufield) {
     const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
-    F2 g[kQ], drho, rho, ux, uy;
+    F2 g[kQ], d, a, ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] = ld2(gin + i * N + c);
-    sp1_moments(K, g, ld2(src + c), drho, rho, ux, uy);
+    sp1_moments<M>(K, g, ld2(src + c), d, a, ux, uy);
     st2(ufield + c, ux);
     st2(ufield + N + c, uy);
 }
 
+template <int M>
 __global__ void __launch_bounds__(256) sp1_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
                                                           const float* __restrict__ src,
                                                           const float* __restrict__ ufield, long long N, SpConst K) {
     const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
-    F2 g[kQ], drho, rho, ux, uy;
+    F2 g[kQ], d, a, ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) g[i] = ld2(gin + i * N + c);
     const F2 S = ld2(src + c);
-    sp1_moments(K, g, S, drho, rho, ux, uy);
+    sp1_moments<M>(K, g, S, d, a, ux, uy);
     // stencil rows: mirror at walls (reading Q7), wrap when periodic
     const int yst[3] = {y == 0 ? (K.walls ? 0 : K.ny - 1) : y - 1, y,
                         y == K.ny - 1 ? (K.walls ? K.ny - 1 : 0) : y + 1};
@@ -314,41 +340,32 @@ __global__ void __launch_bounds__(256) sp1_step_x2_kernel(const float* __restric
         }
     }
     divu *= F2(3.f);
-    const F2 fx(float(K.fx)), fy(float(K.fy));
-    const F2 uF = ux * fx + uy * fy, uu = ux * ux + uy * uy;
-    const F2 Qd = (rho * F2(float(1.0 / 3.0)) + F2(float(K.Qc - 1.0 / 3.0))) * divu;
-    const F2 ig(float(K.inv_tau)), sg(float(K.src));
+    const F2 Qd = (a * F2(float(1.0 / 3.0)) + F2(float(K.Qd0))) * divu;
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
     const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
                        K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const F2 cu = float(sx(i)) * ux + float(sy(i)) * uy, cF = float(sx(i)) * fx + float(sy(i)) * fy;
-        const float c2 = float(sx(i) * sx(i) + sy(i) * sy(i));
-        const F2 si = float(sw(i)) * (F2(3.f) * cu + F2(4.5f) * cu * cu - F2(1.5f) * uu);
-        const F2 geq = drho * F2(float(sw(i))) + rho * si;
-        const F2 Gi = float(sw(i)) * (S + F2(3.f) * cF + F2(9.f) * cu * cF - F2(3.f) * uF -
-                                      F2(4.5f) * (cu * cu - uu * F2(float(1.0 / 3.0))) * S +
-                                      F2(4.5f) * F2(c2 - float(2.0 / 3.0)) * Qd);
-        const F2 post = g[i] - (g[i] - geq) * ig + sg * Gi;
-        sp_store2(gout, N, c, x, ys[sy(i) + 1], K.nx, (sy(i) > 0 && top) || (sy(i) < 0 && bot), i, post);
-    }
+    for (int i = 0; i < kQ; ++i)
+        sp_store2(gout, N, c, x, ys[sy(i) + 1], K.nx, (sy(i) > 0 && top) || (sy(i) < 0 && bot), i,
+                  sp1_post<M>(K, i, g[i], d, a, ux, uy, S, Qd));
 }
 
-template <typename R>
+template <int M, typename R>
 __global__ void sp1_fields_kernel(const R* __restrict__ g, const R* __restrict__ src, long long N, SpConst K,
                                   unsigned mask, double* __restrict__ out) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    R gc[kQ], drho, rho, ux, uy;
+    R gc[kQ], d, a, ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) gc[i] = g[i * N + c];
-    sp1_moments(K, gc, src[c], drho, rho, ux, uy);
+    sp1_moments<M>(K, gc, src[c], d, a, ux, uy);
+    // Remark 1: p = rho c_s^2, rho = 1 + d; Remark 2: p = p_0 + d
+    const double p = M == 1 ? (1.0 + double(d)) / 3.0 : K.p0 + double(d);
     int slot = 0;
     if (mask & LBM_FIELD_UX) out[(slot++) * N + c] = double(ux);
     if (mask & LBM_FIELD_UY) out[(slot++) * N + c] = double(uy);
-    if (mask & LBM_FIELD_P) out[(slot++) * N + c] = (1.0 + double(drho)) / 3.0;   // p = rho c_s^2
-    if (mask & LBM_FIELD_RHO) out[(slot++) * N + c] = 1.0 + double(drho);
+    if (mask & LBM_FIELD_P) out[(slot++) * N + c] = p;
+    if (M == 1 && (mask & LBM_FIELD_RHO)) out[(slot++) * N + c] = 1.0 + double(d);
 }
 
 // ---- Remark 4 scheme (on the Remark 3 model) ----
@@ -419,7 +436,7 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
     }
     const R uu = ux * ux + uy * uy;
     // Eq. 28 for the unshifted f: c_s^2 / (1 - w_0) = 3/5, s_0(u) = -(2/3) u.u, tau_g G_0
-    const R p = R(0.6) * (rest - R(2.0 / 3.0) * uu + R(K.tgm + 0.5) * G[0]);
+    const R p = R(0.6) * (rest - R(2.0 / 3.0) * uu + R(K.tau) * G[0]);
     const R upx = uprev[c], upy = uprev[N + c], Fpx = uprev[2 * N + c], Fpy = uprev[3 * N + c];
     const R ig = R(K.inv_tau);
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
@@ -480,7 +497,7 @@ __global__ void __launch_bounds__(256) sp4_step_x2_kernel(const float* __restric
     for (int i = 1; i < kQ; ++i) rest += f[i];
     const F2 uu = ux * ux + uy * uy;
     const F2 G0 = sp4_G(K, 0, S, ux, uy, Fx, Fy);
-    const F2 p = F2(0.6f) * (rest - F2(float(2.0 / 3.0)) * uu + F2(float(K.tgm + 0.5)) * G0);
+    const F2 p = F2(0.6f) * (rest - F2(float(2.0 / 3.0)) * uu + F2(float(K.tau)) * G0);
     const F2 upx = ld2(uprev + c), upy = ld2(uprev + N + c), Fpx = ld2(uprev + 2 * N + c),
              Fpy = ld2(uprev + 3 * N + c);
     const F2 ig(float(K.inv_tau));
@@ -528,7 +545,7 @@ __global__ void sp4_fields_kernel(const R* __restrict__ f, const R* __restrict__
 #pragma unroll
     for (int i = 1; i < kQ; ++i) rest += fc[i];
     const R G0 = sp4_G(K, 0, src[c], ux, uy, Fx, Fy);
-    const R p = R(0.6) * (rest - R(2.0 / 3.0) * (ux * ux + uy * uy) + R(K.tgm + 0.5) * G0);
+    const R p = R(0.6) * (rest - R(2.0 / 3.0) * (ux * ux + uy * uy) + R(K.tau) * G0);
     int slot = 0;
     if (mask & LBM_FIELD_UX) out[(slot++) * N + c] = double(ux);
     if (mask & LBM_FIELD_UY) out[(slot++) * N + c] = double(uy);
@@ -537,11 +554,11 @@ __global__ void sp4_fields_kernel(const R* __restrict__ f, const R* __restrict__
 
 // populations g_i = stored + w_i, widened to FP64
 template <typename R>
-__global__ void sp1_widen_kernel(const R* __restrict__ in, double* __restrict__ out, long long N) {
+__global__ void sp1_widen_kernel(const R* __restrict__ in, double* __restrict__ out, long long N, double a0) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) out[i * N + c] = double(in[i * N + c]) + sw(i);
+    for (int i = 0; i < kQ; ++i) out[i * N + c] = double(in[i * N + c]) + sw(i) * a0;
 }
 
 template <typename R>
@@ -619,6 +636,43 @@ void sp_release(lbm_sp_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// Remarks 1 and 2: u, then the collision
+template <int M>
+void sp1_enqueue(lbm_sp_ctx* c) {
+    if (c->form == LBM_F64) {
+        const double* gi = static_cast<const double*>(c->g[c->cur]);
+        double* uf = static_cast<double*>(c->ufield);
+        sp1_moments_kernel<M, double><<<blocks(c->N), 256, 0, c->stream>>>(
+            gi, static_cast<const double*>(c->src), c->N, c->K, uf);
+        sp1_step_kernel<M, double><<<blocks(c->N), 256, 0, c->stream>>>(
+            gi, static_cast<double*>(c->g[1 - c->cur]), static_cast<const double*>(c->src), uf, c->N, c->K);
+        return;
+    }
+    const float* gi = static_cast<const float*>(c->g[c->cur]);
+    float* uf = static_cast<float*>(c->ufield);
+    if (c->p.nx % 2 == 0) {   // two cells a thread
+        sp1_moments_x2_kernel<M><<<blocks(c->N / 2), 256, 0, c->stream>>>(
+            gi, static_cast<const float*>(c->src), c->N, c->K, uf);
+        sp1_step_x2_kernel<M><<<blocks(c->N / 2), 256, 0, c->stream>>>(
+            gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), uf, c->N, c->K);
+    } else {
+        sp1_moments_kernel<M, float><<<blocks(c->N), 256, 0, c->stream>>>(
+            gi, static_cast<const float*>(c->src), c->N, c->K, uf);
+        sp1_step_kernel<M, float><<<blocks(c->N), 256, 0, c->stream>>>(
+            gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), uf, c->N, c->K);
+    }
+}
+
+template <int M>
+void sp1_fields(lbm_sp_ctx* c, unsigned mask) {
+    if (c->form == LBM_F64)
+        sp1_fields_kernel<M, double><<<blocks(c->N), 256, 0, c->stream>>>(
+            static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
+    else
+        sp1_fields_kernel<M, float><<<blocks(c->N), 256, 0, c->stream>>>(
+            static_cast<const float*>(c->g[c->cur]), static_cast<const float*>(c->src), c->N, c->K, mask, c->d_tmp);
+}
+
 }  // namespace
 
 extern "C" {
@@ -630,7 +684,10 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
     const lbm_sp_params& p = *params;
     if (p.nx < 3 || p.ny < 3 || (long long)p.nx * p.ny >= (1LL << 31) / 9) return LBM_EINVAL;
     if (p.bc_y != LBM_BC_PERIODIC && p.bc_y != LBM_BC_BOUNCEBACK) return LBM_EINVAL;
-    if (p.model != LBM_SP_INCOMPRESSIBLE_SOURCE && p.model != LBM_SP_NEARLY_INCOMPRESSIBLE) return LBM_EINVAL;
+    if (p.model != LBM_SP_INCOMPRESSIBLE_SOURCE && p.model != LBM_SP_NEARLY_INCOMPRESSIBLE &&
+        p.model != LBM_SP_HE_INCOMPRESSIBLE)
+        return LBM_EINVAL;
+    if (p.model == LBM_SP_HE_INCOMPRESSIBLE && !(std::isfinite(p.p0) && p.p0 > 0)) return LBM_EINVAL;
     if ((p.scheme != LBM_SP_SCHEME_EQ24 && p.scheme != LBM_SP_SCHEME_REMARK4) || p.reserved != 0) return LBM_EINVAL;
     if (!(std::isfinite(p.drag_lin) && p.drag_lin >= 0) || !(std::isfinite(p.drag_quad) && p.drag_quad >= 0))
         return LBM_EINVAL;
@@ -648,13 +705,16 @@ lbm_status lbm_sp_create(const lbm_sp_params* params, int precision, void* cuda_
     c->N = (long long)p.nx * p.ny;
     const double tau = 3.0 * p.nu + 0.5;
     c->K = SpConst{p.nx, p.ny, p.bc_y == LBM_BC_BOUNCEBACK ? 1 : 0, 1.0 / tau, 1.0 - 0.5 / tau, tau - 0.5,
-                   1.0 / 3.0 - p.xi / (tau - 0.5), p.force_x, p.force_y, p.drag_lin, p.drag_quad};
+                   1.0 / 3.0 - p.xi / (tau - 0.5), p.force_x, p.force_y, p.drag_lin, p.drag_quad, p.p0,
+                   tau, -p.xi / (tau - 0.5), 0.5 * p.p0, p.p0 > 0 ? 1.0 / p.p0 : 0.0, 0.5 * p.p0 * p.force_x,
+                   0.5 * p.p0 * p.force_y};
     const size_t e = sp_elem(precision);
     cudaError_t r;
     if ((r = cudaMalloc(&c->g[0], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->g[1], kQ * c->N * e)) != cudaSuccess ||
         (r = cudaMalloc(&c->src, c->N * e)) != cudaSuccess ||
-        (p.model == LBM_SP_NEARLY_INCOMPRESSIBLE && (r = cudaMalloc(&c->ufield, 2 * c->N * e)) != cudaSuccess) ||
+        ((p.model == LBM_SP_NEARLY_INCOMPRESSIBLE || p.model == LBM_SP_HE_INCOMPRESSIBLE) &&
+         (r = cudaMalloc(&c->ufield, 2 * c->N * e)) != cudaSuccess) ||
         (p.scheme == LBM_SP_SCHEME_REMARK4 && (r = cudaMalloc(&c->ufield, 8 * c->N * e)) != cudaSuccess) ||
         (r = cudaMalloc((void**)&c->d_tmp, kQ * c->N * sizeof(double))) != cudaSuccess) {
         sp_release(c);
@@ -718,7 +778,7 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
     if (!c) return LBM_EINVAL;
     if (nsteps < 0) return sp_fail(c, LBM_EINVAL, "nsteps < 0");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
-    const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE;
+    const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE, m2 = c->p.model == LBM_SP_HE_INCOMPRESSIBLE;
     const bool r4 = c->p.scheme == LBM_SP_SCHEME_REMARK4;
     for (int s = 0; s < nsteps; ++s) {
         if (r4) {
@@ -748,31 +808,9 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
             }
             c->uprev = un;
         } else if (m1) {
-            if (c->form == LBM_F64) {
-                const double* gi = static_cast<const double*>(c->g[c->cur]);
-                sp1_moments_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
-                    gi, static_cast<const double*>(c->src), c->N, c->K, static_cast<double*>(c->ufield));
-                sp1_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
-                    gi, static_cast<double*>(c->g[1 - c->cur]), static_cast<const double*>(c->src),
-                    static_cast<const double*>(c->ufield), c->N, c->K);
-            } else {
-                const float* gi = static_cast<const float*>(c->g[c->cur]);
-                float* uf = static_cast<float*>(c->ufield);
-                if (c->p.nx % 2 == 0) {   // two cells a thread
-                    sp1_moments_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(
-                        gi, static_cast<const float*>(c->src), c->N, c->K, uf);
-                    sp1_step_x2_kernel<<<blocks(c->N / 2), 256, 0, c->stream>>>(
-                        gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), uf, c->N,
-                        c->K);
-                } else {
-                    sp1_moments_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
-                        gi, static_cast<const float*>(c->src), c->N, c->K, uf);
-                    sp1_step_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
-                        gi, static_cast<float*>(c->g[1 - c->cur]), static_cast<const float*>(c->src), uf, c->N,
-                        c->K);
-                }
-            }
-        } else if (c->form == LBM_F64)
+            sp1_enqueue<1>(c);
+        } else if (m2) {
+            sp1_enqueue<2>(c);        } else if (c->form == LBM_F64)
             sp_step_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
                 static_cast<const double*>(c->g[c->cur]), static_cast<double*>(c->g[1 - c->cur]),
                 static_cast<const double*>(c->src), c->N, c->K);
@@ -793,7 +831,7 @@ lbm_status lbm_sp_step(lbm_sp_ctx* c, int nsteps) {
 
 lbm_status lbm_sp_get_fields(lbm_sp_ctx* c, unsigned mask, double* host_out) {
     if (!c) return LBM_EINVAL;
-    const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE;
+    const bool m1 = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE, m2 = c->p.model == LBM_SP_HE_INCOMPRESSIBLE;
     const unsigned ok = LBM_FIELD_UX | LBM_FIELD_UY | LBM_FIELD_P | (m1 ? LBM_FIELD_RHO : 0u);
     if (!host_out || mask == 0 || (mask & ~ok)) return sp_fail(c, LBM_EINVAL, "bad mask or output");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
@@ -805,12 +843,10 @@ lbm_status lbm_sp_get_fields(lbm_sp_ctx* c, unsigned mask, double* host_out) {
     else if (c->p.scheme == LBM_SP_SCHEME_REMARK4)
         sp4_fields_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
             static_cast<const float*>(c->g[c->cur]), static_cast<const float*>(c->src), c->N, c->K, mask, c->d_tmp);
-    else if (m1 && c->form == LBM_F64)
-        sp1_fields_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
-            static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
     else if (m1)
-        sp1_fields_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(
-            static_cast<const float*>(c->g[c->cur]), static_cast<const float*>(c->src), c->N, c->K, mask, c->d_tmp);
+        sp1_fields<1>(c, mask);
+    else if (m2)
+        sp1_fields<2>(c, mask);
     else if (c->form == LBM_F64)
         sp_fields_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
             static_cast<const double*>(c->g[c->cur]), static_cast<const double*>(c->src), c->N, c->K, mask, c->d_tmp);
@@ -830,10 +866,14 @@ lbm_status lbm_sp_get_populations(lbm_sp_ctx* c, double* host_g) {
     if (!host_g) return sp_fail(c, LBM_EINVAL, "output is NULL");
     if (!c->ready) return sp_fail(c, LBM_ESTATE, "not initialised");
     const long long n = kQ * c->N;
-    if (c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE && c->form == LBM_F64)
-        sp1_widen_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(static_cast<const double*>(c->g[c->cur]), c->d_tmp, c->N);
-    else if (c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE)
-        sp1_widen_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(static_cast<const float*>(c->g[c->cur]), c->d_tmp, c->N);
+    const bool shifted = c->p.model == LBM_SP_NEARLY_INCOMPRESSIBLE || c->p.model == LBM_SP_HE_INCOMPRESSIBLE;
+    const double a0 = c->p.model == LBM_SP_HE_INCOMPRESSIBLE ? c->p.p0 : 1.0;   // the stored shift w_i a0
+    if (shifted && c->form == LBM_F64)
+        sp1_widen_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(static_cast<const double*>(c->g[c->cur]),
+                                                                      c->d_tmp, c->N, a0);
+    else if (shifted)
+        sp1_widen_kernel<float><<<blocks(c->N), 256, 0, c->stream>>>(static_cast<const float*>(c->g[c->cur]),
+                                                                     c->d_tmp, c->N, a0);
     else if (c->form == LBM_F64)
         sp_widen_kernel<double><<<blocks(n), 256, 0, c->stream>>>(static_cast<const double*>(c->g[c->cur]), c->d_tmp, n);
     else

@@ -74,7 +74,8 @@ class lbm_sp_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
                 ("model", ctypes.c_int32), ("nu", ctypes.c_double), ("xi", ctypes.c_double),
                 ("force_x", ctypes.c_double), ("force_y", ctypes.c_double), ("scheme", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("drag_lin", ctypes.c_double), ("drag_quad", ctypes.c_double)]
+                ("reserved", ctypes.c_int32), ("drag_lin", ctypes.c_double), ("drag_quad", ctypes.c_double),
+                ("p0", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -373,7 +374,8 @@ def _check_sp(st, ctx=None):
 
 class SourceFlow:
     """One single-phase simulation with a mass source on the GPU: Remark 3
-    (div u = S; cfg "model": 0) or Remark 1 ("model": 1); cfg "scheme": 1 runs
+    (div u = S; cfg "model": 0), Remark 1 ("model": 1) or Remark 2 ("model": 2,
+    "p0"; the source is S_1, the force F_1); cfg "scheme": 1 runs
     Remark 3 with the explicit D_i G_i of Remark 4 and the velocity-dependent
     force F_0 - (drag_lin + drag_quad |u|) u."""
 
@@ -381,7 +383,8 @@ class SourceFlow:
         p = lbm_sp_params()
         p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
         p.bc_y = int(cfg.get("walls_y", 0))
-        p.model = int(cfg.get("model", 0))   # 0: Remark 3, 1: Remark 1
+        p.model = int(cfg.get("model", 0))   # 0: Remark 3, 1: Remark 1, 2: Remark 2
+        p.p0 = float(cfg.get("p0", 1.0 / 3.0))
         self.model = p.model
         p.nu, p.xi = float(cfg["nu"]), float(cfg.get("xi", 0.0))
         p.force_x, p.force_y = float(cfg.get("force_x", 0.0)), float(cfg.get("force_y", 0.0))

@@ -81,9 +81,9 @@ def test_create_rejects_bad_input_without_touching_cuda(L):
     # the single-phase model of Remark 3
     sp = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
     spo = ctypes.c_void_p(1234)
-    for field, value in (("nx", 2), ("bc_y", 5), ("model", 2), ("nu", 0.0), ("xi", -1.0),
+    for field, value in (("nx", 2), ("bc_y", 5), ("model", 3), ("model", 2), ("nu", 0.0), ("xi", -1.0),
                          ("force_x", float("nan")), ("scheme", 2), ("reserved", 1),
-                         ("drag_lin", 0.1), ("drag_quad", 0.1)):   # drag needs the Remark 4 scheme
+                         ("drag_lin", 0.1), ("drag_quad", 0.1)):   # model 2 needs p0 > 0; drag the Remark 4 scheme
         bad = L.lbm_sp_params(16, 16, 0, 0, 0.1, 0.0, 0.0, 0.0)
         setattr(bad, field, value)
         assert lib.lbm_sp_create(ctypes.byref(bad), 0, None, ctypes.byref(spo)) == L.LBM_EINVAL

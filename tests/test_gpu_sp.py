@@ -1,5 +1,6 @@
-"""GPU single-phase models of Remark 3 (div u = S) and Remark 1 (nearly
-incompressible, mass source), and Remark 3 under the explicit D_iG_i scheme of
+"""GPU single-phase models of Remark 3 (div u = S), Remark 1 (nearly
+incompressible, mass source) and Remark 2 (He-type, source S_1), and Remark 3
+under the explicit D_iG_i scheme of
 Remark 4 with a drag force, versus their FP64 oracles, and
 the closed-form checks of its oracle pins run on the GPU path."""
 import numpy as np
@@ -197,3 +198,54 @@ def test_remark4_brinkman(L, report, form):
     err = np.abs(ux - ua).max() / ua.max()
     report(err=err)
     assert err < 2e-3
+
+
+# ---------------------------------------------------------------- Remark 2
+@pytest.mark.parametrize("nx", [37, 38])
+@pytest.mark.parametrize("walls,xi", [(0, 0.0), (1, 0.0), (0, 0.03), (1, 0.03)])
+def test_remark2_matches_oracle(L, orc, walls, xi, nx):
+    cfg = dict(nx=nx, ny=23, walls_y=walls, nu=0.07, xi=xi, force_x=6e-6, force_y=-3e-6, p0=0.4)
+    S1 = 3e-4 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * np.cos(2 * np.pi * np.arange(23) / 23)[:, None]
+    S1 = np.ascontiguousarray(S1 + 5e-5)
+    P = orc.sp_params(cfg)
+    g = orc.sp2_init(P)
+    orc.sp2_step(P, S1, g, 40)
+    ref = orc.sp2_fields(P, S1, g)
+    with L.SourceFlow(dict(cfg, model=2), "f64", source=S1) as sim:
+        sim.step(40)
+        got, gg = sim.fields(), sim.populations()
+    assert set(got) == {"ux", "uy", "p"}
+    assert rel(gg, g) < 1e-12 and rel(got["p"], ref["p"]) < 1e-12
+    # the oracle sums absolute populations (|g| ~ 0.2) into u ~ 1e-4 (as for Remark 1)
+    for k in ("ux", "uy"):
+        assert rel(got[k], ref[k]) < 1e-10, (k, rel(got[k], ref[k]))
+    with L.SourceFlow(dict(cfg, model=2), "f32", source=S1) as sim:
+        sim.step(40)
+        got = sim.fields()
+    for k in ("ux", "uy"):
+        assert rel(got[k], ref[k]) < 1e-4, (k, rel(got[k], ref[k]))
+    assert rel(got["p"] - 0.4, ref["p"] - 0.4) < 1e-3
+
+
+def test_remark2_pressure_balance(L):
+    S1 = np.ascontiguousarray(np.random.default_rng(6).uniform(0, 2e-5, (12, 16)))
+    with L.SourceFlow(dict(nx=16, ny=12, walls_y=1, nu=0.08, force_x=1e-6, model=2, p0=0.5), "f64",
+                      source=S1) as sim:
+        m0 = sim.fields()["p"].sum()
+        sim.step(50)
+        m1 = sim.fields()["p"].sum()
+    assert abs(m1 - m0 - 50 * 0.5 * S1.sum()) < 1e-12 * m0
+
+
+@pytest.mark.parametrize("form,bar", [("f64", 1e-3), ("f32", 2e-3)])
+def test_remark2_mass_source_flow(L, report, form, bar):
+    nx, A = 64, 1e-4
+    k = 2 * np.pi / nx
+    S1 = np.ascontiguousarray(np.tile(A * np.sin(k * np.arange(nx)), (3, 1)))
+    with L.SourceFlow(dict(nx=nx, ny=3, nu=0.1, model=2, p0=1.0 / 3.0), form, source=S1) as sim:
+        sim.step(80000)
+        f = sim.fields()
+    ua = -(A / k) * np.cos(k * np.arange(nx))
+    err = np.max(np.abs(f["ux"][0] - ua)) / np.max(np.abs(ua))
+    report(err=err)
+    assert err < bar
