@@ -69,17 +69,18 @@ __host__ __device__ constexpr double sw(int i) { return i == 0 ? 4.0 / 9.0 : (i 
 __host__ __device__ constexpr int sopp(int i) { return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 5 + 2) % 4 + 5); }
 static_assert(sopp(1) == 3 && sopp(2) == 4 && sopp(5) == 7 && sopp(6) == 8 && sopp(8) == 6, "D2Q9 opposites");
 
-// Push-streaming of direction i of a pair (x, x + 1), x even: with bounce, back
+// Push-streaming of direction i of a pair (x, x + 1), x even (32-bit offsets:
+// the context checks 9 nx ny < 2^31): with bounce, back
 // into the pair as the opposite direction (halfway wall); else to row yrow,
 // columns x + c_x and x + 1 + c_x (wrapped). c_x = 0 keeps the pair together.
-__device__ __forceinline__ void sp_store2(float* __restrict__ gout, long long N, long long c, int x, int yrow,
-                                          int nx, bool bounce, int i, F2 v) {
+__device__ __forceinline__ void sp_store2(float* __restrict__ gout, int N, int c, int x, int yrow, int nx,
+                                          bool bounce, int i, F2 v) {
     if (bounce) {
         st2(gout + sopp(i) * N + c, v);
     } else if (sx(i) == 0) {
-        st2(gout + i * N + (long long)yrow * nx + x, v);
+        st2(gout + i * N + yrow * nx + x, v);
     } else {
-        const long long row = i * N + (long long)yrow * nx;
+        const int row = i * N + yrow * nx;
         gout[row + (sx(i) < 0 ? (x == 0 ? nx - 1 : x - 1) : x + 1)] = v.v.x;
         gout[row + (sx(i) < 0 ? x : (x + 2 == nx ? 0 : x + 2))] = v.v.y;
     }
@@ -165,9 +166,9 @@ __global__ void __launch_bounds__(256) sp_step_kernel(const R* __restrict__ gin,
 // even, per thread, computed together in packed FP32 instructions (F2): the
 // loads, the S read and the stores of directions with c_x = 0 are 8-byte
 // pairs; directions with c_x != 0 split into two 4-byte stores. nx even.
-__global__ void __launch_bounds__(256) sp_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
-                                                         const float* __restrict__ src, long long N, SpConst K) {
-    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(256, 4) sp_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
+                                                         const float* __restrict__ src, int N, SpConst K) {
+    const int c = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
     F2 g[kQ], G[kQ];
@@ -298,9 +299,9 @@ __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin
 // FP32, two cells a thread (nx even)
 template <int M>
 __global__ void __launch_bounds__(256) sp1_moments_x2_kernel(const float* __restrict__ gin,
-                                                             const float* __restrict__ src, long long N, SpConst K,
+                                                             const float* __restrict__ src, int N, SpConst K,
                                                              float* __restrict__ ufield) {
-    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const int c = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     F2 g[kQ], d, a, ux, uy;
 #pragma unroll
@@ -311,10 +312,10 @@ __global__ void __launch_bounds__(256) sp1_moments_x2_kernel(const float* __rest
 }
 
 template <int M>
-__global__ void __launch_bounds__(256) sp1_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
+__global__ void __launch_bounds__(256, 3) sp1_step_x2_kernel(const float* __restrict__ gin, float* __restrict__ gout,
                                                           const float* __restrict__ src,
-                                                          const float* __restrict__ ufield, long long N, SpConst K) {
-    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+                                                          const float* __restrict__ ufield, int N, SpConst K) {
+    const int c = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
     F2 g[kQ], d, a, ux, uy;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(256) sp1_step_x2_kernel(const float* __restric
     F2 divu(0.f);   // Eq. 30a applied to u
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const long long row = (long long)yst[r] * K.nx;
+        const int row = yst[r] * K.nx;
         const Row2 UX(ufield + row, x, K.nx), UY(ufield + N + row, x, K.nx);
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
@@ -464,9 +465,9 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
 }
 
 // Remark 4 scheme, FP32, two cells a thread (nx even)
-__global__ void __launch_bounds__(256) sp4_moments_x2_kernel(const float* __restrict__ fin, long long N,
+__global__ void __launch_bounds__(256) sp4_moments_x2_kernel(const float* __restrict__ fin, int N,
                                                              SpConst K, float* __restrict__ unow) {
-    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const int c = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     F2 f[kQ], ux, uy, Fx, Fy;
 #pragma unroll
@@ -482,8 +483,8 @@ __global__ void __launch_bounds__(256) sp4_moments_x2_kernel(const float* __rest
 __global__ void __launch_bounds__(256) sp4_step_x2_kernel(const float* __restrict__ fin, float* __restrict__ fout,
                                                           const float* __restrict__ src,
                                                           const float* __restrict__ unow,
-                                                          const float* __restrict__ uprev, long long N, SpConst K) {
-    const long long c = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+                                                          const float* __restrict__ uprev, int N, SpConst K) {
+    const int c = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
     F2 f[kQ], ux, uy;
@@ -515,8 +516,8 @@ __global__ void __launch_bounds__(256) sp4_step_x2_kernel(const float* __restric
         const F2 Gi = i == 0 ? G0 : sp4_G(K, i, S, ux, uy, Fx, Fy);
         F2 Gn = G0;
         if (i != 0) {
-            const long long row = (long long)yst[sy(i) + 1] * K.nx;
-            const long long a = row + xl[sx(i) + 1], b = row + xr[sx(i) + 1];
+            const int row = yst[sy(i) + 1] * K.nx;
+            const int a = row + xl[sx(i) + 1], b = row + xr[sx(i) + 1];
             auto nb = [&](const float* pl) { return sx(i) == 0 ? ld2(pl + a) : F2(pl[a], pl[b]); };
             Gn = sp4_G(K, i, nb(src), nb(unow), nb(unow + N), nb(unow + 2 * N), nb(unow + 3 * N));
         }
