@@ -262,26 +262,8 @@ __device__ __forceinline__ void collide_cell3(const Args& a, const DevInst& P, c
     const int ys[3] = {Gm.walls ? y - 1 : Gm.wrap(y - 1, Gm.ny), y, Gm.walls ? y + 1 : Gm.wrap(y + 1, Gm.ny)};
     const int zs[3] = {Gm.wrap(z - 1, Gm.nz), z, Gm.wrap(z + 1, Gm.nz)};
     float rest = 0.f;   // conservative form: sum of the stored h_1 .. h_14
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const R wi = R(w(i));
-        const R cu = R(cx(i)) * m.u[0] + R(cy(i)) * m.u[1] + R(cz(i)) * m.u[2];
-        const R cF = R(cx(i)) * m.F[0] + R(cy(i)) * m.F[1] + R(cz(i)) * m.F[2];
-        const R cFt = R(cx(i)) * m.Ft[0] + R(cy(i)) * m.Ft[1] + R(cz(i)) * m.Ft[2];
-        const R c2 = R(cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i));
-        const R si = wi * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-        // Eq. 33 (rho_0 = 0: g_0 is stored shifted by rho_0)
-        const R geq = i == 0 ? R(3) * m.p * (wi - R(1)) + m.rho * si : R(3) * m.p * wi + m.rho * si;
-        // Eq. 34: w_i [S + c.F / c_s^2 + (2 (c.u)(c.Ft) - 2 c_s^2 u.Ft) / (2 c_s^4)
-        //              + (|c|^2 - d c_s^2)(2/d) rho c_s^2 S1 / (2 c_s^4)], d = 3
-        const R Gi = wi * (m.S + R(3) * cF + R(9) * cu * cFt - R(3) * uFt + (c2 - R(1)) * m.rho * m.S1);
-        const R gpost = g[i] - (g[i] - geq) * ig + srcg * Gi;                                  // Eq. 24
-        // Eq. 11 and Eq. 14
-        const R heq = i == 0 ? phi + (wi - R(1)) * em
-                             : wi * em + R(3) * wi * (R(cx(i)) * pu[0] + R(cy(i)) * pu[1] + R(cz(i)) * pu[2]);
-        const R Ri = srch * R(3) * wi * (R(cx(i)) * dpu[0] + R(cy(i)) * dpu[1] + R(cz(i)) * dpu[2]);
-        const R hpost = h[i] - (h[i] - heq) * ih + Ri;                                          // Eq. 10
-        // push-streaming: x + c_i, or back into this cell reversed at a wall
+    // push-streaming of direction i: to x + c_i, or back into this cell reversed at a wall
+    auto emit = [&](int i, R gpost, R hpost) {
         long long dst;
         int k = i;
         if ((cy(i) > 0 && top) || (cy(i) < 0 && bot)) {
@@ -292,12 +274,48 @@ __device__ __forceinline__ void collide_cell3(const Args& a, const DevInst& P, c
         }
         gout[(long long)k * S + dst] = gpost;
         if constexpr (cons) {
-            if (i == 0) continue;   // h_0 after the loop, from phi and the stored others
+            if (i == 0) return;   // h_0 after the loop, from phi and the stored others
             rest += hpost;
             hout[(long long)(k - 1) * S + dst] = hpost;
         } else {
             hout[(long long)k * S + dst] = hpost;
         }
+    };
+    {   // rest direction: s_0 = -w_0 u.u / (2 c_s^2), G_0 and h_0^eq of Eqs. 33, 34, 11
+        const R w0 = R(w(0));
+        const R s0 = w0 * (-R(1.5) * uu);
+        const R geq = R(3) * m.p * (w0 - R(1)) + m.rho * s0;                                    // Eq. 33
+        const R G0 = w0 * (m.S - R(3) * uFt - m.rho * m.S1);                                    // Eq. 34
+        const R heq = phi + (w0 - R(1)) * em;                                                   // Eq. 11
+        emit(0, g[0] - (g[0] - geq) * ig + srcg * G0, h[0] - (h[0] - heq) * ih);
+    }
+    // the moving directions in opposite pairs (i, opp(i)): c_opp = -c_i, so each
+    // of s_i, G_i, h_i^eq and R_i splits into a part even in c (shared) and a
+    // part odd in c (sign flipped)
+    constexpr int kPair[7] = {1, 2, 3, 7, 8, 9, 10};
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const int i = kPair[q], j = opp(i);
+        const R wi = R(w(i));
+        const R cu = R(cx(i)) * m.u[0] + R(cy(i)) * m.u[1] + R(cz(i)) * m.u[2];
+        const R cF = R(cx(i)) * m.F[0] + R(cy(i)) * m.F[1] + R(cz(i)) * m.F[2];
+        const R cFt = R(cx(i)) * m.Ft[0] + R(cy(i)) * m.Ft[1] + R(cz(i)) * m.Ft[2];
+        const R c2 = R(cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i));
+        // Eq. 33 (rho_0 = 0: g_0 is stored shifted by rho_0): w_i p / c_s^2 + rho s_i
+        const R geq_e = R(3) * m.p * wi + m.rho * (wi * (R(4.5) * cu * cu - R(1.5) * uu));
+        const R geq_o = m.rho * (wi * (R(3) * cu));
+        // Eq. 34: w_i [S + c.F / c_s^2 + (2 (c.u)(c.Ft) - 2 c_s^2 u.Ft) / (2 c_s^4)
+        //              + (|c|^2 - d c_s^2)(2/d) rho c_s^2 S1 / (2 c_s^4)], d = 3
+        const R G_e = wi * (m.S + R(9) * cu * cFt - R(3) * uFt + (c2 - R(1)) * m.rho * m.S1);
+        const R G_o = wi * (R(3) * cF);
+        // Eq. 11 and Eq. 14
+        const R heq_e = wi * em;
+        const R heq_o = R(3) * wi * (R(cx(i)) * pu[0] + R(cy(i)) * pu[1] + R(cz(i)) * pu[2]);
+        const R R_o = srch * R(3) * wi * (R(cx(i)) * dpu[0] + R(cy(i)) * dpu[1] + R(cz(i)) * dpu[2]);
+        emit(i, g[i] - (g[i] - (geq_e + geq_o)) * ig + srcg * (G_e + G_o),                       // Eq. 24
+             h[i] - (h[i] - (heq_e + heq_o)) * ih + R_o);                                         // Eq. 10
+        emit(j, g[j] - (g[j] - (geq_e - geq_o)) * ig + srcg * (G_e - G_o),
+             h[j] - (h[j] - (heq_e - heq_o)) * ih - R_o);
     }
     if constexpr (cons) {
         // h_0 = phi - sum of the stored h_1..h_14, as a float pair: sum(phi) is conserved
