@@ -237,6 +237,30 @@ __device__ __forceinline__ R sp1_post(const SpConst& K, int i, R gi, R d, R a, R
     return gi - (gi - geq) * R(K.inv_tau) + R(K.src) * (R(sw(i)) * Gi);
 }
 
+// The same for a direction i and its opposite j = opp(i): c_j = -c_i, so s_i and
+// G_i split into a part even in c (shared) and an odd part (sign flipped).
+template <int M, typename R>
+__device__ __forceinline__ void sp1_post_pair(const SpConst& K, int i, R gi, R gj, R d, R a, R ux, R uy, R S,
+                                              R Qd, R& pi, R& pj) {
+    const R sc = M == 1 ? R(1) : R(K.p0);
+    const R fx = R(K.fx) * sc, fy = R(K.fy) * sc, Sg = S * sc;
+    const R cu = R(sx(i)) * ux + R(sy(i)) * uy, cF = R(sx(i)) * fx + R(sy(i)) * fy;
+    const R uF = ux * fx + uy * fy, uu = ux * ux + uy * uy;
+    const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
+    const R wi = R(sw(i));
+    const R geq_e = d * wi + a * (wi * (R(4.5) * cu * cu - R(1.5) * uu)), geq_o = a * (wi * (R(3) * cu));
+    R G_e = Sg + R(9) * cu * cF - R(3) * uF + R(4.5) * (c2 - R(2.0 / 3.0)) * Qd;
+    if constexpr (M == 1) G_e = G_e - R(4.5) * (cu * cu - uu * R(1.0 / 3.0)) * Sg;   // the u u S of Remark 1
+    G_e = wi * G_e;
+    const R G_o = wi * (R(3) * cF);
+    const R ig = R(K.inv_tau), sg = R(K.src);
+    pi = gi - (gi - (geq_e + geq_o)) * ig + sg * (G_e + G_o);
+    pj = gj - (gj - (geq_e - geq_o)) * ig + sg * (G_e - G_o);
+}
+
+// D2Q9: one direction of each opposite pair (1, 2, 5, 6; their opposites 3, 4, 7, 8)
+__host__ __device__ constexpr int pair2(int q) { return q == 0 ? 1 : q == 1 ? 2 : q == 2 ? 5 : 6; }
+
 template <int M, typename R>
 __global__ void __launch_bounds__(256) sp1_moments_kernel(const R* __restrict__ gin, const R* __restrict__ src,
                                                           long long N, SpConst K, R* __restrict__ ufield) {
@@ -281,9 +305,7 @@ __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
     const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
                        K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const R post = sp1_post<M>(K, i, g[i], d, a, ux, uy, S, Qd);
+    auto emit = [&](int i, R post) {
         long long dst;
         int k = i;
         if ((sy(i) > 0 && top) || (sy(i) < 0 && bot)) {
@@ -293,6 +315,15 @@ __global__ void __launch_bounds__(256) sp1_step_kernel(const R* __restrict__ gin
             dst = (long long)ys[sy(i) + 1] * K.nx + xs[sx(i) + 1];
         }
         gout[k * N + dst] = post;
+    };
+    emit(0, sp1_post<M>(K, 0, g[0], d, a, ux, uy, S, Qd));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = pair2(q), j = sopp(i);
+        R pi, pj;
+        sp1_post_pair<M>(K, i, g[i], g[j], d, a, ux, uy, S, Qd, pi, pj);
+        emit(i, pi);
+        emit(j, pj);
     }
 }
 
@@ -345,10 +376,18 @@ __global__ void __launch_bounds__(256, 3) sp1_step_x2_kernel(const float* __rest
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
     const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
                        K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
+    auto emit = [&](int i, F2 post) {
+        sp_store2(gout, N, c, x, ys[sy(i) + 1], K.nx, (sy(i) > 0 && top) || (sy(i) < 0 && bot), i, post);
+    };
+    emit(0, sp1_post<M>(K, 0, g[0], d, a, ux, uy, S, Qd));
 #pragma unroll
-    for (int i = 0; i < kQ; ++i)
-        sp_store2(gout, N, c, x, ys[sy(i) + 1], K.nx, (sy(i) > 0 && top) || (sy(i) < 0 && bot), i,
-                  sp1_post<M>(K, i, g[i], d, a, ux, uy, S, Qd));
+    for (int q = 0; q < 4; ++q) {
+        const int i = pair2(q), j = sopp(i);
+        F2 pi, pj;
+        sp1_post_pair<M>(K, i, g[i], g[j], d, a, ux, uy, S, Qd, pi, pj);
+        emit(i, pi);
+        emit(j, pj);
+    }
 }
 
 template <int M, typename R>
@@ -396,6 +435,15 @@ __device__ __forceinline__ R sp4_G(const SpConst& K, int i, R S, R ux, R uy, R F
     const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
     return R(sw(i)) * (S + R(3) * cF + R(9) * cu * cF - R(3) * (ux * Fx + uy * Fy) +
                        R(4.5) * (c2 - R(2.0 / 3.0)) * R(K.Qc) * S);
+}
+
+// sp4_G split into the part even in c and the odd part c.F / c_s^2 (times w_i)
+template <typename R>
+__device__ __forceinline__ void sp4_G_parts(const SpConst& K, int i, R S, R ux, R uy, R Fx, R Fy, R& e, R& o) {
+    const R cu = R(sx(i)) * ux + R(sy(i)) * uy, cF = R(sx(i)) * Fx + R(sy(i)) * Fy;
+    const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
+    e = R(sw(i)) * (S + R(9) * cu * cF - R(3) * (ux * Fx + uy * Fy) + R(4.5) * (c2 - R(2.0 / 3.0)) * R(K.Qc) * S);
+    o = R(sw(i)) * (R(3) * cF);
 }
 
 // u = sum c f and F(u) of every cell, four planes (the update at x needs G at
@@ -510,25 +558,39 @@ __global__ void __launch_bounds__(256) sp4_step_x2_kernel(const float* __restric
                         y == K.ny - 1 ? (K.walls ? K.ny - 1 : 0) : y + 1};
     const int xl[3] = {x == 0 ? K.nx - 1 : x - 1, x, x + 1};   // left lane's x + c_x
     const int xr[3] = {x, x + 1, x + 2 == K.nx ? 0 : x + 2};   // right lane's
+    // G_i(x + c_i, t) from the destination's u, F and S
+    auto Gnb = [&](int i) {
+        const int row = yst[sy(i) + 1] * K.nx;
+        const int a = row + xl[sx(i) + 1], b = row + xr[sx(i) + 1];
+        auto nb = [&](const float* pl) { return sx(i) == 0 ? ld2(pl + a) : F2(pl[a], pl[b]); };
+        return sp4_G(K, i, nb(src), nb(unow), nb(unow + N), nb(unow + 2 * N), nb(unow + 3 * N));
+    };
+    {   // rest direction: never crosses a wall; its destination is this cell
+        const F2 Gp = sp4_G(K, 0, S, upx, upy, Fpx, Fpy);
+        const F2 geq = F2(3.f) * p * F2(float(sw(0) - 1.0)) + float(sw(0)) * (-F2(1.5f) * uu);
+        sp_store2(fout, N, c, x, y, K.nx, false, 0, f[0] - (f[0] - geq) * ig + G0 + F2(0.5f) * (G0 - Gp));
+    }
+    // opposite pairs (i, j = opp(i)): G of this cell at t and t - 1 and s_i split
+    // into parts even and odd in c
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const bool wall = (sy(i) > 0 && top) || (sy(i) < 0 && bot);
-        const F2 Gi = i == 0 ? G0 : sp4_G(K, i, S, ux, uy, Fx, Fy);
-        F2 Gn = G0;
-        if (i != 0) {
-            const int row = yst[sy(i) + 1] * K.nx;
-            const int a = row + xl[sx(i) + 1], b = row + xr[sx(i) + 1];
-            auto nb = [&](const float* pl) { return sx(i) == 0 ? ld2(pl + a) : F2(pl[a], pl[b]); };
-            Gn = sp4_G(K, i, nb(src), nb(unow), nb(unow + N), nb(unow + 2 * N), nb(unow + 3 * N));
-        }
-        const F2 Gp = sp4_G(K, i, S, upx, upy, Fpx, Fpy);   // G_i(x, t - 1)
+    for (int q = 0; q < 4; ++q) {
+        const int i = pair2(q), j = sopp(i);
+        const float wi = float(sw(i));
         const F2 cu = float(sx(i)) * ux + float(sy(i)) * uy;
-        const F2 si = float(sw(i)) * (F2(3.f) * cu + F2(4.5f) * cu * cu - F2(1.5f) * uu);
-        const F2 geq = i == 0 ? F2(3.f) * p * F2(float(sw(0) - 1.0)) + si : F2(3.f) * p * F2(float(sw(i))) + si;
-        const F2 post = f[i] - (f[i] - geq) * ig + Gi + F2(0.5f) * (Gn - Gp);
+        const F2 ge = F2(3.f * wi) * p + wi * (F2(4.5f) * cu * cu - F2(1.5f) * uu), go = wi * (F2(3.f) * cu);
+        F2 Ge, Go, Gpe, Gpo;
+        sp4_G_parts(K, i, S, ux, uy, Fx, Fy, Ge, Go);
+        sp4_G_parts(K, i, S, upx, upy, Fpx, Fpy, Gpe, Gpo);
+        const F2 Gi = Ge + Go, Gj = Ge - Go;
+        const F2 Gni = Gnb(i), Gnj = Gnb(j);
+        F2 pi = f[i] - (f[i] - (ge + go)) * ig + Gi + F2(0.5f) * (Gni - (Gpe + Gpo));
+        F2 pj = f[j] - (f[j] - (ge - go)) * ig + Gj + F2(0.5f) * (Gnj - (Gpe - Gpo));
         // bounce-back of g = f - G/2: leaves as i with G_i(x + c_i), returns as opp(i)
-        sp_store2(fout, N, c, x, ys[sy(i) + 1], K.nx, wall, i,
-                  wall ? post - F2(0.5f) * Gn + F2(0.5f) * sp4_G(K, sopp(i), S, ux, uy, Fx, Fy) : post);
+        const bool bi = (sy(i) > 0 && top) || (sy(i) < 0 && bot), bj = (sy(j) > 0 && top) || (sy(j) < 0 && bot);
+        if (bi) pi = pi - F2(0.5f) * Gni + F2(0.5f) * Gj;
+        if (bj) pj = pj - F2(0.5f) * Gnj + F2(0.5f) * Gi;
+        sp_store2(fout, N, c, x, ys[sy(i) + 1], K.nx, bi, i, pi);
+        sp_store2(fout, N, c, x, ys[sy(j) + 1], K.nx, bj, j, pj);
     }
 }
 
