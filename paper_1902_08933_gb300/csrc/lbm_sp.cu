@@ -1,20 +1,19 @@
-// lbm_sp.cu -- the single-phase model of Remark 3 (Sec. 2.3): the generalized
-// lattice Boltzmann model with rho~ = rho_0 and a constant density (rho = 1),
-// which recovers the incompressible Navier-Stokes equations with a mass source
-// (div u = S) and a uniform body force, on the D2Q9 lattice.
+// lbm_sp.cu -- the single-phase models of Sec. 2.3 on the D2Q9 lattice: the
+// generalized lattice Boltzmann model with a mass source, in the forms of
+// Remarks 3, 1 and 2, and the explicit D_i G_i scheme of Remark 4.
 //
-// One kernel a step, one thread a cell: the cell's populations and source give
-// u (Eq. 27a) and p (Eq. 28 with G_0), the equilibrium of Remark 3 (Eq. 25 with
-// rho~ = rho_0, rho = 1; g_0 stored shifted by rho_0) and the force term
+// Remark 3 (model LBM_SP_INCOMPRESSIBLE_SOURCE): rho~ = rho_0 and a constant
+// density (rho = 1), the incompressible Navier-Stokes equations with a mass
+// source (div u = S) and a uniform body force. One kernel a step: the cell's
+// populations and source give u (Eq. 27a) and p (Eq. 28 with G_0), the
+// equilibrium (Eq. 25 with rho~ = rho_0, rho = 1; g_0 stored shifted by rho_0)
+// and the force term
 //   G_i = w_i { S + c_i.F / c_s^2 + (c_i c_i - c_s^2 I):(u F + F u + Q S I) / (2 c_s^4) },
 //   Q = (2/d) c_s^2 - xi / (tau_g - 1/2),
 // then BGK (Eq. 24) and push-streaming (x periodic; y periodic or halfway
 // bounce-back walls). Storage and arithmetic in FP64 or FP32.
 //
-// model LBM_SP_HE_INCOMPRESSIBLE: Remark 2, the same two kernels with g in
-// units of pressure (g^eq = w_i p + p_0 s_i(u), Eq. 29bd; p_0 S_1 and p_0 F_1).
-//
-// model LBM_SP_NEARLY_INCOMPRESSIBLE: Remark 1 (rho~ = rho, p = rho c_s^2): rho =
+// Remark 1 (LBM_SP_NEARLY_INCOMPRESSIBLE; rho~ = rho, p = rho c_s^2): rho =
 // sum g + S/2 (Eq. 27aa), u = (sum c g + F/2) / rho, g^eq = rho (w_i + s_i(u))
 // (Eq. 29bb), G_i with (u F + F u - u u S + Q div(u) I) and Q = (2/d) rho c_s^2 -
 // xi / (tau_g - 1/2); div u by Eq. 30a from a plane of u (mirror at walls), so
@@ -22,11 +21,21 @@
 // stored as g_i - w_i (their rest state at rho = 1), so that FP32 storage keeps
 // the small deviations that carry the flow: rho = 1 + sum(g - w) + S/2.
 //
-// scheme LBM_SP_SCHEME_REMARK4: the Remark 3 model with a velocity-dependent
-// force F(u) = F_0 - (lambda + beta |u|) u, evolved with the explicit D_i G_i of
-// Remark 4 (unshifted f, u = sum c f). A first kernel writes u; the second
-// rebuilds G_i at the destination x + c_i from its u, F(u) and S, and G_i(x, t - 1)
-// from u and F at t - 1 (four planes kept instead of the nine planes of G).
+// Remark 2 (LBM_SP_HE_INCOMPRESSIBLE): the same two kernels with g in units of
+// pressure (g^eq = w_i p + p_0 s_i(u), Eq. 29bd; p_0 S_1 and p_0 F_1), stored as
+// g_i - w_i p_0.
+//
+// Remark 4 (scheme LBM_SP_SCHEME_REMARK4): the Remark 3 model with a
+// velocity-dependent force F(u) = F_0 - (lambda + beta |u|) u, evolved with the
+// explicit D_i G_i (unshifted f, u = sum c f). A first kernel writes u and
+// F(u); the second rebuilds G_i at the destination x + c_i from its u, F(u) and
+// S, and G_i(x, t - 1) from u and F at t - 1 (four planes kept instead of the
+// nine planes of G).
+//
+// FP32 with nx even runs kernels with two horizontally adjacent cells a thread
+// in packed FP32 instructions. The collisions of Remarks 1 and 2 and of the
+// two-cell Remark 4 kernel take opposite directions in pairs (the parts of s_i
+// and G_i even in c shared, the odd parts sign-flipped).
 #include <cmath>
 #include <cstring>
 #include <string>
