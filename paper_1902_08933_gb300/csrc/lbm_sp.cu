@@ -77,6 +77,8 @@ __host__ __device__ constexpr int sy(int i) { return i == 2 || i == 5 || i == 6 
 __host__ __device__ constexpr double sw(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
 __host__ __device__ constexpr int sopp(int i) { return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 5 + 2) % 4 + 5); }
 static_assert(sopp(1) == 3 && sopp(2) == 4 && sopp(5) == 7 && sopp(6) == 8 && sopp(8) == 6, "D2Q9 opposites");
+// one direction of each opposite pair (1, 2, 5, 6; their opposites 3, 4, 7, 8)
+__host__ __device__ constexpr int pair2(int q) { return q == 0 ? 1 : q == 1 ? 2 : q == 2 ? 5 : 6; }
 
 // Push-streaming of direction i of a pair (x, x + 1), x even (32-bit offsets:
 // the context checks 9 nx ny < 2^31): with bounce, back
@@ -124,12 +126,18 @@ __device__ __forceinline__ SpCell<R> sp_moments(const SpConst& K, const R g[kQ],
     m.uy = jy + R(0.5) * fy;
     const R uF = m.ux * fx + m.uy * fy, uu = m.ux * m.ux + m.uy * m.uy;
     const R QS = R(K.Qc) * S;
+    // (c c - c_s^2 I):(u F + F u + Q S I) / (2 c_s^4) = 9 (c.u)(c.F) - 3 u.F + 4.5 (|c|^2 - 2/3) Q S;
+    // for opposite directions the part even in c is shared and c.F / c_s^2 flips sign
+    G[0] = R(sw(0)) * (S - R(3) * uF + R(4.5) * (-R(2.0 / 3.0)) * QS);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
+    for (int q = 0; q < 4; ++q) {
+        const int i = pair2(q), j = sopp(i);
         const R cu = R(sx(i)) * m.ux + R(sy(i)) * m.uy, cF = R(sx(i)) * fx + R(sy(i)) * fy;
         const R c2 = R(sx(i) * sx(i) + sy(i) * sy(i));
-        // (c c - c_s^2 I):(u F + F u + Q S I) / (2 c_s^4) = 9 (c.u)(c.F) - 3 u.F + 4.5 (|c|^2 - 2/3) Q S
-        G[i] = R(sw(i)) * (S + R(3) * cF + R(9) * cu * cF - R(3) * uF + R(4.5) * (c2 - R(2.0 / 3.0)) * QS);
+        const R e = R(sw(i)) * (S + R(9) * cu * cF - R(3) * uF + R(4.5) * (c2 - R(2.0 / 3.0)) * QS);
+        const R o = R(sw(i)) * (R(3) * cF);
+        G[i] = e + o;
+        G[j] = e - o;
     }
     // Eq. 28: c_s^2 / (1 - w_0) = 3/5; s_0(u) = -w_0 u.u / (2 c_s^2) = -(2/3) u.u
     m.p = R(0.6) * (rest + R(0.5) * S - R(2.0 / 3.0) * uu + R(K.tgm) * G[0]);
@@ -267,8 +275,6 @@ __device__ __forceinline__ void sp1_post_pair(const SpConst& K, int i, R gi, R g
     pj = gj - (gj - (geq_e - geq_o)) * ig + sg * (G_e - G_o);
 }
 
-// D2Q9: one direction of each opposite pair (1, 2, 5, 6; their opposites 3, 4, 7, 8)
-__host__ __device__ constexpr int pair2(int q) { return q == 0 ? 1 : q == 1 ? 2 : q == 2 ? 5 : 6; }
 
 template <int M, typename R>
 __global__ void __launch_bounds__(256) sp1_moments_kernel(const R* __restrict__ gin, const R* __restrict__ src,
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int x = (int)(c % K.nx), y = (int)(c / K.nx);
-    R f[kQ], G[kQ], ux, uy;
+    R f[kQ], ux, uy;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[i] = fin[i * N + c];
     const R S = src[c];
@@ -488,36 +494,48 @@ __global__ void __launch_bounds__(256) sp4_step_kernel(const R* __restrict__ fin
     const R Fx = unow[2 * N + c], Fy = unow[3 * N + c];
     R rest = R(0);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        G[i] = sp4_G(K, i, S, ux, uy, Fx, Fy);
-        if (i) rest += f[i];
-    }
+    for (int i = 1; i < kQ; ++i) rest += f[i];
     const R uu = ux * ux + uy * uy;
+    const R G0 = sp4_G(K, 0, S, ux, uy, Fx, Fy);
     // Eq. 28 for the unshifted f: c_s^2 / (1 - w_0) = 3/5, s_0(u) = -(2/3) u.u, tau_g G_0
-    const R p = R(0.6) * (rest - R(2.0 / 3.0) * uu + R(K.tau) * G[0]);
+    const R p = R(0.6) * (rest - R(2.0 / 3.0) * uu + R(K.tau) * G0);
     const R upx = uprev[c], upy = uprev[N + c], Fpx = uprev[2 * N + c], Fpy = uprev[3 * N + c];
     const R ig = R(K.inv_tau);
     const bool bot = K.walls && y == 0, top = K.walls && y == K.ny - 1;
     const int xs[3] = {x == 0 ? K.nx - 1 : x - 1, x, x == K.nx - 1 ? 0 : x + 1};
     const int ys[3] = {K.walls ? y - 1 : (y == 0 ? K.ny - 1 : y - 1), y,
                        K.walls ? y + 1 : (y == K.ny - 1 ? 0 : y + 1)};
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
+    // G_i(x + c_i, t): the destination cell, mirrored about a wall
+    auto Gnb = [&](int i) {
         const bool wall = (sy(i) > 0 && top) || (sy(i) < 0 && bot);
-        // G_i(x + c_i, t): the destination cell, mirrored about a wall
         const long long n = (long long)(wall ? y : ys[sy(i) + 1]) * K.nx + xs[sx(i) + 1];
-        const R Gn = sp4_G(K, i, src[n], unow[n], unow[N + n], unow[2 * N + n], unow[3 * N + n]);
-        const R Gp = sp4_G(K, i, S, upx, upy, Fpx, Fpy);   // G_i(x, t - 1)
-        const R cu = R(sx(i)) * ux + R(sy(i)) * uy;
-        const R si = R(sw(i)) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-        const R geq = i == 0 ? R(3) * p * (R(sw(0)) - R(1)) + si : R(3) * p * R(sw(i)) + si;
-        const R post = f[i] - (f[i] - geq) * ig + G[i] + R(0.5) * (Gn - Gp);
-        if (wall) {
-            // bounce-back of g = f - G/2: leaves as i with G_i(x + c_i), returns as opp(i)
-            fout[sopp(i) * N + c] = post - R(0.5) * Gn + R(0.5) * G[sopp(i)];
-        } else {
+        return sp4_G(K, i, src[n], unow[n], unow[N + n], unow[2 * N + n], unow[3 * N + n]);
+    };
+    // to x + c_i, or (wall) back into this cell as opp(i) after the bounce-back of g = f - G/2
+    auto emit = [&](int i, R post, R Gn, R Gopp) {
+        if ((sy(i) > 0 && top) || (sy(i) < 0 && bot))
+            fout[sopp(i) * N + c] = post - R(0.5) * Gn + R(0.5) * Gopp;
+        else
             fout[i * N + (long long)ys[sy(i) + 1] * K.nx + xs[sx(i) + 1]] = post;
-        }
+    };
+    {   // rest direction: its destination is this cell
+        const R geq = R(3) * p * (R(sw(0)) - R(1)) + R(sw(0)) * (-R(1.5) * uu);
+        const R Gp = sp4_G(K, 0, S, upx, upy, Fpx, Fpy);
+        emit(0, f[0] - (f[0] - geq) * ig + G0 + R(0.5) * (G0 - Gp), G0, G0);
+    }
+    // opposite pairs: G at t and t - 1 and s_i split into parts even and odd in c
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = pair2(q), j = sopp(i);
+        const R wi = R(sw(i));
+        const R cu = R(sx(i)) * ux + R(sy(i)) * uy;
+        const R ge = R(3) * p * wi + wi * (R(4.5) * cu * cu - R(1.5) * uu), go = wi * (R(3) * cu);
+        R Ge, Go, Gpe, Gpo;
+        sp4_G_parts(K, i, S, ux, uy, Fx, Fy, Ge, Go);
+        sp4_G_parts(K, i, S, upx, upy, Fpx, Fpy, Gpe, Gpo);
+        const R Gi = Ge + Go, Gj = Ge - Go, Gni = Gnb(i), Gnj = Gnb(j);
+        emit(i, f[i] - (f[i] - (ge + go)) * ig + Gi + R(0.5) * (Gni - (Gpe + Gpo)), Gni, Gj);
+        emit(j, f[j] - (f[j] - (ge - go)) * ig + Gj + R(0.5) * (Gnj - (Gpe - Gpo)), Gnj, Gi);
     }
 }
 
