@@ -344,8 +344,9 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 /* Releases the context and all its device memory. NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 
-/* ---- single-phase model of Remark 3 (Sec. 2.3) ---------------------------
- * The generalized model with rho~ = rho_0 and a constant density (rho = 1):
+/* ---- single-phase models of Sec. 2.3 (Remarks 3, 1, 2; the Remark 4 scheme) --
+ * Remark 3 (the default model): the generalized model with rho~ = rho_0 and a
+ * constant density (rho = 1):
  * incompressible Navier-Stokes flow with a mass source, div u = S(x), and a
  * uniform body force F, on the D2Q9 lattice (x periodic; y periodic or halfway
  * bounce-back walls). Equilibrium of Remark 3 (g_0 stored shifted by rho_0),
