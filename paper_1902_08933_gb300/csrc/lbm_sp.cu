@@ -838,7 +838,8 @@ lbm_status lbm_sp_init(lbm_sp_ctx* c, const double* source_host) {
     }
     c->cur = 0;
     // at rest: Remark 3 g^eq = rho_0 delta_i0 (g_0 stored shifted by rho_0);
-    // Remark 1 g^eq = w_i at rho = 1 (stored shifted by w_i) -- zero either way
+    // Remark 1 g^eq = w_i at rho = 1, Remark 2 w_i p_0 (stored shifted by
+    // them) -- zero in every case
     if ((r = cudaMemsetAsync(c->g[0], 0, kQ * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
         return sp_cuda(c, r, "state reset");
     // Remark 4 scheme: u at t = -1 is u at t = 0 = 0
@@ -847,7 +848,7 @@ lbm_status lbm_sp_init(lbm_sp_ctx* c, const double* source_host) {
         (r = cudaMemsetAsync(c->ufield, 0, 8 * c->N * sp_elem(c->form), c->stream)) != cudaSuccess)
         return sp_cuda(c, r, "state reset");
     if (c->p.scheme == LBM_SP_SCHEME_REMARK4) {   // F(u = 0) = F_0 at t = -1
-        const double* F0 = &c->p.force_x;
+        const double F0[2] = {c->p.force_x, c->p.force_y};
         for (int a = 0; a < 2; ++a) {
             if (c->form == LBM_F64)
                 sp_fill_kernel<double><<<blocks(c->N), 256, 0, c->stream>>>(
