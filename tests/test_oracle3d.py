@@ -232,3 +232,33 @@ def test_layered_poiseuille_3d_within_paper_table2(orc):
     ua = np.array([orc.layered_ux(y, h, G, muB, muA) for y in yj])
     err = np.abs(ux - ua).sum() / np.abs(ua).sum()
     assert err < 0.0104, err
+
+
+def test_laplace_law_sphere_with_mu_grad_phi_force(orc):
+    # F_s = mu grad(phi) (Sec. 3.1) differs from -phi grad(mu) by grad(phi mu), so
+    # Laplace's law holds for P with p replaced by p - phi mu; left as p the jump
+    # is near twice 2 sigma / R (mu is about 2 sigma / R in both bulks).
+    cfg = wl.static_droplet3(32, R=9.0)
+    cfg["surface_force"] = 0
+    P, st = _run3(orc, cfg, 1000)
+    f = orc.fields3(P, st)
+    bulk_A, bulk_B = f["phi"] > 1 - 1e-3, f["phi"] < 1e-3
+    Pc = f["P"] - f["phi"] * f["mu"]
+    expected = wl.laplace_dp_expected3(cfg)
+    assert abs((Pc[bulk_A].mean() - Pc[bulk_B].mean()) / expected - 1) < 0.05
+    assert abs((f["P"][bulk_A].mean() - f["P"][bulk_B].mean()) / expected - 2) < 0.25
+
+
+@pytest.mark.parametrize("phase", [0.0, 1.0], ids=["phase-B", "phase-A"])
+def test_hydrostatic_rest_under_buoyancy_3d(orc, phase):
+    # Sec. 4.4 buoyancy -(rho - rho_A) g along -y: a uniform phase at rest between
+    # walls keeps u = 0 with dp/dy = (rho_A - rho) g exactly (linear p).
+    g = 1e-5
+    cfg = wl.layered_poiseuille3(nx=2, ny=16, nz=2, force_x=0.0, rho_ratio=10.0)
+    cfg.update(nu_A=1.0 / 6.0, nu_B=1.0 / 6.0, gravity=g, init=dict(kind="uniform", value=phase))
+    P, st = _run3(orc, cfg, 10000)
+    f = orc.fields3(P, st)
+    expected = (cfg["rho_A"] - cfg["rho_B"]) * g if phase == 0.0 else 0.0
+    dpdy = (f["p"][:, 2:, :] - f["p"][:, :-2, :]) / 2.0
+    assert np.max(np.abs(dpdy[:, 2:-2, :] - expected)) < 1e-12 * 9e-5
+    assert np.max(np.abs(np.stack([f["ux"], f["uy"], f["uz"]]))) < 1e-15

@@ -115,6 +115,46 @@ def test_laplace_law(orc, R):
     assert abs(dp / wl.laplace_dp_expected(cfg) - 1) < 0.02
 
 
+@pytest.mark.parametrize("R", [12.0, 16.0])
+def test_laplace_law_with_mu_grad_phi_force(orc, R):
+    # Sec. 3.1 allows F_s = mu grad(phi) as well as -phi grad(mu). They differ by
+    # a gradient: mu grad(phi) = -phi grad(mu) + grad(phi mu), so the hydrodynamic
+    # pressure of the mu grad(phi) form is that of the -phi grad(mu) form plus
+    # phi mu, and Laplace's law of Sec. 4.2 holds for P with p replaced by
+    # p - phi mu. Left as p, the jump comes out near 2 sigma / R (mu is about
+    # sigma / R in both bulks at equilibrium); a flipped or dropped term makes it 0.
+    cfg = wl.static_droplet(n=64, R=R)
+    cfg["surface_force"] = 0
+    P, st = _run(orc, cfg, 10000)
+    f = orc.fields(P, st)
+    bulk_A, bulk_B = f["phi"] > 1 - 1e-3, f["phi"] < 1e-3
+    Pc = f["P"] - f["phi"] * f["mu"]
+    dp = Pc[bulk_A].mean() - Pc[bulk_B].mean()
+    assert abs(dp / wl.laplace_dp_expected(cfg) - 1) < 0.02
+    raw = f["P"][bulk_A].mean() - f["P"][bulk_B].mean()
+    assert abs(raw / wl.laplace_dp_expected(cfg) - 2) < 0.15
+
+
+@pytest.mark.parametrize("phase", [0.0, 1.0], ids=["phase-B", "phase-A"])
+def test_hydrostatic_rest_under_buoyancy(orc, phase):
+    # Sec. 4.4 buoyancy F_y = -(rho - rho_A) g. A uniform phase at rest between
+    # halfway bounce-back walls has the exact steady state u = 0 with a pressure
+    # that is linear in y: grad p = F, so dp/dy = (rho_A - rho_B) g in phase B and
+    # 0 in phase A (rho = rho_A there). Two phases fix the affine function of rho:
+    # a flipped sign, a factor, or rho_B in place of rho_A fails one of them.
+    ny, g = 16, 1e-5
+    cfg = wl.layered_poiseuille(nx=4, ny=ny, force_x=0.0, rho_ratio=10.0)
+    cfg.update(nu_A=1.0 / 6.0, nu_B=1.0 / 6.0, gravity=g, init=dict(kind="uniform", value=phase))
+    P, st = _run(orc, cfg, 10000)
+    f = orc.fields(P, st)
+    expected = -(cfg["rho_B"] - cfg["rho_A"]) * g if phase == 0.0 else 0.0
+    for x in range(4):
+        p = f["p"][:, x]
+        dpdy = (p[2:] - p[:-2]) / 2.0          # exact on a linear profile
+        assert np.max(np.abs(dpdy[2:-2] - expected)) < 1e-12 * 9e-5
+    assert np.max(np.hypot(f["ux"], f["uy"])) < 1e-15
+
+
 def test_cahn_hilliard_linear_growth_rate(orc):
     # Linearising the C-H equation (Eqs. 3a, 8) about phi = 1/2 (psi''(1/2) = -beta):
     # a mode cos(kx) grows at M k^2 (beta - kappa k^2); with the stencil of Eq. 30b,
