@@ -35,7 +35,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# bytes each storage form moves a lattice update (state read once and written once)
 BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176}
+# the method's algorithmic bytes: 9 + 9 populations, phi u (2) and p read and
+# written once in the form's word size; the two-float h_0 of f32_c (8 bytes, not
+# 4) is the form's own addition and not counted
+ALGO_BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_c": 168, "f32_g16": 132, "f32_h16": 100}
 # D3Q15: 15 + 15 populations, phi u (3), p, each read and written once
 BYTES_PER_LUP_D3 = {"f64": 544, "f32": 272, "f32_c": 280}
 METRIC = "MLUPS and % of HBM peak, FP64 vs FP32/FP16-storage vs batched, at stated error"
@@ -53,12 +58,16 @@ def parse():
                     help="load path of the step kernel (lbm_set_pipeline)")
     ap.add_argument("--kernel-run", default=None,
                     choices=["bubble3d", "source_flow", "source_flow_remark1", "source_flow_remark2",
-                             "source_flow_remark4"],
+                             "source_flow_remark4", "batched"],
                     help="only time one step loop of another workload (for profiling): the "
-                         "128 x 256 x 128 D3Q15 bubble or the 4096 x 4096 single-phase source "
-                         "flow of Remark 3, Remark 1 or the Remark 4 scheme with drag")
+                         "128 x 256 x 128 D3Q15 bubble, the 4096 x 4096 single-phase source "
+                         "flow of Remark 3, Remark 1 or the Remark 4 scheme with drag, or the "
+                         "512 mixed instances of the batched configuration")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the side-by-side forms, e2e and CPU legs")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="time the built-in launch plan instead of the autotuner's choice "
+                         "(profiling runs: no trial launches before the timed ones)")
     return ap.parse_args()
 
 
@@ -203,63 +212,63 @@ def time_steps(lbm, sim, stream, steps, warmup):
 
 
 # ------------------------------------------------------------------------- CPU oracle
-def oracle_rate(cfg, target_s=15.0):
-    """FP64 oracle on the host cores: one step of the full grid timed once, then as
-    many whole steps as fit in about target_s seconds."""
-    from oracle import oracle as orc
-    from paper_1902_08933_gb300 import workloads as wl
-    orc.build()
-    P = orc.params(cfg)
-    st = orc.init(P, wl.initial_phi(cfg))
-    t0 = time.perf_counter()
-    orc.step(P, st, 1)
-    t1 = time.perf_counter()
-    n = max(1, min(200, int(target_s / max(t1 - t0, 1e-6)) - 1))
-    t2 = time.perf_counter()
-    orc.step(P, st, n)
-    t3 = time.perf_counter()
-    cells = cfg["nx"] * cfg["ny"]
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return cells * n / (t3 - t2) / 1e6, threads, n, t3 - t2
+def oracle_rate(threads, seconds):
+    """FP64 oracle (its -O3 timed build) on the host cores, in a child process
+    with OMP_NUM_THREADS = threads: whole 1024 x 4096 steps for about `seconds`
+    (a full-width slab where one step is too long). Returns oracle.timing's record."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), LBM_ORACLE_BUILD="timed")
+    r = subprocess.run([sys.executable, "-m", "oracle.timing", "--seconds", str(seconds)],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: %s" % r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle as it stands, on the host cores, each
-    step one time step of a bounded horizontal slab of the bubble workload."""
+    """Reference arm: the FP64 CPU oracle as it stands (its -O3 timed build) on the
+    host cores, each step one whole time step of the 1024 x 4096 bubble, or of a
+    full-width horizontal slab of it where the whole run would not end within
+    about two minutes."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    os.environ["LBM_ORACLE_BUILD"] = "timed"
     from oracle import oracle as orc
+    from oracle import timing
     from paper_1902_08933_gb300 import workloads as wl
     orc.build()
     full = wl.rising_bubble()
-    # slab: full width, rows sized so one step takes about 40 ms on this host
-    probe = dict(full, ny=64, init=dict(full["init"], cy=32.0))
-    P = orc.params(probe)
-    st = orc.init(P, wl.initial_phi(probe))
+    P = orc.params(full)
+    st = orc.init(P, wl.initial_phi(full))
     t0 = time.perf_counter()
-    orc.step(P, st, 2)
-    per_row = (time.perf_counter() - t0) / 2 / 64
-    rows = int(max(16, min(full["ny"], 0.04 / max(per_row, 1e-9))))
-    cfg = dict(full, ny=rows, init=dict(full["init"], cy=rows / 2.0))
-    P = orc.params(cfg)
-    st = orc.init(P, wl.initial_phi(cfg))
+    orc.step(P, st, 1)
+    t_step = time.perf_counter() - t0
+    budget_s = 120.0
+    cfg = full
+    if (args.steps + args.warmup) * t_step > budget_s:
+        rows = int(max(16, min(full["ny"], full["ny"] * budget_s /
+                               ((args.steps + args.warmup) * t_step))))
+        cfg = dict(full, ny=rows, init=dict(full["init"], cy=rows / 2.0))
+        P = orc.params(cfg)
+        st = orc.init(P, wl.initial_phi(cfg))
     orc.step(P, st, args.warmup)
     t0 = time.perf_counter()
     orc.step(P, st, args.steps)
     dt = time.perf_counter() - t0
     cells = cfg["nx"] * cfg["ny"]
     mlups = cells * args.steps / dt / 1e6
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = "%d x %d slab of the 1024 x 4096 bubble (walls in y), %d steps" % (
-        cfg["nx"], cfg["ny"], args.steps)
+    threads = timing.omp_threads()
+    same = cfg is full
+    sample = ("%d whole 1024 x 4096 steps" % args.steps if same else
+              "%d steps of a %d x %d slab of the 1024 x 4096 bubble (walls in y)" % (
+                  args.steps, cfg["nx"], cfg["ny"])) + ", gcc -O3 build"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "rising_bubble_1024x4096_rho10_qim (CPU slab sample)",
-                   "sample_rows": rows},
+        "config": {"workload": "rising_bubble_1024x4096_rho10_qim" + ("" if same else " (CPU slab sample)"),
+                   "rows": cfg["ny"], "same_config": same},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -276,7 +285,14 @@ def kernel_run(args):
     from paper_1902_08933_gb300 import workloads as wl
     build.build()
     stream = torch.cuda.Stream()
-    if args.kernel_run == "bubble3d":
+    if args.kernel_run == "batched":
+        cfgs = wl.batched_mixed(512)
+        cells = int(wl.lups(cfgs, 1))
+        form = args.form
+        sim = lbm.Simulation(cfgs, form, stream=stream.cuda_stream,
+                             phi0=[wl.initial_phi(c) for c in cfgs])
+        bpl = BYTES_PER_LUP[form]
+    elif args.kernel_run == "bubble3d":
         cfg = wl.rising_bubble3()
         cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
         form = args.form if args.form in BYTES_PER_LUP_D3 else "f32_c"
@@ -294,6 +310,10 @@ def kernel_run(args):
             spcfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
         sim = lbm.SourceFlow(spcfg, form, stream=stream.cuda_stream, source=src)
         bpl = {0: 76, 1: 132, 2: 132, 4: 160}[model] * (2 if form == "f64" else 1)
+    shape = None
+    if args.kernel_run == "batched" and not args.no_tune:
+        sim.step(2)
+        shape = lbm.lbm_autotune_shape(sim.ctx)
     sim.step(max(args.warmup, 2))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -304,7 +324,8 @@ def kernel_run(args):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"kernel_run": args.kernel_run, "form": form, "ms_per_step": ms,
-                      "MLUPS": cells / ms / 1e3, "GBps_algorithmic": bpl * cells / ms / 1e6}))
+                      "MLUPS": cells / ms / 1e3, "GBps_algorithmic": bpl * cells / ms / 1e6,
+                      "launch_shape": shape}))
     sim.close()
 
 
@@ -344,6 +365,10 @@ def main():
     lbm.lbm_set_pipeline(sim.ctx, {"auto": lbm.LBM_PIPELINE_AUTO, "plain": lbm.LBM_PIPELINE_PLAIN,
                                    "async": lbm.LBM_PIPELINE_ASYNC, "tma": lbm.LBM_PIPELINE_TMA,
                                    "pairs": lbm.LBM_PIPELINE_PAIRS}[args.pipeline])
+    shape = None
+    if args.pipeline == "auto" and not args.no_tune:
+        sim.step(2)
+        shape = lbm.lbm_autotune_shape(sim.ctx)   # state and time level are left as they were
     launches = lbm.lbm_launches_per_step(sim.ctx)
     variant = lbm.lbm_launch_info(sim.ctx, 0)["variant"]
     warm(sim, args.warmup)
@@ -370,7 +395,8 @@ def main():
     sim.close()
     value = world * cells * args.steps / (ms * 1e-3) / 1e6
     per_launch_s = ms * 1e-3 / (args.steps * launches)
-    achieved = BYTES_PER_LUP[args.form] * cells / per_launch_s / 1e9
+    achieved = ALGO_BYTES_PER_LUP[args.form] * cells / per_launch_s / 1e9
+    achieved_form = BYTES_PER_LUP[args.form] * cells / per_launch_s / 1e9
     traffic = traffic_record("%s" % args.form)
     result = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -384,11 +410,14 @@ def main():
                                                   "f32_c": "h0 2xf32, h1-8 f32, g f32"}[args.form],
                    "l2": "state %.0f MB > 129 MB L2, no flush" % (
                        2 * BYTES_PER_LUP[args.form] / 2 * cells / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "launch_shape": shape if shape else {"pipeline": args.pipeline, "tuned": False}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_lup": BYTES_PER_LUP[args.form]},
+                     "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[args.form],
+                     "form_bytes_per_lup": BYTES_PER_LUP[args.form],
+                     "frac_form_bytes": achieved_form / hbm_peak},
         "clocks": clk,
         "gpu_launches": args.steps * launches,
         "mass_drift": abs(d["sum_phi"] - phi0.sum()) / phi0.sum(),
@@ -450,13 +479,17 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     cfgs = wl.batched_mixed(512)
     lups_per_step = wl.lups(cfgs, 1)
     batched = {}
-    for form in ("f32", "f32_g16"):
+    for form in ("f32", "f32_g16", "f32_h16", "f32_c"):
         with lbm.Simulation(cfgs, form, stream=stream.cuda_stream,
                             phi0=[wl.initial_phi(c) for c in cfgs]) as sim:
             Kb = 100
+            sim.step(2)
+            shape = lbm.lbm_autotune_shape(sim.ctx)
             ms = time_steps(lbm, sim, stream, Kb, 5)
             batched[form] = {"MLUPS": lups_per_step * Kb / (ms * 1e-3) / 1e6,
-                             "launches_per_step": lbm.lbm_launches_per_step(sim.ctx)}
+                             "launches_per_step": lbm.lbm_launches_per_step(sim.ctx),
+                             "variant": lbm.lbm_launch_info(sim.ctx, 0)["variant"],
+                             "launch_shape": shape}
     batched["instances"] = len(cfgs)
     batched["cells"] = int(lups_per_step)
     out["batched"] = batched
@@ -519,7 +552,9 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     # The record of step t is copied asynchronously into one of NSLOT pinned
     # slots and checked on the host once step t has finished, NSLOT - 1 steps
     # later, so the host never waits on the step it has just queued.
-    Ke = max(20, args.steps // 4)
+    # 500 steps at least whatever --steps is, so that the one-time phi0 upload
+    # and field read-back are spread as in a real run, not over a handful of steps
+    Ke = max(500, args.steps // 4)
     pinned = torch.from_numpy(phi0).pin_memory()
     host_phi0 = pinned.numpy()
     fields_out = torch.zeros((4, cfg["ny"], cfg["nx"]), dtype=torch.float64).pin_memory().numpy()
@@ -551,20 +586,39 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
             done[tc % NSLOT].synchronize()
             check(recs[tc % NSLOT], tc)
         mon = {"sum_phi": recs[(Ke - 1) % NSLOT].sum_phi}
+        t1 = time.perf_counter()
         lbm.lbm_get_fields(sim.ctx, 0, 0xF, fields_out)
         dt = time.perf_counter() - t0
+        t_read = time.perf_counter() - t1
+    # the one-time copies alone (same calls, outside the timed loop)
+    with lbm.Simulation(cfg, args.form, stream=stream.cuda_stream) as sim:
+        lbm.lbm_init(sim.ctx, 0, host_phi0)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        lbm.lbm_init(sim.ctx, 0, host_phi0)
+        t_init = time.perf_counter() - t2
     d2h = ctypes.sizeof(lbm.lbm_monitor) + 8 * 4 * cells / Ke
     out["e2e"] = {"value": cells * Ke / dt / 1e6, "unit": "MLUPS",
                   "h2d_bytes_per_step": 8 * cells / Ke, "d2h_bytes_per_step": d2h,
                   "steps": Ke, "per_step": "lbm_step(1) with the fused monitor + lbm_read_monitor_async "
                                           "(sum phi, kinetic energy, max |u| to pinned host memory, "
                                           "checked once the step has finished)",
+                  "once": "lbm_init from pinned host phi0 (%.1f MB, about %.2f ms) before the first step, "
+                          "lbm_get_fields of phi, ux, uy, p to pinned host memory (%.1f MB, %.2f ms) after "
+                          "the last, both inside the timed region and spread over its %d steps" % (
+                              8 * cells / 1e6, t_init * 1e3, 32 * cells / 1e6, t_read * 1e3, Ke),
+                  "ms_per_step_loop": (dt - t_init - t_read) * 1e3 / Ke,
                   "mass_drift_monitor": abs(mon["sum_phi"] - float(phi0.sum())) / float(phi0.sum())}
 
-    # CPU oracle on the host cores (bounded sample: whole-grid steps for ~15 s)
-    mlups, threads, n, secs = oracle_rate(cfg)
-    out["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-                           "sample": "%d full 1024x4096 steps (%.1f s), FP64, OpenMP over rows" % (n, secs)}
+    # CPU oracle on the host cores (bounded samples of the same workload: whole-grid
+    # steps for about 12 s on every core, then a single-thread figure)
+    allc = oracle_rate(os.cpu_count() or 1, 12.0)
+    one = oracle_rate(1, 8.0)
+    out["cpu_baseline"] = {"value": allc["mlups"], "unit": "MLUPS", "cores": allc["threads"],
+                           "kind": "oracle", "build": allc["build"],
+                           "sample": allc["sample"] + ", OpenMP over rows",
+                           "single_thread": {"value": one["mlups"], "unit": "MLUPS", "cores": 1,
+                                             "sample": one["sample"]}}
     return out
 
 

@@ -135,8 +135,9 @@ typedef struct lbm_monitor {
     double kinetic_energy;               /* sum of rho |u|^2 / 2 (u of Eq. 27a)         */
     double max_u;                        /* max |u|                                     */
     int32_t nonfinite;                   /* 1 if phi or u was NaN or infinite somewhere */
-    int32_t device_status;               /* the context's device status word then (0 ok,
-                                            LBM_ETIMEOUT: a bounded wait ran out)       */
+    int32_t device_status;               /* the context's device status word when the
+                                            instance's last block of that step finished
+                                            (0 ok, LBM_ETIMEOUT: a bounded wait ran out) */
     int64_t time;                        /* time level the sums belong to               */
 } lbm_monitor;
 
@@ -180,8 +181,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * step of every lbm_step call runs step kernels that also reduce, over the
  * cells they collide, sum(phi), the kinetic energy sum(rho |u|^2 / 2) and
  * max |u| of the fields at that step's input time level (the fields
- * lbm_get_fields returns at that time), plus one small kernel that combines the
- * per-block values of each instance in a fixed order; the other steps run the
+ * lbm_get_fields returns at that time); the last block of each instance to
+ * finish combines the per-block values of that instance in a fixed order (the
+ * work-list order, whichever block comes last) and writes its record, so the
+ * monitored step is as many launches as a plain one. The other steps run the
  * plain kernels. FP64 forms sum in FP64; FP32-arithmetic forms sum phi in a
  * float-float pair per thread (about 48 bits) and the energy in FP32 per thread,
  * then in FP64. Allocates the per-instance record on the first enable.
@@ -220,6 +223,33 @@ lbm_status lbm_get_fields_device(lbm_ctx* ctx, int instance, unsigned mask, doub
  * Returns LBM_ENONFINITE (with *out filled) if a population is not finite. */
 lbm_status lbm_diagnostics(lbm_ctx* ctx, int instance, lbm_diag* out);
 
+/* Row exchange for a domain split into horizontal slabs (one slab per GPU, or
+ * several slabs as instances of one context). The paper has no counterpart:
+ * this moves state, it computes nothing. One time step of a cell depends on the
+ * state of the cells up to three rows away (phi of h at distance two feeds mu,
+ * whose stencil feeds the collision of a neighbour, which streams into the
+ * cell), so a slab that also holds 3k rows of its neighbours' state (ghost
+ * rows, in a walled instance whose edge rows are those ghosts) advances its own
+ * rows exactly for k steps; then the ghost rows are refreshed from the
+ * neighbours' own rows with these two calls. D2Q9 contexts only.
+ *
+ * lbm_row_bytes: bytes one row of an instance's state takes in the storage form:
+ *   every population plane (h, the two-float h_0 plane of the conservative
+ *   forms, g), the two planes of phi u of the previous step and p of the
+ *   previous step, nx elements each; 0 for an invalid context or instance.
+ * lbm_pack_rows: copies rows [y0, y0 + nrows) of the instance's current state
+ *   into dev_buf (caller-owned device memory of at least
+ *   nrows * lbm_row_bytes bytes, checked against `bytes`), plane by plane in the
+ *   order above, each plane's rows contiguous. Asynchronous on the context's
+ *   stream (the buffer is valid once the stream has passed this point).
+ * lbm_unpack_rows: the reverse: writes rows [y0, y0 + nrows) of the instance's
+ *   current state from dev_buf (same layout), on the context's stream.
+ * Errors: LBM_EINVAL (NULL context or buffer, bad instance, rows outside
+ * [0, ny), bytes too small, D3Q15 context), LBM_ECUDA. */
+size_t lbm_row_bytes(const lbm_ctx* ctx, int instance);
+lbm_status lbm_pack_rows(lbm_ctx* ctx, int instance, int y0, int nrows, void* dev_buf, size_t bytes);
+lbm_status lbm_unpack_rows(lbm_ctx* ctx, int instance, int y0, int nrows, const void* dev_buf, size_t bytes);
+
 /* Raw populations of one instance, converted to FP64 (debugging and tests):
  * host_h and host_g receive 9*nx*ny doubles each (plane i at i*nx*ny), g with
  * g_0 - rho_0 (rho_0 = 0). Either pointer may be NULL. Synchronises. */
@@ -254,8 +284,16 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
  *                      sm_100+, with 8-byte pair loads and stores
  *                      (FP32-arithmetic forms, instances with nx even, strips
  *                      of at least 64 columns).
- *  LBM_PIPELINE_AUTO   (default) PAIRS where available, else ASYNC, else TMA,
- *                      else PLAIN.
+ *  LBM_PIPELINE_BATCHED the PAIRS kernel over every instance of the context in
+ *                      ONE persistent launch a step: blocks of 128 threads take
+ *                      descriptors of two strips of up to 128 columns (two
+ *                      thread groups with their own barriers) from an
+ *                      on-device queue, longest runs first. The strip width is
+ *                      fixed (lbm_set_launch sets the run length only). Only
+ *                      when every instance can use PAIRS; else as AUTO.
+ *  LBM_PIPELINE_AUTO   (default) BATCHED for contexts of several instances that
+ *                      all can use it; otherwise PAIRS where available, else
+ *                      ASYNC, else TMA, else PLAIN.
  * An instance that cannot use a variant falls back to PLAIN. Takes effect at
  * the next lbm_step. LBM_EINVAL for an unknown mode.
  * D3Q15 contexts: PLAIN runs the unfused step (phi, mu and the collision as
@@ -265,7 +303,7 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
  * which runs the unfused step (faster there). Both give the same result. */
 enum {
     LBM_PIPELINE_AUTO = 0, LBM_PIPELINE_PLAIN = 1, LBM_PIPELINE_ASYNC = 2, LBM_PIPELINE_TMA = 3,
-    LBM_PIPELINE_PAIRS = 4
+    LBM_PIPELINE_PAIRS = 4, LBM_PIPELINE_BATCHED = 5
 };
 lbm_status lbm_set_pipeline(lbm_ctx* ctx, int mode);
 
@@ -279,13 +317,45 @@ lbm_status lbm_set_graphs(lbm_ctx* ctx, int enable);
 
 /* Launch index (0 .. lbm_launches_per_step - 1) of one step: strip width,
  * number of thread blocks, and the load path it uses (0 plain, 1 cp.async,
- * 2 TMA, 3 pairs). Any output pointer may be NULL. LBM_EINVAL for an index out
- * of range. */
+ * 2 TMA, 3 pairs, 4 batched: the one persistent launch, whose blocks count is
+ * its grid, one block per resident slot, however many descriptors it takes).
+ * Any output pointer may be NULL. LBM_EINVAL for an index out of range. */
 lbm_status lbm_launch_info(lbm_ctx* ctx, int index, int* tile_x, int* blocks, int* variant);
 
-/* Times the candidate launch shapes on the current state (the state is saved
- * and restored around the trials) and keeps the fastest. best_tile_x / best_rows
- * may be NULL. Synchronises. */
+/* Launch shape chosen by the autotuner (the paper has no counterpart; this is
+ * scheduling, not arithmetic: every shape computes the same step). */
+typedef struct lbm_launch_shape {
+    int32_t pipeline;                    /* LBM_PIPELINE_* (load path; one or two cells
+                                            a thread; the batched launch)             */
+    int32_t tile_x;                      /* strip width asked for (0: built-in choice) */
+    int32_t rows;                        /* run length asked for (0: built-in choice)  */
+    int32_t trials;                      /* distinct plans timed; 0: from the cache    */
+    double ms_per_step;                  /* measured time of the chosen shape          */
+    double default_ms_per_step;          /* measured time of the built-in plan         */
+} lbm_launch_shape;
+
+enum { LBM_TUNE_NO_CACHE = 1 };
+
+/* Autotuner. Times, on the context's current state, every distinct plan among
+ * load paths (LBM_PIPELINE_PAIRS, BATCHED, PLAIN, ASYNC, TMA -- i.e. one or two
+ * cells per thread, one launch per strip width or one for the whole context)
+ * x strip widths {built-in, 64, 128, 256} x run lengths {built-in, 8, 16, 32,
+ * 64}, the built-in plan (AUTO, 0, 0) first; plans that launch the same work
+ * are timed once (two warm-up steps, then the best of two 8-step timings with
+ * CUDA events). Keeps the fastest (lbm_set_pipeline / lbm_set_launch) and
+ * stores it in a process-wide cache keyed by device, storage form and the
+ * instances' sizes and boundaries, which later calls on a context of the same
+ * key use without trials (flags = LBM_TUNE_NO_CACHE forces the trials). The
+ * trials run real steps on a saved copy of the state: afterwards the state,
+ * the buffer parity, lbm_time and the monitor settings are exactly as before
+ * (the backup is device memory of the state's size, freed before returning).
+ * out may be NULL. Synchronises. Errors: LBM_EINVAL (NULL context, D3Q15,
+ * unknown flags), LBM_ESTATE (an instance not initialised), LBM_ECUDA. */
+lbm_status lbm_autotune_shape(lbm_ctx* ctx, int flags, lbm_launch_shape* out);
+
+/* The same trials (never from the cache); returns the strip width and run
+ * length of the chosen shape (its load path is set on the context too).
+ * best_tile_x / best_rows may be NULL. Synchronises. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int* best_tile_x, int* best_rows);
 
 /* Kernel launches queued by one lbm_step(1) (for accounting); 0 on error. */
@@ -312,10 +382,13 @@ int64_t lbm_time(const lbm_ctx* ctx, int instance);
  * into the library (229 KB, held by every GPU that loads it until exit), so
  * nx * ny may be at most 16,777,216 cells; larger grids return LBM_EINVAL, as
  * do NULL pointers or nx, ny < 1. The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture. All calls share the array, so
- * calls that overlap on the GPU (several streams or devices' threads at once)
- * race. Asynchronous; LBM_ECUDA if the set-up or a launch fails. */
+ * array's device address (cudaGetSymbolAddress) with the device current and
+ * keeps it for the life of the process; make that first call before any stream
+ * capture, and do not reset the device (cudaDeviceReset) after it, since the
+ * kept address would then be stale. Every device has its own copy of the
+ * array: calls that overlap on the same device (several streams, or several
+ * host threads using one device) race on it, calls on different devices do
+ * not. Asynchronous; LBM_ECUDA if the set-up or a launch fails. */
 lbm_status lbm_reduce_fields_noalloc(const double* fields_device, int nx, int ny,
                                      void* cuda_stream, double* out_device);
 

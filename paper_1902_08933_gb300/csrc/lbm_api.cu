@@ -1,9 +1,12 @@
 // lbm_api.cu -- the C ABI of include/lbm.h: contexts, device memory, work
 // planning, kernel dispatch, field readback, diagnostics and checkpoints.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -150,6 +153,11 @@ struct lbm_ctx {
     std::vector<Launch> launches;
     std::vector<WorkItem> work;
     WorkItem* d_work = nullptr;
+    // batched step (one persistent launch over all instances): block descriptors
+    // and the queue counters the kernel takes them with
+    lbm::BlockDesc* d_desc = nullptr;
+    int ndesc = 0;
+    int* d_queue = nullptr;
     bool plan_dirty = true;
     // CUDA graph of 2 * graph_pairs steps starting from cur == 0 (built on first use,
     // dropped when the plan changes)
@@ -163,6 +171,7 @@ struct lbm_ctx {
     bool monitor = false;
     double* d_mon_partials = nullptr;   // kMonQ doubles per work item
     int* d_mon_csr = nullptr;           // per instance: work items [ptr[k], ptr[k+1]) of idx
+    int* d_mon_count = nullptr;         // per instance: blocks of the monitored step done (0 between steps)
     lbm_monitor* d_mon = nullptr;       // one record per instance
     int64_t steps_total = 0;            // steps taken by the context
     int64_t* d_time_base = nullptr;     // per instance: time - steps_total (device copy)
@@ -211,6 +220,16 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.work = nullptr;
     a.status = c->d_status;
     a.mon = nullptr;
+    a.mon_all = nullptr;
+    a.mon_count = nullptr;
+    a.mon_csr = nullptr;
+    a.mon_n = 0;
+    a.mon_rec = nullptr;
+    a.time_base = nullptr;
+    a.mon_step = 0;
+    a.desc = c->d_desc;
+    a.ndesc = c->ndesc;
+    a.queue = c->d_queue;
     return a;
 }
 
@@ -249,12 +268,13 @@ int default_tile_pairs(int nx) {   // strip width of the paired kernel (2 column
 // kernel 16-byte row segments (nx % 8 == 0, see lbm_step_tma.cuh); both exist for
 // the FP32-arithmetic forms, the cp.async kernel for FP32 storage of h and p.
 void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, bool f_tma,
-            int* tile, int* variant) {
+            int* tile, int* variant, int mode = -1) {
     const bool pairs_ok = f_pairs && p.nx % 2 == 0 && (c->tile_req == 0 || c->tile_req >= 64);
     const bool tma_ok = f_tma && p.nx % 8 == 0 && p.nx >= 8;
     int v = lbm::kPlain;
-    switch (c->pipeline) {
+    switch (mode < 0 ? c->pipeline : mode) {
         case LBM_PIPELINE_AUTO:
+        case LBM_PIPELINE_BATCHED:   // (when the batched launch does not apply)
             v = pairs_ok ? lbm::kPairs : (f_async ? lbm::kAsync : (tma_ok ? lbm::kTma : lbm::kPlain));
             break;
         case LBM_PIPELINE_PAIRS: v = pairs_ok ? lbm::kPairs : lbm::kPlain; break;
@@ -273,6 +293,22 @@ void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, b
 // share a run boundary read its halo rows at the same time (both at their start
 // or both at their end), from L2 rather than HBM.
 lbm_status plan_d3(lbm_ctx* c);
+lbm_status plan_batched(lbm_ctx* c, bool f_pairs, bool f_async, bool f_tma, int sms);
+lbm_status finish_plan(lbm_ctx* c);
+
+// The batched launch serves a context when asked for (LBM_PIPELINE_BATCHED) or,
+// under LBM_PIPELINE_AUTO, when it holds several instances; in both cases only
+// if every instance can use the paired kernel.
+bool use_batched(const lbm_ctx* c, bool f_pairs, bool f_async, bool f_tma) {
+    if (c->d3 || !f_pairs) return false;
+    if (c->pipeline != LBM_PIPELINE_BATCHED && !(c->pipeline == LBM_PIPELINE_AUTO && c->n > 1)) return false;
+    for (const lbm_params& p : c->params) {
+        int tx = 0, variant = 0;
+        choose(c, p, f_pairs, f_async, f_tma, &tx, &variant, LBM_PIPELINE_PAIRS);
+        if (variant != lbm::kPairs) return false;
+    }
+    return true;
+}
 
 lbm_status plan(lbm_ctx* c) {
     if (c->d3) return plan_d3(c);
@@ -292,6 +328,7 @@ lbm_status plan(lbm_ctx* c) {
         f_tma = lbm::has_tma_t<decltype(F)::value>();
         return cudaSuccess;
     });
+    if (use_batched(c, f_pairs, f_async, f_tma)) return plan_batched(c, f_pairs, f_async, f_tma, sms);
     // Several instances: one run length for all, sized for about four waves of
     // blocks (blocks of different instances differ in width and length, so one
     // exact wave cannot be had; shorter runs balance better but re-read more
@@ -370,6 +407,72 @@ lbm_status plan(lbm_ctx* c) {
         c->launches.push_back({tiles[k / 4], (int)c->work.size(), (int)by_class[k].size(), k % 4});
         c->work.insert(c->work.end(), by_class[k].begin(), by_class[k].end());
     }
+    c->ndesc = 0;
+    return finish_plan(c);
+}
+
+// Batched plan: the paired kernel's work items of every instance -- strips of
+// 128 columns (the batched kernel's group width; narrower instances take one
+// strip), runs of rows with alternating directions -- paired into block
+// descriptors (items of equal run length together) and sorted by run length,
+// longest first, so the queue hands out the long descriptors first and the
+// short ones fill the tail. Run length: about four descriptors per resident
+// block, unless set by lbm_set_launch (its strip width does not apply here).
+lbm_status plan_batched(lbm_ctx* c, bool, bool, bool, int sms) {
+    int occ = 1;
+    by_form(c->form, [&](auto F) {
+        occ = std::max(1, lbm::batched_occupancy_t<decltype(F)::value>());
+        return cudaSuccess;
+    });
+    constexpr int kStrip = 128;
+    int rows = c->rows_req;
+    if (rows <= 0) {
+        double group_rows = 0;
+        for (const lbm_params& p : c->params) group_rows += (double)((p.nx + kStrip - 1) / kStrip) * p.ny;
+        rows = (int)std::lround(group_rows / (2.0 * 4.0 * sms * occ));
+        rows = std::max(8, std::min(64, rows));
+    }
+    std::vector<WorkItem> items;
+    for (int k = 0; k < c->n; ++k) {
+        const lbm_params& p = c->params[k];
+        const int r = std::min(rows, p.ny);
+        const int strips = (p.nx + kStrip - 1) / kStrip, nchunks = (p.ny + r - 1) / r;
+        for (int st = 0; st < strips; ++st)
+            for (int ch = 0; ch < nchunks; ++ch) {
+                const int y0 = ch * r, y1 = std::min(p.ny, y0 + r);
+                WorkItem w;
+                w.inst = k;
+                w.x0 = st * kStrip;
+                w.nrows = y1 - y0;
+                w.dir = (ch % 2 == 0) ? -1 : 1;
+                w.ystart = w.dir < 0 ? y1 - 1 : y0;
+                w.pad = 0;
+                items.push_back(w);
+            }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem& x, const WorkItem& y) { return x.nrows > y.nrows; });
+    c->work = items;
+    std::vector<lbm::BlockDesc> host;
+    for (int j = 0; j < (int)items.size(); j += 2) {
+        lbm::BlockDesc d;
+        d.item[0] = j;
+        d.item[1] = j + 1 < (int)items.size() ? j + 1 : -1;
+        host.push_back(d);   // items sorted by run length: so are the descriptors
+    }
+    c->ndesc = (int)host.size();
+    c->launches.clear();
+    c->launches.push_back({kStrip, 0, (int)std::min<long long>(c->ndesc, (long long)sms * occ), lbm::kBatched});
+    cudaFree(c->d_desc);
+    c->d_desc = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_desc, host.size() * sizeof(lbm::BlockDesc)));
+    LBM_CK(c, cudaMemcpy(c->d_desc, host.data(), host.size() * sizeof(lbm::BlockDesc), cudaMemcpyHostToDevice));
+    if (!c->d_queue) LBM_CK(c, cudaMalloc(&c->d_queue, 2 * sizeof(int)));
+    LBM_CK(c, cudaMemset(c->d_queue, 0, 2 * sizeof(int)));
+    return finish_plan(c);
+}
+
+// Uploads the work list and sets up the monitor's per-instance item lists.
+lbm_status finish_plan(lbm_ctx* c) {
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -390,11 +493,15 @@ lbm_status plan(lbm_ctx* c) {
     }
     cudaFree(c->d_mon_partials);
     cudaFree(c->d_mon_csr);
+    cudaFree(c->d_mon_count);
     c->d_mon_partials = nullptr;
     c->d_mon_csr = nullptr;
+    c->d_mon_count = nullptr;
     LBM_CK(c, cudaMalloc(&c->d_mon_partials, c->work.size() * lbm::kMonQ * sizeof(double)));
     LBM_CK(c, cudaMalloc(&c->d_mon_csr, csr.size() * sizeof(int)));
     LBM_CK(c, cudaMemcpy(c->d_mon_csr, csr.data(), csr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    LBM_CK(c, cudaMalloc(&c->d_mon_count, (size_t)c->n * sizeof(int)));
+    LBM_CK(c, cudaMemset(c->d_mon_count, 0, (size_t)c->n * sizeof(int)));
     c->plan_dirty = false;
     return LBM_OK;
 }
@@ -515,6 +622,8 @@ void release(lbm_ctx* c) {
     cudaFree(c->sc.philo);
     cudaFree(c->d_inst);
     cudaFree(c->d_work);
+    cudaFree(c->d_desc);
+    cudaFree(c->d_queue);
     cudaFree(c->d_tmp);
     cudaFree(c->d_out);
     cudaFree(c->d_partials);
@@ -522,6 +631,7 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_status);
     cudaFree(c->d_mon_partials);
     cudaFree(c->d_mon_csr);
+    cudaFree(c->d_mon_count);
     cudaFree(c->d_mon);
     cudaFree(c->d_time_base);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -688,59 +798,30 @@ lbm_status lbm_init_device(lbm_ctx* c, int instance, const double* phi0_device) 
 }
 
 namespace {
-// One block per instance adds the monitor slots of its work items: thread t
-// takes items t, t + 128, ..., then a fixed shuffle / shared-memory tree combines
-// the threads (a fixed order, so the sums do not depend on timing). Then max
-// |u|^2 becomes max |u| and the record gets the non-finite flag, the status word
-// as the stream reaches it, and the time level.
-constexpr int kMonThreads = 128;
-__global__ void __launch_bounds__(kMonThreads) monitor_final(const double* __restrict__ partials,
-                                                             const int* __restrict__ csr, int n,
-                                                             const int* __restrict__ status, int64_t step,
-                                                             const int64_t* __restrict__ time_base,
-                                                             lbm_monitor* __restrict__ out) {
-    const int k = blockIdx.x, t = threadIdx.x;
-    const int* idx = csr + n + 1;
-    double m = 0.0, e = 0.0, u = 0.0, f = 0.0;
-    for (int j = csr[k] + t; j < csr[k + 1]; j += kMonThreads) {
-        const double* p = partials + (long long)idx[j] * lbm::kMonQ;
-        m += p[0];
-        e += p[1];
-        u = fmax(u, p[2]);
-        f += p[3];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        m += __shfl_down_sync(0xffffffffu, m, o);
-        e += __shfl_down_sync(0xffffffffu, e, o);
-        u = fmax(u, __shfl_down_sync(0xffffffffu, u, o));
-        f += __shfl_down_sync(0xffffffffu, f, o);
-    }
-    __shared__ double red[4][kMonThreads / 32];
-    const int lane = t & 31, w = t >> 5;
-    if (lane == 0) { red[0][w] = m; red[1][w] = e; red[2][w] = u; red[3][w] = f; }
-    __syncthreads();
-    if (t == 0) {
-        for (int v = 1; v < kMonThreads / 32; ++v) {
-            m += red[0][v];
-            e += red[1][v];
-            u = fmax(u, red[2][v]);
-            f += red[3][v];
-        }
-        lbm_monitor& r = out[k];
-        r.sum_phi = m;
-        r.kinetic_energy = e;
-        r.max_u = sqrt(u);
-        r.nonfinite = f != 0.0 ? 1 : 0;
-        r.device_status = *status;
-        r.time = step + time_base[k];
-    }
-}
+// lbm_monitor is written on the GPU through its device mirror.
+static_assert(sizeof(lbm::MonRecord) == sizeof(lbm_monitor), "monitor record layout");
+static_assert(offsetof(lbm::MonRecord, nonfinite) == offsetof(lbm_monitor, nonfinite) &&
+                  offsetof(lbm::MonRecord, device_status) == offsetof(lbm_monitor, device_status) &&
+                  offsetof(lbm::MonRecord, time) == offsetof(lbm_monitor, time),
+              "monitor record layout");
 
 // Queues one launch class of one time step on stream s, reading buffer set `in`.
-cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStream_t s, bool monitor) {
+// With `monitor` its blocks also reduce the per-step monitor; the last block of
+// each instance writes that instance's record for time level mon_step.
+cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStream_t s, bool monitor,
+                          int64_t mon_step = 0) {
     StepArgs a = step_args(c, in);
     a.work = c->d_work + L.offset;
-    a.mon = monitor ? c->d_mon_partials + (long long)L.offset * lbm::kMonQ : nullptr;
+    if (monitor) {
+        a.mon = c->d_mon_partials + (long long)L.offset * lbm::kMonQ;
+        a.mon_all = c->d_mon_partials;
+        a.mon_count = c->d_mon_count;
+        a.mon_csr = c->d_mon_csr;
+        a.mon_n = c->n;
+        a.mon_rec = reinterpret_cast<lbm::MonRecord*>(c->d_mon);
+        a.time_base = c->d_time_base;
+        a.mon_step = mon_step;
+    }
     return by_form(c->form, [&](auto F) {
         return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, s, L.variant, monitor);
     });
@@ -769,13 +850,8 @@ cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_s
         return lbm::launch_march3(c->form, a, c->sc, c->d_work, (int)c->work.size(), c->stream);
     }
     for (const auto& L : c->launches) {
-        cudaError_t e = enqueue_class(c, in, L, c->stream, monitor);
+        cudaError_t e = enqueue_class(c, in, L, c->stream, monitor, mon_step);
         if (e != cudaSuccess) return e;
-    }
-    if (monitor) {
-        monitor_final<<<c->n, kMonThreads, 0, c->stream>>>(c->d_mon_partials, c->d_mon_csr, c->n, c->d_status,
-                                                   mon_step, c->d_time_base, c->d_mon);
-        return cudaGetLastError();
     }
     return cudaSuccess;
 }
@@ -1032,6 +1108,71 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int instance, lbm_diag* out) {
     return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// The state of a context as storage segments (current buffers): h planes, the
+// two-float h_0 plane of conservative forms, g planes, phi u, p -- the order of
+// checkpoints and of the row exchange.
+struct Segment { void* dev; size_t elem; int planes; };
+
+std::vector<Segment> segments(lbm_ctx* c) {
+    std::vector<Segment> s;
+    s.push_back({c->h[c->cur], h_elem(c->form), h_planes(c->form, c->q)});
+    if (conservative(c->form)) s.push_back({c->h0[c->cur], 8, 1});
+    s.push_back({c->g[c->cur], g_elem(c->form), c->q});
+    s.push_back({c->phiu, a_elem(c->form), c->d3 ? 3 : 2});
+    s.push_back({c->p[c->cur], a_elem(c->form), 1});
+    return s;
+}
+
+// Rows [y0, y0 + nrows) of every state plane of an instance to or from a packed
+// device buffer: one 2-D copy per storage segment (pitch = the plane stride).
+lbm_status copy_rows(lbm_ctx* c, int instance, int y0, int nrows, void* buf, size_t bytes, bool pack) {
+    lbm_status st = check_instance(c, instance);
+    if (st != LBM_OK) return st;
+    if (!buf) return fail(c, LBM_EINVAL, "row buffer is NULL");
+    if (c->d3) return fail(c, LBM_EINVAL, "row exchange serves D2Q9 contexts");
+    const lbm_params& p = c->params[instance];
+    if (nrows < 1 || y0 < 0 || y0 + nrows > p.ny) return fail(c, LBM_EINVAL, "rows outside the instance");
+    if (bytes < (size_t)nrows * lbm_row_bytes(c, instance)) return fail(c, LBM_EINVAL, "row buffer too small");
+    LBM_CK(c, cudaSetDevice(c->device));
+    const size_t cell0 = (size_t)c->inst[instance].base + (size_t)y0 * p.nx;
+    const size_t cells = (size_t)nrows * p.nx;
+    unsigned char* b = static_cast<unsigned char*>(buf);
+    for (const Segment& sg : segments(c)) {
+        unsigned char* plane0 = static_cast<unsigned char*>(sg.dev) + cell0 * sg.elem;
+        const size_t width = cells * sg.elem, pitch = (size_t)c->S * sg.elem;
+        cudaError_t e = pack ? cudaMemcpy2DAsync(b, width, plane0, pitch, width, sg.planes, cudaMemcpyDeviceToDevice,
+                                                 c->stream)
+                             : cudaMemcpy2DAsync(plane0, pitch, b, width, width, sg.planes, cudaMemcpyDeviceToDevice,
+                                                 c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, pack ? "row pack" : "row unpack");
+        b += width * sg.planes;
+    }
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t lbm_row_bytes(const lbm_ctx* c, int instance) {
+    if (!c || instance < 0 || instance >= c->n || c->d3) return 0;
+    size_t per_cell = 0;
+    for (const Segment& sg : segments(const_cast<lbm_ctx*>(c))) per_cell += sg.elem * sg.planes;
+    return per_cell * (size_t)c->params[instance].nx;
+}
+
+lbm_status lbm_pack_rows(lbm_ctx* c, int instance, int y0, int nrows, void* dev_buf, size_t bytes) {
+    if (!c) return LBM_EINVAL;
+    return copy_rows(c, instance, y0, nrows, dev_buf, bytes, true);
+}
+
+lbm_status lbm_unpack_rows(lbm_ctx* c, int instance, int y0, int nrows, const void* dev_buf, size_t bytes) {
+    if (!c) return LBM_EINVAL;
+    return copy_rows(c, instance, y0, nrows, const_cast<void*>(dev_buf), bytes, false);
+}
+
 lbm_status lbm_get_populations(lbm_ctx* c, int instance, double* host_h, double* host_g) {
     lbm_status st = check_instance(c, instance);
     if (st != LBM_OK) return st;
@@ -1063,18 +1204,6 @@ lbm_status lbm_get_populations(lbm_ctx* c, int instance, double* host_h, double*
 // ---- checkpoints --------------------------------------------------------
 namespace {
 const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
-
-struct Segment { void* dev; size_t elem; int planes; };
-
-std::vector<Segment> segments(lbm_ctx* c) {
-    std::vector<Segment> s;
-    s.push_back({c->h[c->cur], h_elem(c->form), h_planes(c->form, c->q)});
-    if (conservative(c->form)) s.push_back({c->h0[c->cur], 8, 1});
-    s.push_back({c->g[c->cur], g_elem(c->form), c->q});
-    s.push_back({c->phiu, a_elem(c->form), c->d3 ? 3 : 2});
-    s.push_back({c->p[c->cur], a_elem(c->form), 1});
-    return s;
-}
 
 bool little_endian() {
     const uint32_t one = 1;
@@ -1177,78 +1306,186 @@ lbm_status lbm_set_launch(lbm_ctx* c, int tile_x, int rows) {
     return LBM_OK;
 }
 
-lbm_status lbm_autotune(lbm_ctx* c, int* best_tile_x, int* best_rows) {
+namespace {
+// Tuned launch shapes, per device, storage form and instance-size signature
+// (the list of nx, ny, nz, walls of the context's instances), for the life of
+// the process: a second context of the same shape takes the shape without trials.
+std::mutex g_tune_mutex;
+std::map<std::string, lbm_launch_shape> g_tune_cache;
+
+std::string tune_key(const lbm_ctx* c) {
+    std::string k = std::to_string(c->device) + "/" + std::to_string(c->form) + "/";
+    for (const lbm_params& p : c->params)
+        k += std::to_string(p.nx) + "x" + std::to_string(p.ny) + "x" + std::to_string(p.nz) +
+             (p.bc_y == LBM_BC_BOUNCEBACK ? "w," : "p,");
+    return k;
+}
+
+// What one configuration launches: the launch classes (strip width, blocks,
+// load path) and the work items; two configurations with the same plan need
+// only one trial.
+std::string plan_signature(const lbm_ctx* c) {
+    std::string sig;
+    for (const auto& L : c->launches)
+        sig += std::to_string(L.tx) + ":" + std::to_string(L.count) + ":" + std::to_string(L.variant) + ";";
+    for (const WorkItem& w : c->work) sig += std::to_string(w.nrows) + ",";
+    return sig;
+}
+}  // namespace
+
+lbm_status lbm_autotune_shape(lbm_ctx* c, int flags, lbm_launch_shape* out) {
     if (!c) return LBM_EINVAL;
     if (c->d3) return fail(c, LBM_EINVAL, "D3Q15 contexts have no launch shape to tune");
+    if (flags & ~LBM_TUNE_NO_CACHE) return fail(c, LBM_EINVAL, "unknown autotune flags");
     for (int k = 0; k < c->n; ++k)
         if (!c->ready[k]) return fail(c, LBM_ESTATE, "instance not initialised");
     LBM_CK(c, cudaSetDevice(c->device));
+    lbm_status st = sticky(c);
+    if (st != LBM_OK) return st;
+    const std::string key = tune_key(c);
+    if (!(flags & LBM_TUNE_NO_CACHE)) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            lbm_launch_shape r = it->second;
+            r.trials = 0;
+            c->pipeline = r.pipeline;
+            c->tile_req = r.tile_x;
+            c->rows_req = r.rows;
+            c->plan_dirty = true;
+            if (out) *out = r;
+            return LBM_OK;
+        }
+    }
     LBM_CK(c, cudaStreamSynchronize(c->stream));
     // Save the state (current buffers) so the trial steps leave no trace.
     std::vector<Segment> segs = segments(c);
     std::vector<void*> saved;
-    for (const Segment& s : segs) {
+    for (const Segment& sg : segs) {
         void* b = nullptr;
-        const size_t bytes = (size_t)s.planes * c->S * s.elem;
+        const size_t bytes = (size_t)sg.planes * c->S * sg.elem;
         cudaError_t e = cudaMalloc(&b, bytes);
         if (e != cudaSuccess) {
             for (void* q : saved) cudaFree(q);
             return cuda_fail(c, e, "autotune backup");
         }
-        cudaMemcpyAsync(b, s.dev, bytes, cudaMemcpyDeviceToDevice, c->stream);
         saved.push_back(b);
+        e = cudaMemcpyAsync(b, sg.dev, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) {
+            for (void* q : saved) cudaFree(q);
+            return cuda_fail(c, e, "autotune backup");
+        }
     }
     const int cur0 = c->cur;
     const std::vector<int64_t> time0 = c->time;
-    const int tiles[3] = {64, 128, 256};
-    const int rows_c[5] = {0, 8, 16, 32, 64};
-    float best = 1e30f;
-    int bt = c->tile_req, br = c->rows_req;
-    cudaEvent_t e0, e1;
+    const std::vector<int64_t> mon_time0 = c->mon_time;
+    const int64_t steps0 = c->steps_total;
+    const bool monitor0 = c->monitor;
+    const int pipe0 = c->pipeline, tile0 = c->tile_req, rows0 = c->rows_req;
+    c->monitor = false;
+    // Candidates: load path (two cells a thread in packed FP32, the batched
+    // launch, one cell a thread with plain, cp.async or TMA loads), strip width,
+    // run length; the built-in plan (AUTO, 0, 0) first.
+    struct Cand { int pipe, tile, rows; };
+    std::vector<Cand> cands{{LBM_PIPELINE_AUTO, 0, 0}};
+    const int pipes[] = {LBM_PIPELINE_PAIRS, LBM_PIPELINE_BATCHED, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC,
+                         LBM_PIPELINE_TMA};
+    const int tiles[] = {0, 64, 128, 256};
+    const int rows_c[] = {0, 8, 16, 32, 64};
+    for (int pp : pipes)
+        for (int tx : tiles)
+            for (int r : rows_c) cands.push_back({pp, pp == LBM_PIPELINE_BATCHED ? 0 : tx, r});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    lbm_status st = LBM_OK;
-    for (int tx : tiles) {
-        bool fits = false;
-        for (const auto& p : c->params) fits = fits || p.nx >= tx / 2;
-        if (!fits) continue;
-        for (int r : rows_c) {
-            c->tile_req = tx;
-            c->rows_req = r;
-            c->plan_dirty = true;
-            if ((st = lbm_step(c, 2)) != LBM_OK) break;   // warm-up
+    std::vector<std::string> seen;
+    float best = 1e30f, deflt = 0.f;
+    Cand bc = cands[0];
+    int trials = 0;
+    for (const Cand& cd : cands) {
+        c->pipeline = cd.pipe;
+        c->tile_req = cd.tile;
+        c->rows_req = cd.rows;
+        c->plan_dirty = true;
+        if ((st = plan(c)) != LBM_OK) break;
+        const std::string sig = plan_signature(c);
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+        seen.push_back(sig);
+        ++trials;
+        // warm-up (captures the graph of this plan), then the best of two timings
+        if ((st = lbm_step(c, 2)) != LBM_OK) break;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {
             cudaEventRecord(e0, c->stream);
-            if ((st = lbm_step(c, 6)) != LBM_OK) break;
+            st = lbm_step(c, 8);
             cudaEventRecord(e1, c->stream);
             cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                bt = tx;
-                br = r;
-            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t / 8.f);
         }
         if (st != LBM_OK) break;
+        if (trials == 1) deflt = ms;
+        if (ms < best) {
+            best = ms;
+            bc = cd;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // Restore the state, the clocks and the monitor exactly as they were.
     c->cur = cur0;
     segs = segments(c);
-    for (size_t k = 0; k < segs.size(); ++k) {
+    for (size_t k = 0; k < segs.size(); ++k)
         cudaMemcpyAsync(segs[k].dev, saved[k], (size_t)segs[k].planes * c->S * segs[k].elem,
                         cudaMemcpyDeviceToDevice, c->stream);
-    }
-    cudaStreamSynchronize(c->stream);
+    cudaError_t se = cudaStreamSynchronize(c->stream);
     for (void* q : saved) cudaFree(q);
     c->time = time0;
-    if (st != LBM_OK) return st;
-    c->tile_req = bt;
-    c->rows_req = br;
+    c->mon_time = mon_time0;
+    c->monitor = monitor0;
+    if (st == LBM_OK && se != cudaSuccess) st = cuda_fail(c, se, "autotune restore");
+    if (c->steps_total != steps0) {   // the device time base counts from steps_total
+        std::vector<int64_t> base(c->n);
+        for (int k = 0; k < c->n; ++k) base[k] = c->time[k] - steps0;
+        c->steps_total = steps0;
+        if (cudaMemcpy(c->d_time_base, base.data(), c->n * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess &&
+            st == LBM_OK)
+            st = fail(c, LBM_ECUDA, "autotune: time base restore");
+    }
+    if (st != LBM_OK) {
+        c->pipeline = pipe0;
+        c->tile_req = tile0;
+        c->rows_req = rows0;
+        c->plan_dirty = true;
+        return st;
+    }
+    c->pipeline = bc.pipe;
+    c->tile_req = bc.tile;
+    c->rows_req = bc.rows;
     c->plan_dirty = true;
-    if (best_tile_x) *best_tile_x = bt;
-    if (best_rows) *best_rows = br;
+    lbm_launch_shape r;
+    r.pipeline = bc.pipe;
+    r.tile_x = bc.tile;
+    r.rows = bc.rows;
+    r.trials = trials;
+    r.ms_per_step = best;
+    r.default_ms_per_step = deflt;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = r;
+    }
+    if (out) *out = r;
     return sticky(c);
+}
+
+lbm_status lbm_autotune(lbm_ctx* c, int* best_tile_x, int* best_rows) {
+    lbm_launch_shape r;
+    lbm_status st = lbm_autotune_shape(c, LBM_TUNE_NO_CACHE, &r);
+    if (st != LBM_OK) return st;
+    if (best_tile_x) *best_tile_x = r.tile_x;
+    if (best_rows) *best_rows = r.rows;
+    return LBM_OK;
 }
 
 int lbm_launches_per_step(const lbm_ctx* c) {
@@ -1302,7 +1539,7 @@ lbm_status lbm_sync(lbm_ctx* c) {
 
 lbm_status lbm_set_pipeline(lbm_ctx* c, int mode) {
     if (!c) return LBM_EINVAL;
-    if (mode < LBM_PIPELINE_AUTO || mode > LBM_PIPELINE_PAIRS)
+    if (mode < LBM_PIPELINE_AUTO || mode > LBM_PIPELINE_BATCHED)
         return fail(c, LBM_EINVAL, "pipeline mode must be one of LBM_PIPELINE_*");
     c->pipeline = mode;
     c->plan_dirty = true;

@@ -295,7 +295,12 @@ struct Macro {
     V rho, ux, uy, Fx, Fy, Ftx, Fty, S, S1, tgm /* tau_g - 1/2 */, inv_tau_g, p;
 };
 
-template <typename V, typename S>
+// GSC: the g values come in multiplied by the FP16 storage scale gs of the
+// instance (as they are stored). gs is a power of two, and multiplying by a power
+// of two commutes exactly with every rounded operation (no value here comes near
+// the FP32 overflow or subnormal range), so un-scaling the three sums that use g
+// (j_x, j_y, the sum of Eq. 28) gives bit for bit what un-scaling every g_i would.
+template <bool GSC = false, typename V, typename S>
 __device__ __forceinline__ Macro<V> macroscopic(const Consts<S>& C, const V g[9], V phi, V mu,
                                                 V gphix, V gphiy, V gmux, V gmuy, V lapmu,
                                                 V gpx, V gpy) {
@@ -308,8 +313,12 @@ __device__ __forceinline__ Macro<V> macroscopic(const Consts<S>& C, const V g[9]
     else { Fsx = -(phi * gmux); Fsy = -(phi * gmuy); }
     m.Fx = Fsx + V(C.force_x);
     m.Fy = fmadd(m.rho - V(C.rho_A), V(-C.gravity), Fsy + V(C.force_y));   // buoyancy, Sec. 4.4
-    const V jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const V jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    V jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    V jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    if constexpr (GSC) {
+        jx = jx * V(C.igs);
+        jy = jy * V(C.igs);
+    }
     const V inv_rho = rcp(m.rho);
     m.ux = fmadd(V(S(0.5)), m.Fx, jx) * inv_rho;      // Eq. 27a
     m.uy = fmadd(V(S(0.5)), m.Fy, jy) * inv_rho;
@@ -335,7 +344,8 @@ __device__ __forceinline__ Macro<V> macroscopic(const Consts<S>& C, const V g[9]
         const V uFt = fmadd(m.ux, m.Ftx, m.uy * m.Fty);
         G0 = V(w0) * (fmadd(V(S(-3)), uFt, m.S) - m.rho * m.S1);
     }
-    const V sum_g = (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+    V sum_g = (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+    if constexpr (GSC) sum_g = sum_g * V(C.igs);
     const V uu = fmadd(m.ux, m.ux, m.uy * m.uy);
     // Eq. 28 (Eq. 29 for the previous scheme): c_s^2 / (1 - w0) = 3/5, s_0 = -1.5 w0 u.u
     m.p = V(S(0.6)) * fmadd(m.tgm, G0, fmadd(m.rho * V(S(-1.5) * w0), uu, fmadd(V(S(0.5)), m.S, sum_g)));
@@ -353,26 +363,43 @@ __device__ __forceinline__ Macro<V> macroscopic(const Consts<S>& C, const V g[9]
 // The collision written once, handing each result to emit(i, g*_i, h*_i) as soon
 // as its pair of directions is formed (rest direction first), so callers that
 // store right away keep few values alive.
-template <typename V, typename S, typename Emit>
+// GSC / HSC: g / h come in and go out in the units they are stored in, i.e.
+// multiplied by the FP16 storage scale gs / hs (powers of two). The scale is
+// folded into per-cell factors (the relaxation weights of g; eta mu, phi u and
+// the R_i constant of h), which gives bit for bit the scaled result of the
+// unscaled arithmetic (see macroscopic) at a few multiplies a cell instead of
+// two per stored value.
+template <bool GSC = false, bool HSC = false, typename V, typename S, typename Emit>
 __device__ __forceinline__ void collide_emit(const Consts<S>& C, const Macro<V>& m, V phi, V mu,
                                              V ddx, V ddy, const V g[9], const V h[9], Emit&& emit) {
+    auto hsc = [&](S k) {   // a constant of the h update in the units h is stored in
+        if constexpr (HSC) return k * C.hs;
+        else return k;
+    };
     const V uu = fmadd(m.ux, m.ux, m.uy * m.uy);
     const V uFt = fmadd(m.ux, m.Ftx, m.uy * m.Fty);
     const V om = m.inv_tau_g, om1 = V(S(1)) - om;
     const V gsrc = fmadd(V(S(-0.5)), om, V(S(1)));
+    V omg = om, gsrcg = gsrc;   // weights of g^eq and G_i in the units g is stored in
+    if constexpr (GSC) {
+        omg = om * V(C.gs);
+        gsrcg = gsrc * V(C.gs);
+    }
     const V omh = V(C.inv_tau_h), omh1 = V(S(1) - C.inv_tau_h);
     const V p3 = V(S(3)) * m.p;
     const V rS1 = m.rho * m.S1;
-    const V etamu = V(C.eta) * mu;
-    const V phiux = phi * m.ux, phiuy = phi * m.uy;
+    const V etamu = V(hsc(C.eta)) * mu;
+    V phih = phi;
+    if constexpr (HSC) phih = phi * V(C.hs);
+    const V phiux = phih * m.ux, phiuy = phih * m.uy;
     const V uu15 = V(S(-1.5)) * uu;
     // rest direction (c = 0): G_0 = w0 (S - 3 u.F~ - rho S1), R_0 = 0
     {
         const S w0 = w_of<S>(0);
         const V geq = fmadd(V(w0 - S(1)), p3, m.rho * (V(w0) * uu15));
         const V G = V(w0) * (fmadd(V(S(-3)), uFt, m.S) - rS1);
-        const V heq = fmadd(V(w0 - S(1)), etamu, phi);
-        emit(0, fmadd(om1, g[0], fmadd(om, geq, gsrc * G)), fmadd(omh1, h[0], omh * heq));
+        const V heq = fmadd(V(w0 - S(1)), etamu, phih);
+        emit(0, fmadd(om1, g[0], fmadd(omg, geq, gsrcg * G)), fmadd(omh1, h[0], omh * heq));
     }
 #pragma unroll
     for (int i = 1; i <= 6; ++i) {
@@ -391,10 +418,10 @@ __device__ __forceinline__ void collide_emit(const Consts<S>& C, const Macro<V>&
         const V G_o = V(S(3) * w) * cF;
         const V heq_e = V(w) * etamu;
         const V heq_o = V(S(3) * w) * cdot(cx, cy, phiux, phiuy);
-        const V R_o = V(C.src_h * S(3) * w) * cdot(cx, cy, ddx, ddy);
-        emit(i, fmadd(om1, g[i], fmadd(om, geq_e + geq_o, gsrc * (G_e + G_o))),
+        const V R_o = V(hsc(C.src_h * S(3) * w)) * cdot(cx, cy, ddx, ddy);
+        emit(i, fmadd(om1, g[i], fmadd(omg, geq_e + geq_o, gsrcg * (G_e + G_o))),
              fmadd(omh1, h[i], fmadd(omh, heq_e + heq_o, R_o)));
-        emit(j, fmadd(om1, g[j], fmadd(om, geq_e - geq_o, gsrc * (G_e - G_o))),
+        emit(j, fmadd(om1, g[j], fmadd(omg, geq_e - geq_o, gsrcg * (G_e - G_o))),
              fmadd(omh1, h[j], fmadd(omh, heq_e - heq_o, -R_o)));
     }
 }
@@ -473,13 +500,33 @@ template <> struct MonAcc<float> {
 };
 
 // Block reduction of the monitor sums; thread 0 writes {sum phi, kinetic
-// energy, max |u|^2, non-finite flag} to out. Every thread of the block calls it.
+// energy, max |u|^2, non-finite flag} to this block's slot a.mon[blockIdx.x].
+// The last block of instance `inst` to get here (arrival counter) then adds the
+// slots of all of that instance's blocks in work-list order -- thread t takes
+// items t, t + blockDim, ..., then a fixed shuffle / shared-memory tree, so the
+// sums do not depend on which block came last -- and writes the instance's
+// record: max |u|^2 becomes max |u|, plus the non-finite flag, the status word
+// and the time level. No second launch. Every thread of the block calls it.
+//
+// The group of threads doing this is a whole block (bar 0, grp 0) or one of the
+// thread groups of the batched kernel (named barrier `bar`, group `grp` < 4,
+// nthr threads, tid its index in the group); item is the work item whose slot
+// the group writes.
+__device__ __forceinline__ void group_sync(int bar, int nthr) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+}
+
 template <typename R>
-__device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, double* out) {
-    __shared__ double red[3][32];
+__device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const StepArgs& a, int inst, int item,
+                                                int tid, int nthr, int bar, int grp) {
+    __shared__ double red_all[4][4][8];   // [group][quantity][warp]: up to 8 warps a group
+    __shared__ int last_all[4];
+    double (*red)[8] = red_all[grp];
+    int& is_last = last_all[grp];
     double v[3];
     acc.result(v[0], v[1], v[2]);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = nthr >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
@@ -487,14 +534,56 @@ __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, double* ou
         v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
     }
     if (lane == 0) { red[0][warp] = v[0]; red[1][warp] = v[1]; red[2][warp] = v[2]; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    group_sync(bar, nthr);
+    const int* idx = a.mon_csr + a.mon_n + 1;
+    const int first = a.mon_csr[inst], items = a.mon_csr[inst + 1] - first;
+    if (tid == 0) {
         double m = red[0][0], k = red[1][0], u = red[2][0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { m += red[0][w]; k += red[1][w]; u = fmax(u, red[2][w]); }
+        for (int w = 1; w < nwarps; ++w) { m += red[0][w]; k += red[1][w]; u = fmax(u, red[2][w]); }
+        double* out = a.mon + (long long)item * kMonQ;
         out[0] = m;
         out[1] = k;
         out[2] = u;
         out[3] = (isfinite(m) && isfinite(k)) ? 0.0 : 1.0;
+        __threadfence();                                  // the slot before the count
+        is_last = atomicAdd(a.mon_count + inst, 1) == items - 1;
+    }
+    group_sync(bar, nthr);
+    if (!is_last) return;
+    __threadfence();                                      // the count before the slots
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < items; j += nthr) {
+        const double* p = a.mon_all + (long long)idx[first + j] * kMonQ;
+        s[0] += __ldcg(p);
+        s[1] += __ldcg(p + 1);
+        s[2] = fmax(s[2], __ldcg(p + 2));
+        s[3] += __ldcg(p + 3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s[0] += __shfl_down_sync(0xffffffffu, s[0], o);
+        s[1] += __shfl_down_sync(0xffffffffu, s[1], o);
+        s[2] = fmax(s[2], __shfl_down_sync(0xffffffffu, s[2], o));
+        s[3] += __shfl_down_sync(0xffffffffu, s[3], o);
+    }
+    group_sync(bar, nthr);                                // red[] is reused
+    if (lane == 0) { red[0][warp] = s[0]; red[1][warp] = s[1]; red[2][warp] = s[2]; red[3][warp] = s[3]; }
+    group_sync(bar, nthr);
+    if (tid == 0) {
+        for (int w = 1; w < nwarps; ++w) {
+            s[0] += red[0][w];
+            s[1] += red[1][w];
+            s[2] = fmax(s[2], red[2][w]);
+            s[3] += red[3][w];
+        }
+        MonRecord& r = a.mon_rec[inst];
+        r.sum_phi = s[0];
+        r.kinetic_energy = s[1];
+        r.max_u = sqrt(s[2]);
+        r.nonfinite = s[3] != 0.0 ? 1 : 0;
+        r.device_status = *(volatile int*)a.status;
+        r.time = a.mon_step + a.time_base[inst];
+        a.mon_count[inst] = 0;                            // ready for the next monitored step
     }
 }
 
@@ -832,7 +921,7 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
         __syncthreads();
         collide_row(Y, g, pux, puy);
     }
-    if constexpr (MON) mon_block_store(mon, a.mon + (long long)blockIdx.x * kMonQ);
+    if constexpr (MON) mon_block_store(mon, a, wk.inst, blockIdx.x, threadIdx.x, TX, 0, 0);
 }
 
 }  // namespace lbm

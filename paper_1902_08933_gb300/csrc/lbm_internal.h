@@ -36,6 +36,13 @@ struct WorkItem {
     int inst, x0, ystart, nrows, dir, pad;
 };
 
+// A block's share of the batched step (step_kernel_x2_batched): two work items
+// (strips of up to 128 columns) that two groups of 64 threads march side by
+// side; an unused entry is -1.
+struct BlockDesc {
+    int item[2];
+};
+
 // Device buffers of one step (ping-pong: *_in is time t, *_out time t + 1).
 struct StepArgs {
     const void* h_in;  void* h_out;     // 9 planes (h_1..h_8 only for conservative forms)
@@ -48,6 +55,29 @@ struct StepArgs {
     const WorkItem* work;
     int* status;                        // device status word (0 = ok), see kStatusTimeout
     double* mon;                        // monitor: kMonQ doubles per block of this launch
+    // Per-step monitor, final reduction (kernels with the monitor only): after
+    // storing its slot a block counts itself in mon_count[instance]; the last
+    // block of an instance adds that instance's slots in work-list order and
+    // writes its record, then sets the counter back to zero.
+    double* mon_all;                    // slots of every work item of the plan
+    int* mon_count;                     // per instance: blocks of this step done
+    const int* mon_csr;                 // per instance k: items idx[csr[k] .. csr[k+1]) (idx at csr + n + 1)
+    int mon_n;                          // instances
+    struct MonRecord* mon_rec;          // one record per instance
+    const int64_t* time_base;           // per instance: time level - steps of the context
+    long long mon_step;                 // steps of the context before the monitored step
+    // batched step only: block descriptors, their number, and the queue
+    // counters {next descriptor, blocks finished} (zero between steps)
+    const BlockDesc* desc;
+    int ndesc;
+    int* queue;
+};
+
+// Device layout of lbm_monitor (include/lbm.h; the host checks size and offsets).
+struct MonRecord {
+    double sum_phi, kinetic_energy, max_u;
+    int32_t nonfinite, device_status;
+    int64_t time;
 };
 
 // Doubles a block of a monitored step writes: sum phi, kinetic energy,
@@ -79,11 +109,14 @@ constexpr int kDiagBlocks = 304;      // 2 x 152 SMs
 // Step kernel variants: synchronous loads; per-thread cp.async prefetch (FP32
 // storage of h and p); bulk copies by the TMA (FP32 arithmetic, 16-byte rows);
 // two cells per thread in packed FP32 (FP32 arithmetic, nx even, tile >= 64).
-enum StepVariant { kPlain = 0, kAsync = 1, kTma = 2, kPairs = 3 };
+// kBatched: the pairs kernel over every instance in one persistent launch
+// (block descriptors of two 128-column strips).
+enum StepVariant { kPlain = 0, kAsync = 1, kTma = 2, kPairs = 3, kBatched = 4 };
 template <int FORM> cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s,
                                               int variant, bool monitor);
 template <int FORM> cudaError_t prepare_step_t();          // opt-in shared memory sizes
 template <int FORM> size_t step_smem_t(int tile_x);
+template <int FORM> int batched_occupancy_t();             // resident blocks per SM, batched kernel
 template <int FORM> int step_occupancy_t(int tile_x, int variant);   // resident blocks per SM
 template <int FORM> bool has_tma_t();                      // the form has a TMA-fed kernel
 template <int FORM> bool has_async_t();                    // the form has the cp.async kernel

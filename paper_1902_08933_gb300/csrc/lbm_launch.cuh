@@ -60,6 +60,14 @@ cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t
     if (nwork <= 0) return cudaSuccess;
     if (monitor && a.mon == nullptr) return cudaErrorInvalidValue;
     if constexpr (kHasTma<FORM>) {
+        if (variant == kBatched) {   // nwork = blocks of the persistent grid
+            if (a.desc == nullptr || a.queue == nullptr) return cudaErrorInvalidValue;
+            if (monitor)
+                step_kernel_x2_batched<FORM, true><<<nwork, 128, X2Batched<FORM>::bytes, s>>>(a);
+            else
+                step_kernel_x2_batched<FORM><<<nwork, 128, X2Batched<FORM>::bytes, s>>>(a);
+            return cudaGetLastError();
+        }
         if (variant == kPairs) {
             switch (tile_x) {
                 case 64: return launch_pairs_tx<FORM, 32>(a, nwork, s, monitor);
@@ -113,7 +121,26 @@ cudaError_t prepare_step_t() {
     if ((e = prep_tx<FORM, 32>()) != cudaSuccess) return e;
     if ((e = prep_tx<FORM, 64>()) != cudaSuccess) return e;
     if ((e = prep_tx<FORM, 128>()) != cudaSuccess) return e;
-    return prep_tx<FORM, 256>();
+    if ((e = prep_tx<FORM, 256>()) != cudaSuccess) return e;
+    if constexpr (kHasTma<FORM>) {
+        e = cudaFuncSetAttribute(step_kernel_x2_batched<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)X2Batched<FORM>::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel_x2_batched<FORM, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X2Batched<FORM>::bytes);
+    }
+    return e;
+}
+
+template <int FORM>
+int batched_occupancy_t() {
+    if constexpr (kHasTma<FORM>) {
+        int n = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_x2_batched<FORM>, 128,
+                                                                      X2Batched<FORM>::bytes);
+        return e == cudaSuccess ? n : 0;
+    }
+    return 0;
 }
 
 template <int FORM>
@@ -213,6 +240,7 @@ cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h, do
     template cudaError_t launch_step_t<F>(int, const StepArgs&, int, cudaStream_t, int, bool); \
     template cudaError_t prepare_step_t<F>();                                                 \
     template size_t step_smem_t<F>(int);                                                      \
+    template int batched_occupancy_t<F>();                                                    \
     template int step_occupancy_t<F>(int, int);                                               \
     template bool has_tma_t<F>();                                                             \
     template bool has_async_t<F>();                                                           \

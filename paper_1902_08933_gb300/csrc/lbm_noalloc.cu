@@ -23,10 +23,10 @@ constexpr int kMaxBlocks = 2048;                     // blocks the scratch array
 constexpr long long kMaxCells = (long long)kCellsPerBlock * kMaxBlocks;   // 16,777,216
 constexpr int kQ = lbm::kDiagQuantities;
 
-// Per-block partial sums of the last call (2048 x 14 doubles = 229 KB per GPU).
-// Every call overwrites the slots of the blocks it launches before reading them,
-// so nothing needs clearing; two calls in flight at once on the GPU share this
-// array and race.
+// Per-block partial sums of the last call (2048 x 14 doubles = 229 KB per GPU;
+// each device holds its own copy). Every call overwrites the slots of the blocks
+// it launches before reading them, so nothing needs clearing; two calls in
+// flight at once on the same device share this array and race.
 static __device__ __align__(256) double g_partials[kMaxBlocks * kQ];
 
 constexpr int kMaxDevices = 64;
@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(kFinalThreads) reduce_fields_final(const doubl
     }
 }
 
-// Device address of g_partials on the current device, looked up once per device.
+// Device address of g_partials on the current device, looked up once per device
+// and kept for the life of the process (a cudaDeviceReset after the first call
+// would leave it stale; the header says so).
 cudaError_t scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

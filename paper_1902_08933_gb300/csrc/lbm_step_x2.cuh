@@ -34,9 +34,22 @@ __device__ __forceinline__ void st_pair(float* p, F2 v) { *reinterpret_cast<floa
 __device__ __forceinline__ void st_pair(__half* p, F2 v) {
     *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
 }
-__device__ __forceinline__ void st_one(float* p, float v) { *p = v; }
-__device__ __forceinline__ void st_one(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ F2 lds_pair(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
+// The two cells' results in the storage type of a plane (FP16: one packed
+// conversion for both), then stored as a pair or one cell at a time.
+__device__ __forceinline__ float2 to_store(F2 v, const float*) { return v.v; }
+__device__ __forceinline__ __half2 to_store(F2 v, const __half*) { return __float22half2_rn(v.v); }
+__device__ __forceinline__ void st_both(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+__device__ __forceinline__ void st_both(__half* p, __half2 v) { *reinterpret_cast<__half2*>(p) = v; }
+__device__ __forceinline__ void st_first(float* p, float2 v) { *p = v.x; }
+__device__ __forceinline__ void st_first(__half* p, __half2 v) { *p = __low2half(v); }
+__device__ __forceinline__ void st_second(float* p, float2 v) { *p = v.y; }
+__device__ __forceinline__ void st_second(__half* p, __half2 v) { *p = __high2half(v); }
+// the stored values read back as FP32 (exact)
+__device__ __forceinline__ float first_f(float2 v) { return v.x; }
+__device__ __forceinline__ float first_f(__half2 v) { return __low2float(v); }
+__device__ __forceinline__ float second_f(float2 v) { return v.y; }
+__device__ __forceinline__ float second_f(__half2 v) { return __high2float(v); }
 
 template <int FORM, int TX>
 struct X2Smem {
@@ -65,27 +78,32 @@ struct X2Occ {
     static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
 };
 
-template <int FORM, int TX, bool MON = false>
-__global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(const StepArgs a) {
+// One work item (a strip of 2 TX columns of one instance, a run of rows) marched
+// by a group of TX threads: a whole thread block (step_kernel_x2: barrier 0, the
+// one __syncthreads uses) or one of the thread groups of the batched kernel
+// (step_kernel_x2_batched: named barrier 1 + group). smem_raw is the group's own
+// X2Smem<FORM, TX> region, tid the thread's index in the group, item the work
+// item's index in StepArgs::work (and of its monitor slot).
+template <int FORM, int TX, bool MON>
+__device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned char* smem_raw, int tid,
+                                        int bar, int grp) {
     using F = Form<FORM>;
     using HT = typename F::HT;
     using GT = typename F::GT;
     using L = X2Smem<FORM, TX>;
     static_assert(sizeof(typename F::R) == 4, "the paired kernel serves the FP32-arithmetic forms");
     constexpr int SW = L::SW, RW = L::RW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     float* phiR = reinterpret_cast<float*>(smem_raw);   // [8][RW]
     float* muR = phiR + 8 * RW;                          // [4][RW]
     float* pR = muR + 4 * RW;                            // [4][RW]
     unsigned char* hR = smem_raw + L::RINGS;             // [4] slots of L::SLOT bytes
 
-    const WorkItem wk = a.work[blockIdx.x];
+    const WorkItem wk = a.work[item];
     Consts<float> C;
     C.load(a.inst[wk.inst]);
     const int nx = C.nx, ny = C.ny, walls = C.walls;
     const int x0 = wk.x0, d = wk.dir;
     const int w = min(SW, nx - x0);
-    const int tid = threadIdx.x;
     const int base = (int)C.base;
     const long long S = a.S;
     const HT* hin = static_cast<const HT*>(a.h_in);
@@ -97,7 +115,10 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
     const float* p_in = static_cast<const float*>(a.p_in);
     float* p_out = static_cast<float*>(a.p_out);
     float* phiu = static_cast<float*>(a.phiu);
-    const float hs = C.hs, ihs = C.ihs, gs = C.gs, igs = C.igs;
+    // FP16 planes hold their values times a power-of-two scale (hs, gs); the
+    // arithmetic keeps h and g in those units (collide_emit / macroscopic with
+    // their scale flags), so only the sum of h that forms phi is un-scaled.
+    const float ihs = C.ihs;
     MonAcc<float> mon;
 
     auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
@@ -114,26 +135,11 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
         return reinterpret_cast<HT*>(hslot(y) + L::H0B + (F::cons ? i - 1 : i) * L::HPB);
     };
     auto hpairs = [&](int y) { return reinterpret_cast<float2*>(hslot(y)); };   // conservative h_0
-    // stored pair -> arithmetic values
-    auto cvt_h = [&](F2 v) { return F::h16 ? v * ihs : v; };
-
-    // population i >= 1 (all i for non-conservative forms) of the cell pair at c
-    auto ld_h = [&](int i, int c) -> F2 {
-        const F2 v = ld_pair(hin + (long long)(F::cons ? i - 1 : i) * S + c);
-        return F::h16 ? v * ihs : v;
-    };
-    auto ld_g = [&](int i, int c) -> F2 {
-        const F2 v = ld_pair(gin + (long long)i * S + c);
-        return F::g16 ? v * igs : v;
-    };
-    auto st_h1 = [&](int k, int c, float v) {
-        st_one(hout + (long long)(F::cons ? k - 1 : k) * S + c, F::h16 ? v * hs : v);
-    };
-    auto st_h2 = [&](int k, int c, F2 v) {
-        st_pair(hout + (long long)(F::cons ? k - 1 : k) * S + c, F::h16 ? v * hs : v);
-    };
-    auto st_g1 = [&](int k, int c, float v) { st_one(gout + (long long)k * S + c, F::g16 ? v * gs : v); };
-    auto st_g2 = [&](int k, int c, F2 v) { st_pair(gout + (long long)k * S + c, F::g16 ? v * gs : v); };
+    // population i of the cell pair at c as stored (FP16: still scaled by gs)
+    auto ld_g = [&](int i, int c) -> F2 { return ld_pair(gin + (long long)i * S + c); };
+    // output planes: h_k (k >= 1 for conservative forms), g_k
+    auto hplane_out = [&](int k) { return hout + (long long)(F::cons ? k - 1 : k) * S; };
+    auto gplane_out = [&](int k) { return gout + (long long)k * S; };
 
     // Column pairs of the lead / p rows: pair q covers x0-2+2q, x0-1+2q (ring index 2+2q).
     const int nq = (w + 4) >> 1;
@@ -153,7 +159,8 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
         if constexpr (F::cons) {
             F2 s8 = F2(0.f);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) s8 = s8 + cvt_h(ld_pair(hplane(Lr, i) + j));
+            for (int i = 1; i < 9; ++i) s8 = s8 + ld_pair(hplane(Lr, i) + j);
+            if constexpr (F::h16) s8 = s8 * ihs;   // exact: ihs is a power of two
             float4* h0p = reinterpret_cast<float4*>(&hpairs(Lr)[j]);
             const float4 h0 = *h0p;                                     // (hi, lo) of both cells
             float sa, ea, ha, la, sb, eb, hb, lb;
@@ -164,9 +171,10 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
             phi = F2(ha, hb);
             *h0p = make_float4(0.f, la, 0.f, lb);                       // low parts of phi
         } else {
-            phi = cvt_h(ld_pair(hplane(Lr, 0) + j));
+            static_assert(!F::h16, "FP16 h is stored with the conservative h_0 only");
+            phi = ld_pair(hplane(Lr, 0) + j);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) phi = phi + cvt_h(ld_pair(hplane(Lr, i) + j));   // Eq. 18
+            for (int i = 1; i < 9; ++i) phi = phi + ld_pair(hplane(Lr, i) + j);   // Eq. 18
         }
         st_pair(prow(Lr) + j, phi);
     };
@@ -310,9 +318,9 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
             h[0] = lo;
         }
 #pragma unroll
-        for (int i = F::cons ? 1 : 0; i < 9; ++i) h[i] = cvt_h(ld_pair(hplane(Y, i) + jX));
+        for (int i = F::cons ? 1 : 0; i < 9; ++i) h[i] = ld_pair(hplane(Y, i) + jX);   // as stored
 
-        const Macro<F2> m = macroscopic(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
+        const Macro<F2> m = macroscopic<F::g16>(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
         const F2 phiux = phi * m.ux, phiuy = phi * m.uy;
         if constexpr (MON) {
             mon.add(phi.v.x, lo.v.x, m.rho.v.x, m.ux.v.x, m.uy.v.x);
@@ -324,39 +332,45 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
         const bool bot = walls && Y == 0, top = walls && Y == ny - 1;
         const int rDn = bot ? 0 : rowoff(Y - 1);
         const int rUp = top ? 0 : rowoff(Y + 1);
-        float ra = 0.f, rb = 0.f;   // sums of the stored h_1..h_8 of the two cells
-        collide_emit(C, m, phi, mu, phiux - pu_x, phiuy - pu_y, g, h, [&](int i, F2 gi, F2 hi) {
+        // sums of the stored h_1..h_8 of the two cells (FP16 h: in units of hs)
+        float ra = 0.f, rb = 0.f;
+        collide_emit<F::g16, F::h16>(C, m, phi, mu, phiux - pu_x, phiuy - pu_y, g, h, [&](int i, F2 gi, F2 hi) {
+            const auto gq = to_store(gi, gout);
             if constexpr (F::cons) {
                 if (i == 0) {          // rest direction: g_0 now, h_0 after all h_1..h_8
-                    st_g2(0, c, gi);
+                    st_both(gplane_out(0) + c, gq);
                     return;
                 }
-                if constexpr (F::h16)
-                    hi = F2(__half2float(__float2half_rn(hi.v.x * hs)) * ihs,
-                            __half2float(__float2half_rn(hi.v.y * hs)) * ihs);
-                ra += hi.v.x;
-                rb += hi.v.y;
+            }
+            const auto hq = to_store(hi, hout);
+            if constexpr (F::cons) {
+                ra += first_f(hq);
+                rb += second_f(hq);
             }
             const int cyi = cy_of(i), cxi = cx_of(i);
             if ((cyi > 0 && top) || (cyi < 0 && bot)) {   // back into the own pair, reversed
                 const int k = opp_of(i);
-                st_h2(k, c, hi);
-                st_g2(k, c, gi);
+                st_both(hplane_out(k) + c, hq);
+                st_both(gplane_out(k) + c, gq);
                 return;
             }
             const int r = cyi == 0 ? rY : (cyi > 0 ? rUp : rDn);
             if (cxi == 0) {
-                if (!F::cons || i != 0) st_h2(i, r + X, hi);
-                st_g2(i, r + X, gi);
+                if (!F::cons || i != 0) st_both(hplane_out(i) + r + X, hq);
+                st_both(gplane_out(i) + r + X, gq);
             } else {
                 const int da = r + (cxi > 0 ? X + 1 : colm);   // destination of cell X
                 const int db = r + (cxi > 0 ? colp : X);       // destination of cell X + 1
-                st_h1(i, da, hi.v.x);
-                st_h1(i, db, hi.v.y);
-                st_g1(i, da, gi.v.x);
-                st_g1(i, db, gi.v.y);
+                st_first(hplane_out(i) + da, hq);
+                st_second(hplane_out(i) + db, hq);
+                st_first(gplane_out(i) + da, gq);
+                st_second(gplane_out(i) + db, gq);
             }
         });
+        if constexpr (F::h16) {   // exact: ihs is a power of two
+            ra *= ihs;
+            rb *= ihs;
+        }
         if constexpr (F::cons) {
             float s_, e_, hi, l2;
             float4 h0c;
@@ -379,12 +393,12 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
             if (ghost(Y0 + k * d) == (pass == 1)) lead_row(Y0 + k * d);
     p_row(Y0 - d);
     p_row(Y0);
-    __syncthreads();
+    group_sync(bar, TX);
     // the slot of row Y0 - 2d (read only above) takes the first lead row
     prefetch(Y0 + 2 * d, Y0 + d);
     mu_row(Y0);
     mu_row(Y0 - d);
-    __syncthreads();
+    group_sync(bar, TX);
     for (int k = 0; k < wk.nrows; ++k) {
         const int Y = Y0 + k * d;
         // g and phi*u of the collision pair, loaded before the barriers
@@ -404,15 +418,68 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
         if constexpr (!F::h16)
             if (k + 1 < wk.nrows) l2_prefetch_row(Y + d);
         lead_row_async(Y + 2 * d);
-        __syncthreads();
+        group_sync(bar, TX);
         // every thread is past the collision of row Y - d: the h slot of row Y - d
         // and the p slot of row Y - 2d are free for the next iteration's rows
         if (k + 1 < wk.nrows) prefetch(Y + 3 * d, Y + 2 * d);
         mu_row(Y + d);
-        __syncthreads();
+        group_sync(bar, TX);
         collide_row(Y, g, pux, puy);
     }
-    if constexpr (MON) mon_block_store(mon, a.mon + (long long)blockIdx.x * kMonQ);
+    if constexpr (MON) mon_block_store(mon, a, wk.inst, item, tid, TX, bar, grp);
+}
+
+template <int FORM, int TX, bool MON = false>
+__global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(const StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    x2_item<FORM, TX, MON>(a, blockIdx.x, smem_raw, threadIdx.x, 0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// The batched step: every instance of a context in one persistent launch.
+// Blocks of 128 threads take block descriptors (BlockDesc: two work items,
+// strips of up to 128 columns) from a queue -- an atomic counter over the
+// descriptors, which the planner sorts longest run first -- until it runs dry.
+// Each item runs on its own group of 64 threads with its own shared-memory
+// region and its own named barrier, so the two groups march independently
+// (different instances, run lengths and directions); the block meets again
+// only between descriptors. One group size for every instance keeps one code
+// path (mixing 32-, 64- and 128-thread paths in one kernel made the register
+// allocator spill). The last block to finish sets the queue back to zero for
+// the next step.
+// Three resident blocks a SM (up to 168 registers a thread) for every form: at
+// four, the FP16-h form's batched kernel spilled at its 128-register cap and ran
+// at 23.2k MLUPS on the 512 mixed instances.
+template <int FORM>
+struct X2Batched {
+    static constexpr size_t bytes = 2 * X2Smem<FORM, 64>::bytes;
+    static constexpr int by_smem = (int)((228u * 1024u) / (bytes + 1024u));
+    static constexpr int occ = by_smem < 3 ? by_smem : 3;
+};
+
+template <int FORM, bool MON = false>
+__global__ void __launch_bounds__(128, X2Batched<FORM>::occ) step_kernel_x2_batched(const StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_desc;
+    const int tid = threadIdx.x;
+    const int g = tid >> 6;   // thread group: 0 or 1
+    for (;;) {
+        if (tid == 0) s_desc = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = s_desc;
+        if (q >= a.ndesc) break;
+        const int item = a.desc[q].item[g];
+        if (item >= 0)
+            x2_item<FORM, 64, MON>(a, item, smem_raw + g * X2Smem<FORM, 64>::bytes, tid & 63, 1 + g, g);
+        __syncthreads();   // both groups are done with their regions; s_desc may change
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 1, 1) == (int)gridDim.x - 1) {   // every block is past the queue
+            a.queue[0] = 0;
+            a.queue[1] = 0;
+        }
+    }
 }
 
 }  // namespace lbm

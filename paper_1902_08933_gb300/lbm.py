@@ -28,7 +28,8 @@ LBM_FS_MU_GRADPHI, LBM_FS_PHI_GRADMU = 0, 1
 LBM_VISC_INV_LINEAR, LBM_VISC_STEP = 0, 1
 LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C = 0, 1, 2, 3, 4
 LBM_PIPELINE_AUTO, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC, LBM_PIPELINE_TMA, LBM_PIPELINE_PAIRS = 0, 1, 2, 3, 4
-VARIANTS = {0: "plain", 1: "async", 2: "tma", 3: "pairs"}
+LBM_PIPELINE_BATCHED = 5
+VARIANTS = {0: "plain", 1: "async", 2: "tma", 3: "pairs", 4: "batched"}
 FIELDS = ("phi", "ux", "uy", "p", "rho", "mu", "P")
 FIELDS3 = FIELDS + ("uz",)          # D3Q15 lattices (nz >= 2) also have uz
 FIELD_BITS = {name: 1 << k for k, name in enumerate(FIELDS3)}
@@ -70,6 +71,12 @@ class lbm_monitor(ctypes.Structure):
                 ("device_status", ctypes.c_int32), ("time", ctypes.c_int64)]
 
 
+class lbm_launch_shape(ctypes.Structure):
+    _fields_ = [("pipeline", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("ms_per_step", ctypes.c_double),
+                ("default_ms_per_step", ctypes.c_double)]
+
+
 class lbm_sp_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
                 ("model", ctypes.c_int32), ("nu", ctypes.c_double), ("xi", ctypes.c_double),
@@ -106,6 +113,10 @@ SIGNATURES = [
     ("lbm_launch_info", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_autotune_shape", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_launch_shape)]),
+    ("lbm_row_bytes", ctypes.c_size_t, [_VP, ctypes.c_int]),
+    ("lbm_pack_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t]),
+    ("lbm_unpack_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t]),
     ("lbm_launches_per_step", ctypes.c_int, [_VP]),
     ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
     ("lbm_reduce_fields_noalloc", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
@@ -268,6 +279,36 @@ def lbm_autotune(ctx):
     t, r = ctypes.c_int(), ctypes.c_int()
     _check(library().lbm_autotune(ctx, ctypes.byref(t), ctypes.byref(r)), ctx)
     return t.value, r.value
+
+
+def lbm_row_bytes(ctx, instance: int) -> int:
+    """Bytes of state one row of an instance takes (0 if not applicable)."""
+    return int(library().lbm_row_bytes(ctx, int(instance)))
+
+
+def lbm_pack_rows(ctx, instance: int, y0: int, nrows: int, dev_ptr: int, nbytes: int):
+    """Queues the copy of rows [y0, y0 + nrows) of the instance's state into
+    caller device memory at dev_ptr (nbytes available)."""
+    _check(library().lbm_pack_rows(ctx, int(instance), int(y0), int(nrows), _VP(dev_ptr), int(nbytes)), ctx)
+
+
+def lbm_unpack_rows(ctx, instance: int, y0: int, nrows: int, dev_ptr: int, nbytes: int):
+    """Queues the copy of rows [y0, y0 + nrows) of the instance's state from
+    caller device memory at dev_ptr."""
+    _check(library().lbm_unpack_rows(ctx, int(instance), int(y0), int(nrows), _VP(dev_ptr), int(nbytes)), ctx)
+
+
+LBM_TUNE_NO_CACHE = 1
+PIPELINES = {0: "auto", 1: "plain", 2: "async", 3: "tma", 4: "pairs", 5: "batched"}
+
+
+def lbm_autotune_shape(ctx, flags: int = 0) -> dict:
+    """Runs (or takes from the cache) the autotuner; returns the chosen shape."""
+    r = lbm_launch_shape()
+    _check(library().lbm_autotune_shape(ctx, int(flags), ctypes.byref(r)), ctx)
+    return {"pipeline": PIPELINES.get(r.pipeline, r.pipeline), "tile_x": r.tile_x, "rows": r.rows,
+            "trials": r.trials, "ms_per_step": r.ms_per_step,
+            "default_ms_per_step": r.default_ms_per_step}
 
 
 def lbm_launches_per_step(ctx) -> int:

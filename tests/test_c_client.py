@@ -27,9 +27,11 @@ int main(void) {
     sp.nx = 2; sp.ny = 16; sp.nu = 0.1;              /* nx < 3 */
     if (lbm_sp_create(&sp, LBM_F64, 0, &sctx) != LBM_EINVAL || sctx != 0) return 3;
     if (lbm_step(0, 1) != LBM_EINVAL || lbm_sp_step(0, 1) != LBM_EINVAL) return 4;
+    if (lbm_autotune_shape(0, 0, 0) != LBM_EINVAL) return 5;
     lbm_destroy(0);
     lbm_sp_destroy(0);
-    printf("ok %d %d\n", (int)sizeof(lbm_params), (int)sizeof(lbm_sp_params));
+    printf("ok %d %d %d %d\n", (int)sizeof(lbm_params), (int)sizeof(lbm_sp_params),
+           (int)sizeof(lbm_monitor), (int)sizeof(lbm_launch_shape));
     return 0;
 }
 """
@@ -53,6 +55,8 @@ def test_header_compiles_as_c99_and_links(tmp_path):
     # the Python binding's structures have the C layout
     from paper_1902_08933_gb300 import lbm
     import ctypes
-    _, n_params, n_sp = r.stdout.split()
+    _, n_params, n_sp, n_mon, n_shape = r.stdout.split()
     assert ctypes.sizeof(lbm.lbm_params) == int(n_params)
     assert ctypes.sizeof(lbm.lbm_sp_params) == int(n_sp)
+    assert ctypes.sizeof(lbm.lbm_monitor) == int(n_mon)
+    assert ctypes.sizeof(lbm.lbm_launch_shape) == int(n_shape)

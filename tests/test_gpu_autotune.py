@@ -1,0 +1,102 @@
+"""The autotuner (lbm_autotune_shape): it runs real trial steps, so the state it
+hands back must be bit for bit the state it was given, with the same time level;
+the shape it keeps must not be slower than the built-in plan; and its choice is
+cached per (device, form, instance sizes)."""
+import statistics
+
+import numpy as np
+import pytest
+
+from paper_1902_08933_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_08933_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def _ms_per_step(L, sim, stream, steps, reps=7):
+    import torch
+    out = []
+    sim.step(4)                      # (re)plans and captures the graph outside the timing
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / steps)
+    return statistics.median(out)
+
+
+def test_autotune_leaves_state_and_time_untouched(L):
+    cfgs = [wl.rising_bubble(nx=256, ny=96, R=14, cy=30, W=4.0, Re=8.0), wl.static_droplet(n=64, R=15)]
+    with L.Simulation(cfgs, "f32_c", phi0=[wl.initial_phi(c) for c in cfgs]) as sim:
+        sim.step(13)                 # odd: the tuner must give back the buffer parity too
+        L.lbm_set_monitor(sim.ctx, True)
+        sim.step(1)
+        before = [sim.populations(k) for k in range(2)]
+        t0 = [L.lbm_time(sim.ctx, k) for k in range(2)]
+        m0 = L.lbm_read_monitor(sim.ctx, 0)
+        shape = L.lbm_autotune_shape(sim.ctx, L.LBM_TUNE_NO_CACHE)
+        assert shape["trials"] > 1 and shape["ms_per_step"] > 0
+        after = [sim.populations(k) for k in range(2)]
+        for (ha, ga), (hb, gb) in zip(before, after):
+            assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
+        assert [L.lbm_time(sim.ctx, k) for k in range(2)] == t0
+        m1 = L.lbm_read_monitor(sim.ctx, 0)      # the last record is still the one before
+        assert m1["time"] == m0["time"] and m1["sum_phi"] == m0["sum_phi"]
+        # and the run continues exactly like an untuned one
+        sim.step(6)
+        tuned = [sim.populations(k) for k in range(2)]
+    with L.Simulation(cfgs, "f32_c", phi0=[wl.initial_phi(c) for c in cfgs]) as ref:
+        ref.step(13)
+        L.lbm_set_monitor(ref.ctx, True)
+        ref.step(1)
+        ref.step(6)
+        plain = [ref.populations(k) for k in range(2)]
+    for (ha, ga), (hb, gb) in zip(tuned, plain):
+        assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
+
+
+@pytest.mark.parametrize("case", ["bubble_1024x4096", "batched_512"])
+def test_autotuned_shape_is_not_slower_than_builtin(L, report, case):
+    import torch
+    if case == "bubble_1024x4096":
+        cfgs, form, steps = [wl.rising_bubble()], "f32_c", 200
+    else:
+        cfgs, form, steps = wl.batched_mixed(512), "f32", 60
+    stream = torch.cuda.Stream()
+    with L.Simulation(cfgs, form, stream=stream.cuda_stream,
+                      phi0=[wl.initial_phi(c) for c in cfgs]) as sim:
+        sim.step(4)
+        shape = L.lbm_autotune_shape(sim.ctx, L.LBM_TUNE_NO_CACHE)
+        tuned = _ms_per_step(L, sim, stream, steps)
+        L.lbm_set_pipeline(sim.ctx, L.LBM_PIPELINE_AUTO)
+        L.lbm_set_launch(sim.ctx, 0, 0)
+        builtin = _ms_per_step(L, sim, stream, steps)
+    report(tuned_ms=tuned, builtin_ms=builtin, trials=shape["trials"], pipeline=shape["pipeline"],
+           tile_x=shape["tile_x"], rows=shape["rows"])
+    assert tuned <= 1.03 * builtin, (shape, tuned, builtin)
+
+
+def test_autotune_cache(L):
+    cfg = wl.rising_bubble(nx=192, ny=80, R=12, cy=26, W=4.0, Re=8.0)
+    phi = wl.initial_phi(cfg)
+    with L.Simulation(cfg, "f32", phi0=[phi]) as a:
+        first = L.lbm_autotune_shape(a.ctx, L.LBM_TUNE_NO_CACHE)
+    with L.Simulation(cfg, "f32", phi0=[phi]) as b:
+        again = L.lbm_autotune_shape(b.ctx)
+        info = L.lbm_launch_info(b.ctx, 0)
+    assert first["trials"] > 0 and again["trials"] == 0
+    assert (again["pipeline"], again["tile_x"], again["rows"]) == (first["pipeline"], first["tile_x"], first["rows"])
+    assert info["variant"] in ("plain", "async", "tma", "pairs", "batched")
+    with L.Simulation(cfg, "f64", phi0=[phi]) as c:   # another form: another key
+        assert L.lbm_autotune_shape(c.ctx)["trials"] > 0
