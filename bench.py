@@ -16,7 +16,10 @@ than the 129 MB L2, so no L2 flush is needed between steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank advances its own independent replica of the
-workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
+workload (weak scaling, no data-path collective) for the headline value; the
+line also carries the 512 mixed instances split by instance across the ranks
+and the 1024 x 4096 bubble split into slabs with a ghost-row exchange over NCCL
+(both strong scaling). Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -423,6 +426,9 @@ def main():
         "mass_drift": abs(d["sum_phi"] - phi0.sum()) / phi0.sum(),
     }
 
+    if world > 1 and not args.headline_only:
+        result["multi_gpu"] = multi_gpu_legs(args, lbm, wl, cfg, phi0, stream, rank, world)
+
     if not args.headline_only and rank == 0:
         result.update(side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak))
 
@@ -431,6 +437,57 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def multi_gpu_legs(args, lbm, wl, cfg, phi0, stream, rank, world):
+    """Under torchrun with N > 1 (one rank per GPU), besides the replicas of the
+    headline: (1) the 512 mixed instances split by instance (sharding.py: no
+    exchange while stepping), (2) the 1024 x 4096 bubble as N horizontal slabs
+    with 12 ghost rows, exchanged over NCCL every 4 steps (slab.py). Both fix the
+    total work (strong scaling); the job time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    from paper_1902_08933_gb300 import sharding, slab
+    out = {}
+    K = max(50, args.steps // 4)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        dist.barrier()
+        return sharding.max_over_ranks(secs, device=torch.device("cuda", torch.cuda.current_device()))
+
+    cfgs = wl.batched_mixed(512)
+    cells = [c["nx"] * c["ny"] for c in cfgs]
+    mine = sharding.shard(cells, rank, world)
+    with lbm.Simulation([cfgs[i] for i in mine], "f32", stream=stream.cuda_stream,
+                        phi0=[wl.initial_phi(cfgs[i]) for i in mine]) as sim:
+        sim.step(2)
+        lbm.lbm_autotune_shape(sim.ctx)
+        warm(sim, 6)
+        secs = timed(lambda: sim.step(K))
+    out["batched_sharded"] = {"MLUPS": sum(cells) * K / secs / 1e6, "steps": K, "scaling": "strong",
+                              "instances_per_rank": len(mine),
+                              "imbalance": sharding.imbalance(cells, world)}
+    ghost = 12
+    slabs = slab.plan(cfg["ny"], world, ghost, periodic=not cfg["walls_y"])
+    me = slabs[rank]
+    with torch.cuda.stream(stream), lbm.Simulation(
+            slab.local_config(cfg, me, world), args.form, stream=stream.cuda_stream,
+            phi0=[slab.local_field(phi0, me)]) as sim:
+        run = slab.SlabRun(slabs, ghost, {rank: slab.GpuSlab(lbm, sim, 0)}, not cfg["walls_y"],
+                           group=dist.group.WORLD)
+        run.start()
+        run.advance(2 * run.k)
+        secs = timed(lambda: run.advance(K))
+    out["slab"] = {"MLUPS": cfg["nx"] * cfg["ny"] * K / secs / 1e6, "steps": K, "scaling": "strong",
+                   "ghost_rows": ghost, "steps_between_exchanges": ghost // slab.REACH,
+                   "rows_per_rank": me.own, "form": args.form}
+    return out
 
 
 def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
@@ -451,11 +508,14 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
             f = sim.fields(0, ("phi", "ux", "uy", "p"))
             if form == "f64":
                 ref = f
+            shape = lbm.lbm_autotune_shape(sim.ctx)
             ms = time_steps(lbm, sim, stream, K, 5)
             mlups = cells * K / (ms * 1e-3) / 1e6
             gbs = BYTES_PER_LUP[form] * cells / (ms * 1e-3 / K) / 1e9
             forms[form] = {"MLUPS": mlups, "GBps": gbs, "frac_hbm": gbs / hbm_peak,
-                           "steps": K,
+                           "frac_hbm_algorithmic": ALGO_BYTES_PER_LUP[form] * cells / (ms * 1e-3 / K) / 1e9 / hbm_peak,
+                           "steps": K, "launch_shape": shape,
+                           "kernel": lbm.lbm_launch_info(sim.ctx, 0)["variant"],
                            "roofline": fp64_roofline(mlups) if form == "f64" else
                            {"bound": "hbm", "frac": gbs / hbm_peak},
                            "err_vs_f64_after_%d_steps" % acc_steps: (
@@ -572,11 +632,23 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
         lbm.lbm_init(sim.ctx, 0, host_phi0)
         sim.step(5)
         lbm.lbm_read_monitor(sim.ctx, 0)
+        # the monitored step writes its record into the pinned slot itself
+        # (lbm_step_monitored); where the device cannot write that memory, the
+        # record is copied after the step instead (lbm_read_monitor_async)
+        try:
+            lbm.lbm_step_monitored(sim.ctx, 1, slots[0].data_ptr())
+            direct = True
+        except lbm.LbmError:
+            direct = False
+        sim.sync()
         t0 = time.perf_counter()
         lbm.lbm_init(sim.ctx, 0, host_phi0)
         for t in range(Ke):
-            lbm.lbm_step(sim.ctx, 1)
-            lbm.lbm_read_monitor_async(sim.ctx, 0, slots[t % NSLOT].data_ptr())
+            if direct:
+                lbm.lbm_step_monitored(sim.ctx, 1, slots[t % NSLOT].data_ptr())
+            else:
+                lbm.lbm_step(sim.ctx, 1)
+                lbm.lbm_read_monitor_async(sim.ctx, 0, slots[t % NSLOT].data_ptr())
             done[t % NSLOT].record(stream)
             if t >= NSLOT - 1:
                 tc = t - NSLOT + 1
@@ -600,9 +672,12 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     d2h = ctypes.sizeof(lbm.lbm_monitor) + 8 * 4 * cells / Ke
     out["e2e"] = {"value": cells * Ke / dt / 1e6, "unit": "MLUPS",
                   "h2d_bytes_per_step": 8 * cells / Ke, "d2h_bytes_per_step": d2h,
-                  "steps": Ke, "per_step": "lbm_step(1) with the fused monitor + lbm_read_monitor_async "
-                                          "(sum phi, kinetic energy, max |u| to pinned host memory, "
-                                          "checked once the step has finished)",
+                  "steps": Ke, "per_step": ("lbm_step_monitored(1): the step kernels also reduce sum phi, "
+                                           "kinetic energy and max |u| and write that record into a pinned "
+                                           "host slot from the GPU" if direct else
+                                           "lbm_step(1) with the fused monitor + lbm_read_monitor_async into a "
+                                           "pinned host slot") + "; each record checked on the host once its "
+                                          "step has finished, %d steps later" % (NSLOT - 1),
                   "once": "lbm_init from pinned host phi0 (%.1f MB, about %.2f ms) before the first step, "
                           "lbm_get_fields of phi, ux, uy, p to pinned host memory (%.1f MB, %.2f ms) after "
                           "the last, both inside the timed region and spread over its %d steps" % (

@@ -199,6 +199,18 @@ lbm_status lbm_set_monitor(lbm_ctx* ctx, int enable);
  * lbm_sync), LBM_ENONFINITE (phi or u not finite somewhere; *out is filled). */
 lbm_status lbm_read_monitor(lbm_ctx* ctx, int instance, lbm_monitor* out);
 
+/* lbm_step with the monitor's records written straight into caller memory:
+ * the monitored (last) step's kernels write each instance's record into
+ * host_records[instance] (n_instances records; pinned host memory the device
+ * can write, e.g. from cudaMallocHost) themselves, from the GPU, so no copy is
+ * queued after the step. The records are valid once the stream has passed the
+ * step (lbm_sync, or a CUDA event recorded after the call); the caller checks
+ * their nonfinite and device_status fields. They are also kept for
+ * lbm_read_monitor. Give each call its own records while earlier ones may
+ * still be read. Errors: LBM_EINVAL (NULL context or records, nsteps < 1,
+ * memory the device cannot write), LBM_ESTATE (monitor off), as lbm_step. */
+lbm_status lbm_step_monitored(lbm_ctx* ctx, int nsteps, lbm_monitor* host_records);
+
 /* As lbm_read_monitor without the wait: queues on the context's stream the copy
  * of the record into host_out (caller-owned; pinned memory, e.g. from
  * cudaMallocHost, keeps the copy asynchronous) and returns. The record is valid

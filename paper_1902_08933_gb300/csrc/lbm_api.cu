@@ -173,6 +173,7 @@ struct lbm_ctx {
     int* d_mon_csr = nullptr;           // per instance: work items [ptr[k], ptr[k+1]) of idx
     int* d_mon_count = nullptr;         // per instance: blocks of the monitored step done (0 between steps)
     lbm_monitor* d_mon = nullptr;       // one record per instance
+    lbm::MonRecord* mon_host_dev = nullptr;   // during lbm_step_monitored: the caller's mapped host records
     int64_t steps_total = 0;            // steps taken by the context
     int64_t* d_time_base = nullptr;     // per instance: time - steps_total (device copy)
     lbm_monitor* h_mon = nullptr;       // pinned staging record
@@ -230,6 +231,7 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.desc = c->d_desc;
     a.ndesc = c->ndesc;
     a.queue = c->d_queue;
+    a.mon_host = nullptr;
     return a;
 }
 
@@ -821,6 +823,7 @@ cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStre
         a.mon_rec = reinterpret_cast<lbm::MonRecord*>(c->d_mon);
         a.time_base = c->d_time_base;
         a.mon_step = mon_step;
+        a.mon_host = c->mon_host_dev;
     }
     return by_form(c->form, [&](auto F) {
         return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, s, L.variant, monitor);
@@ -969,6 +972,24 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         if (mon_last) c->mon_time[k] = c->time[k] - 1;
     }
     return LBM_OK;
+}
+
+lbm_status lbm_step_monitored(lbm_ctx* c, int nsteps, lbm_monitor* host_records) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 1) return fail(c, LBM_EINVAL, "nsteps < 1");
+    if (!host_records) return fail(c, LBM_EINVAL, "host_records is NULL");
+    if (!c->monitor || !c->d_mon) return fail(c, LBM_ESTATE, "the per-step monitor is off (lbm_set_monitor)");
+    LBM_CK(c, cudaSetDevice(c->device));
+    void* dptr = nullptr;
+    if (cudaHostGetDevicePointer(&dptr, host_records, 0) != cudaSuccess || !dptr) {
+        cudaGetLastError();
+        return fail(c, LBM_EINVAL, "host_records must be pinned host memory the device can write "
+                                   "(cudaMallocHost / cudaHostAlloc)");
+    }
+    c->mon_host_dev = static_cast<lbm::MonRecord*>(dptr);
+    const lbm_status st = lbm_step(c, nsteps);
+    c->mon_host_dev = nullptr;
+    return st;
 }
 
 lbm_status lbm_set_monitor(lbm_ctx* c, int enable) {

@@ -498,6 +498,27 @@ template <> struct MonAcc<float> {
         mass = double(mh) + double(ml); kin = double(ke); umax2 = double(u2);
     }
 };
+// Two cells a thread (the paired kernel): the same sums kept per lane of the
+// packed FP32 instructions (TwoSum in FADD2), lanes combined in FP64 at the end.
+template <> struct MonAcc<F2> {
+    F2 mh = F2(0.f), ml = F2(0.f), ke = F2(0.f);
+    float u2 = 0.f;
+    __device__ __forceinline__ void add(F2 phi, F2 lo, F2 rho, F2 ux, F2 uy) {
+        const F2 sm = mh + phi;                      // TwoSum, lane by lane
+        const F2 bb = sm - mh;
+        const F2 e = (mh - (sm - bb)) + (phi - bb);
+        mh = sm;
+        ml = ml + (e + lo);
+        const F2 uu = fmadd(ux, ux, uy * uy);
+        ke = fmadd(F2(0.5f) * rho, uu, ke);
+        u2 = fmaxf(u2, fmaxf(uu.v.x, uu.v.y));
+    }
+    __device__ __forceinline__ void result(double& mass, double& kin, double& umax2) const {
+        mass = (double(mh.v.x) + double(ml.v.x)) + (double(mh.v.y) + double(ml.v.y));
+        kin = double(ke.v.x) + double(ke.v.y);
+        umax2 = double(u2);
+    }
+};
 
 // Block reduction of the monitor sums; thread 0 writes {sum phi, kinetic
 // energy, max |u|^2, non-finite flag} to this block's slot a.mon[blockIdx.x].
@@ -513,7 +534,11 @@ template <> struct MonAcc<float> {
 // nthr threads, tid its index in the group); item is the work item whose slot
 // the group writes.
 __device__ __forceinline__ void group_sync(int bar, int nthr) {
-    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+    if (bar == 0) {   // the whole block (a compile-time 0 wherever a kernel passes it)
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+    }
 }
 
 template <typename R>
@@ -583,6 +608,7 @@ __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const Step
         r.nonfinite = s[3] != 0.0 ? 1 : 0;
         r.device_status = *(volatile int*)a.status;
         r.time = a.mon_step + a.time_base[inst];
+        if (a.mon_host) a.mon_host[inst] = r;             // caller's pinned host record, written from here
         a.mon_count[inst] = 0;                            // ready for the next monitored step
     }
 }

@@ -64,6 +64,7 @@ struct StepArgs {
     const int* mon_csr;                 // per instance k: items idx[csr[k] .. csr[k+1]) (idx at csr + n + 1)
     int mon_n;                          // instances
     struct MonRecord* mon_rec;          // one record per instance
+    struct MonRecord* mon_host;         // optional: caller's pinned host records (device-mapped), or null
     const int64_t* time_base;           // per instance: time level - steps of the context
     long long mon_step;                 // steps of the context before the monitored step
     // batched step only: block descriptors, their number, and the queue

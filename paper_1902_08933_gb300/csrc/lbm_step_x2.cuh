@@ -119,7 +119,7 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
     // arithmetic keeps h and g in those units (collide_emit / macroscopic with
     // their scale flags), so only the sum of h that forms phi is un-scaled.
     const float ihs = C.ihs;
-    MonAcc<float> mon;
+    MonAcc<F2> mon;
 
     auto wrapx = [nx](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
     auto rowg = [ny, walls](int y) { return walls ? y : (y < 0 ? y + ny : (y >= ny ? y - ny : y)); };
@@ -323,8 +323,7 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
         const Macro<F2> m = macroscopic<F::g16>(C, g, phi, mu, gphix, gphiy, gmux, gmuy, lapmu, gpx, gpy);
         const F2 phiux = phi * m.ux, phiuy = phi * m.uy;
         if constexpr (MON) {
-            mon.add(phi.v.x, lo.v.x, m.rho.v.x, m.ux.v.x, m.uy.v.x);
-            mon.add(phi.v.y, lo.v.y, m.rho.v.y, m.ux.v.y, m.uy.v.y);
+            mon.add(phi, lo, m.rho, m.ux, m.uy);
         }
         // Push-streaming as each result is formed (halfway bounce-back into walls;
         // wall rows uniform per row). Conservative forms: h_0 goes last, as phi

@@ -101,6 +101,7 @@ SIGNATURES = [
     ("lbm_set_monitor", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_read_monitor", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_monitor)]),
     ("lbm_read_monitor_async", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("lbm_step_monitored", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     ("lbm_get_fields", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _DP]),
     ("lbm_get_fields_device", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _VP]),
     ("lbm_diagnostics", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_diag)]),
@@ -213,6 +214,12 @@ def lbm_read_monitor(ctx, instance: int) -> dict:
         _check(st, ctx)
     return {"sum_phi": m.sum_phi, "kinetic_energy": m.kinetic_energy, "max_u": m.max_u,
             "time": m.time, "status": st}
+
+
+def lbm_step_monitored(ctx, nsteps: int, host_records_ptr: int):
+    """lbm_step whose monitored last step writes the records (one lbm_monitor per
+    instance) into pinned host memory at host_records_ptr, from the GPU."""
+    _check(library().lbm_step_monitored(ctx, int(nsteps), _VP(host_records_ptr)), ctx)
 
 
 def lbm_read_monitor_async(ctx, instance: int, host_record_ptr: int):

@@ -205,3 +205,34 @@ def test_monitor_record_carries_a_wait_timeout(L):
         with pytest.raises(L.LbmError) as e:
             L.lbm_read_monitor(sim.ctx, 0)
         assert e.value.status == L.LBM_ETIMEOUT
+
+
+def test_step_monitored_writes_records_to_host(L):
+    # lbm_step_monitored: the monitored step's kernels write each instance's
+    # record into pinned host memory themselves; the records equal the ones
+    # lbm_read_monitor returns, call after call, batched launch included
+    import ctypes
+    import torch
+    cfgs = [wl.rising_bubble(nx=96, ny=64, R=10.0, cy=20.0, Re=5.0), wl.static_droplet(n=64, R=16.0),
+            wl.static_droplet(n=48, R=11.0)]
+    n = len(cfgs)
+    size = ctypes.sizeof(L.lbm_monitor)
+    slots = [torch.zeros(n * size, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    with L.Simulation(cfgs, "f32_c", phi0=[wl.initial_phi(c) for c in cfgs]) as sim:
+        L.lbm_set_monitor(sim.ctx, True)
+        for call in range(4):
+            slot = slots[call % 2]
+            slot.zero_()
+            L.lbm_step_monitored(sim.ctx, 3, slot.data_ptr())
+            sim.sync()
+            for k in range(n):
+                r = L.lbm_monitor.from_address(slot.data_ptr() + k * size)
+                m = L.lbm_read_monitor(sim.ctx, k)
+                assert r.time == 3 * call + 2 == m["time"]
+                assert r.nonfinite == 0 and r.device_status == 0
+                assert (r.sum_phi, r.kinetic_energy, r.max_u) == (m["sum_phi"], m["kinetic_energy"], m["max_u"])
+        with pytest.raises(L.LbmError):
+            L.lbm_step_monitored(sim.ctx, 0, slots[0].data_ptr())
+        L.lbm_set_monitor(sim.ctx, False)
+        with pytest.raises(L.LbmError):
+            L.lbm_step_monitored(sim.ctx, 1, slots[0].data_ptr())
