@@ -39,11 +39,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # bytes each storage form moves a lattice update (state read once and written once)
-BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176}
+BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176, "f32_cc": 176}
 # the method's algorithmic bytes: 9 + 9 populations, phi u (2) and p read and
 # written once in the form's word size; the two-float h_0 of f32_c (8 bytes, not
 # 4) is the form's own addition and not counted
-ALGO_BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_c": 168, "f32_g16": 132, "f32_h16": 100}
+ALGO_BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_c": 168, "f32_cc": 168, "f32_g16": 132, "f32_h16": 100}
 # D3Q15: 15 + 15 populations, phi u (3), p, each read and written once
 BYTES_PER_LUP_D3 = {"f64": 544, "f32": 272, "f32_c": 280}
 METRIC = "MLUPS and % of HBM peak, FP64 vs FP32/FP16-storage vs batched, at stated error"
@@ -410,7 +410,9 @@ def main():
                    "form": args.form, "load_path": variant, "storage": {"f64": "f64", "f32": "f32",
                                                   "f32_g16": "h0 2xf32, h1-8 f32, g f16",
                                                   "f32_h16": "h0 2xf32, h1-8 f16, g f16",
-                                                  "f32_c": "h0 2xf32, h1-8 f32, g f32"}[args.form],
+                                                  "f32_c": "h0 2xf32, h1-8 f32, g f32",
+                                                  "f32_cc": "h0 2xf32, h1-8 f32, g f32, "
+                                                            "mu from the two-float phi"}[args.form],
                    "l2": "state %.0f MB > 129 MB L2, no flush" % (
                        2 * BYTES_PER_LUP[args.form] / 2 * cells / 1e6),
                    "parallelism": "replicas" if world > 1 else "single",
@@ -502,7 +504,7 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     acc_steps = 200
     ref = None
     forms = {}
-    for form in ("f64", "f32", "f32_c", "f32_g16", "f32_h16"):
+    for form in ("f64", "f32", "f32_c", "f32_cc", "f32_g16", "f32_h16"):
         with lbm.Simulation(cfg, form, stream=stream.cuda_stream, phi0=[phi0]) as sim:
             sim.step(acc_steps)
             f = sim.fields(0, ("phi", "ux", "uy", "p"))

@@ -68,11 +68,16 @@ enum { LBM_VISC_INV_LINEAR = 0, LBM_VISC_STEP = 1 };
  *  LBM_F32_H16  FP32 arithmetic; h_1..h_8 and g in FP16, scaled; conservative
  *               h_0 [108].
  *  LBM_F32_C    FP32 arithmetic and storage with conservative h_0 [176].
+ *  LBM_F32_CC   LBM_F32_C whose step also forms the chemical potential (Eq. 8)
+ *               from phi = hi + lo, the two-float phi the conservative h_0
+ *               gives (compensated mu: about 40 times closer to FP64 in p and u
+ *               over the first steps of the rising bubble, for about 4 % of the
+ *               step time; kernels with two cells a thread, nx even) [176].
  * Conservative h_0: h_0 is stored as a pair of floats (hi + lo) set after each
  * collision to phi minus the stored h_1..h_8 with error-free FP32 operations,
  * so that storage rounding cannot create or destroy phi (sum of phi conserved
  * to ~1e-13 relative instead of drifting ~2^-24 per step in plain FP32). */
-enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_G16 = 2, LBM_F32_H16 = 3, LBM_F32_C = 4 };
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_G16 = 2, LBM_F32_H16 = 3, LBM_F32_C = 4, LBM_F32_CC = 5 };
 
 /* Field selection bits for lbm_get_fields*: outputs are written field-major in
  * this bit order, each field nx*ny doubles (nx*ny*nz on a D3Q15 lattice, cell
@@ -181,11 +186,11 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * step of every lbm_step call runs step kernels that also reduce, over the
  * cells they collide, sum(phi), the kinetic energy sum(rho |u|^2 / 2) and
  * max |u| of the fields at that step's input time level (the fields
- * lbm_get_fields returns at that time); the last block of each instance to
- * finish combines the per-block values of that instance in a fixed order (the
- * work-list order, whichever block comes last) and writes its record, so the
- * monitored step is as many launches as a plain one. The other steps run the
- * plain kernels. FP64 forms sum in FP64; FP32-arithmetic forms sum phi in a
+ * lbm_get_fields returns at that time); the blocks then combine their values
+ * in a two-level tree (sub-groups of an instance's blocks, then the
+ * sub-groups), each sum in a fixed order whichever blocks finish last, and the
+ * last of them writes the instance's record, so the monitored step is as many
+ * launches as a plain one. The other steps run the plain kernels. FP64 forms sum in FP64; FP32-arithmetic forms sum phi in a
  * float-float pair per thread (about 48 bits) and the energy in FP32 per thread,
  * then in FP64. Allocates the per-instance record on the first enable.
  * Errors: LBM_EINVAL (NULL context), LBM_ENOMEM/LBM_ECUDA (allocation). */

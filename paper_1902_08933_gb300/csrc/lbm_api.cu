@@ -21,7 +21,7 @@ using lbm::WorkItem;
 
 namespace {
 
-constexpr int kForms = 5;
+constexpr int kForms = 6;
 
 template <typename Fn>
 cudaError_t by_form(int form, Fn&& fn) {
@@ -31,6 +31,7 @@ cudaError_t by_form(int form, Fn&& fn) {
         case 2: return fn(std::integral_constant<int, 2>{});
         case 3: return fn(std::integral_constant<int, 3>{});
         case 4: return fn(std::integral_constant<int, 4>{});
+        case 5: return fn(std::integral_constant<int, 5>{});
         default: return cudaErrorInvalidValue;
     }
 }
@@ -171,7 +172,8 @@ struct lbm_ctx {
     bool monitor = false;
     double* d_mon_partials = nullptr;   // kMonQ doubles per work item
     int* d_mon_csr = nullptr;           // per instance: work items [ptr[k], ptr[k+1]) of idx
-    int* d_mon_count = nullptr;         // per instance: blocks of the monitored step done (0 between steps)
+    int* d_mon_count = nullptr;         // per instance: the reduction tree's counters (0 between steps)
+    double* d_mon_sub = nullptr;        // per instance: kMonSub sub-group slots
     lbm_monitor* d_mon = nullptr;       // one record per instance
     lbm::MonRecord* mon_host_dev = nullptr;   // during lbm_step_monitored: the caller's mapped host records
     int64_t steps_total = 0;            // steps taken by the context
@@ -222,6 +224,7 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.status = c->d_status;
     a.mon = nullptr;
     a.mon_all = nullptr;
+    a.mon_sub = nullptr;
     a.mon_count = nullptr;
     a.mon_csr = nullptr;
     a.mon_n = 0;
@@ -480,30 +483,40 @@ lbm_status finish_plan(lbm_ctx* c) {
         c->graph = nullptr;
         c->graph_steps = 0;
     }
-    if (c->d_work) cudaFree(c->d_work);
-    c->d_work = nullptr;
-    LBM_CK(c, cudaMalloc(&c->d_work, c->work.size() * sizeof(WorkItem)));
-    LBM_CK(c, cudaMemcpy(c->d_work, c->work.data(), c->work.size() * sizeof(WorkItem),
-                         cudaMemcpyHostToDevice));
-    // monitor: per-block slots and, per instance, the list of its work items
+    // monitor: per-block slots and, per instance, the list of its work items;
+    // each item's position within its instance's list (its sub-group in the
+    // monitor's reduction tree) goes into WorkItem::pad
     std::vector<int> csr(c->n + 1 + c->work.size(), 0);
     for (const WorkItem& w : c->work) ++csr[w.inst + 1];
     for (int k = 0; k < c->n; ++k) csr[k + 1] += csr[k];
     {
         std::vector<int> fill(csr.begin(), csr.begin() + c->n);
-        for (size_t j = 0; j < c->work.size(); ++j) csr[c->n + 1 + fill[c->work[j].inst]++] = (int)j;
+        for (size_t j = 0; j < c->work.size(); ++j) {
+            const int k = c->work[j].inst;
+            c->work[j].pad = fill[k] - csr[k];
+            csr[c->n + 1 + fill[k]++] = (int)j;
+        }
     }
+    if (c->d_work) cudaFree(c->d_work);
+    c->d_work = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_work, c->work.size() * sizeof(WorkItem)));
+    LBM_CK(c, cudaMemcpy(c->d_work, c->work.data(), c->work.size() * sizeof(WorkItem),
+                         cudaMemcpyHostToDevice));
     cudaFree(c->d_mon_partials);
     cudaFree(c->d_mon_csr);
     cudaFree(c->d_mon_count);
+    cudaFree(c->d_mon_sub);
     c->d_mon_partials = nullptr;
     c->d_mon_csr = nullptr;
     c->d_mon_count = nullptr;
+    c->d_mon_sub = nullptr;
+    const size_t ncnt = (size_t)c->n * (lbm::kMonSub + 1) * lbm::kCounterStride;
     LBM_CK(c, cudaMalloc(&c->d_mon_partials, c->work.size() * lbm::kMonQ * sizeof(double)));
+    LBM_CK(c, cudaMalloc(&c->d_mon_sub, (size_t)c->n * lbm::kMonSub * lbm::kMonQ * sizeof(double)));
     LBM_CK(c, cudaMalloc(&c->d_mon_csr, csr.size() * sizeof(int)));
     LBM_CK(c, cudaMemcpy(c->d_mon_csr, csr.data(), csr.size() * sizeof(int), cudaMemcpyHostToDevice));
-    LBM_CK(c, cudaMalloc(&c->d_mon_count, (size_t)c->n * sizeof(int)));
-    LBM_CK(c, cudaMemset(c->d_mon_count, 0, (size_t)c->n * sizeof(int)));
+    LBM_CK(c, cudaMalloc(&c->d_mon_count, ncnt * sizeof(int)));
+    LBM_CK(c, cudaMemset(c->d_mon_count, 0, ncnt * sizeof(int)));
     c->plan_dirty = false;
     return LBM_OK;
 }
@@ -634,6 +647,7 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_mon_partials);
     cudaFree(c->d_mon_csr);
     cudaFree(c->d_mon_count);
+    cudaFree(c->d_mon_sub);
     cudaFree(c->d_mon);
     cudaFree(c->d_time_base);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -817,6 +831,7 @@ cudaError_t enqueue_class(lbm_ctx* c, int in, const lbm_ctx::Launch& L, cudaStre
     if (monitor) {
         a.mon = c->d_mon_partials + (long long)L.offset * lbm::kMonQ;
         a.mon_all = c->d_mon_partials;
+        a.mon_sub = c->d_mon_sub;
         a.mon_count = c->d_mon_count;
         a.mon_csr = c->d_mon_csr;
         a.mon_n = c->n;

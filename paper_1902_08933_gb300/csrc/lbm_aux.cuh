@@ -68,7 +68,11 @@ __global__ void init_kernel(const StepArgs a, const double* __restrict__ phi0, i
 
 // ---------------------------------------------------------------------------
 // Macroscopic fields and diagnostics of one instance, in three passes over
-// global memory (phi, then mu, then everything else) -- off the hot loop.
+// global memory (phi, then mu, then everything else) -- off the hot loop. They
+// compute in FP64 whatever the storage form: the stored populations convert to
+// FP64 exactly (phi of the conservative forms from its two-float h_0 to about
+// 2^-48), so the fields, sums and the Laplace pressure P of Sec. 4.2 measure the
+// stored state without adding FP32 rounding of their own.
 template <int FORM>
 __global__ void phi_pass(const AuxArgs a) {
     using F = Form<FORM>;
@@ -103,7 +107,7 @@ __device__ __forceinline__ void gather(const double* f, int nx, int ny, int wall
 
 template <int FORM>
 __global__ void mu_pass(const AuxArgs a) {
-    using R = typename Form<FORM>::R;
+    using R = double;
     Consts<R> C;
     C.load(a.inst[a.instance]);
     const int n = C.nx * C.ny;
@@ -116,16 +120,17 @@ __global__ void mu_pass(const AuxArgs a) {
 
 // Everything one cell's macroscopic stage produces, plus the Laplace-law P of Sec. 4.2.
 template <int FORM>
-__device__ __forceinline__ void cell_fields(const AuxArgs& a, const Consts<typename Form<FORM>::R>& C,
-                                            int cell, typename Form<FORM>::R out[7], bool& finite) {
+__device__ __forceinline__ void cell_fields(const AuxArgs& a, const Consts<double>& C, int cell, double out[7],
+                                            bool& finite) {
     using F = Form<FORM>;
-    using R = typename F::R;
+    using R = double;
+    using SR = typename F::R;   // the storage form's arithmetic type: the values as loaded
     using AT = typename F::AT;
     PopIO<F> io;
     io.hin = static_cast<const typename F::HT*>(a.h);
     io.h0in = static_cast<const float2*>(a.h0);
     io.gin = static_cast<const typename F::GT*>(a.g);
-    io.S = a.S; io.hs = C.hs; io.ihs = C.ihs; io.gs = C.gs; io.igs = C.igs;
+    io.S = a.S; io.hs = SR(C.hs); io.ihs = SR(C.ihs); io.gs = SR(C.gs); io.igs = SR(C.igs);
     const int x = cell % C.nx, y = cell / C.nx;
     const long long c = C.base + cell;
     Nbr<R> nphi, nmu;
@@ -141,12 +146,13 @@ __device__ __forceinline__ void cell_fields(const AuxArgs& a, const Consts<typen
             else yy = yy < 0 ? yy + C.ny : (yy >= C.ny ? yy - C.ny : yy);
             np.z[dy + 1][dx + 1] = R(pp[yy * C.nx + xx]);
         }
-    R g[9], hv[9], lo;
+    R g[9];
+    SR hv[9], lo;
     io.phi_of(c, hv, lo);
     finite = isfinite(lo);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        g[i] = io.load_g(i, c);
+        g[i] = R(io.load_g(i, c));   // exact: FP16 or FP32 times a power of two
         finite = finite && isfinite(g[i]) && isfinite(hv[i]);
     }
     R gphix, gphiy, gmux, gmuy, gpx, gpy;
@@ -166,7 +172,7 @@ __device__ __forceinline__ void cell_fields(const AuxArgs& a, const Consts<typen
 
 template <int FORM>
 __global__ void fields_pass(const AuxArgs a) {
-    using R = typename Form<FORM>::R;
+    using R = double;
     Consts<R> C;
     C.load(a.inst[a.instance]);
     const int n = C.nx * C.ny;
@@ -197,7 +203,7 @@ __device__ __forceinline__ double warp_max(double v) {
 
 template <int FORM>
 __global__ void __launch_bounds__(256) diag_pass(const AuxArgs a) {
-    using R = typename Form<FORM>::R;
+    using R = double;
     Consts<R> C;
     C.load(a.inst[a.instance]);
     const int n = C.nx * C.ny;

@@ -55,6 +55,10 @@ __host__ __device__ constexpr R w_of(int i) {
 //   2 LBM_F32_G16  h_1..8 FP32, g FP16 (scaled), aux FP32, h_0 conservative.
 //   3 LBM_F32_H16  h_1..8 FP16 (scaled), g FP16 (scaled), aux FP32, h_0 conservative.
 //   4 LBM_F32_C    h_1..8 FP32, g FP32, aux FP32, h_0 conservative.
+//   5 LBM_F32_CC   form 4, and mu formed from the two-float phi ("comp").
+// "comp" (form 5): the paired kernels also form mu from phi = hi + lo
+// (compensated stencil, chem_pot2). The FP16-storage forms do not offer it:
+// their storage rounding dominates, and the extra stencil cost them 5-6 %.
 // "Conservative h_0": h_0 is kept as an unevaluated sum of two floats (hi + lo)
 // in a plane of its own and, after each collision, set to phi minus the stored
 // (rounded) h_1..h_8, with error-free FP32 transformations. The stored
@@ -65,23 +69,27 @@ __host__ __device__ constexpr R w_of(int i) {
 template <int FORM> struct Form;
 template <> struct Form<0> {
     using R = double; using HT = double; using GT = double; using AT = double;
-    static constexpr bool h16 = false, g16 = false, cons = false;
+    static constexpr bool h16 = false, g16 = false, cons = false, comp = false;
 };
 template <> struct Form<1> {
     using R = float; using HT = float; using GT = float; using AT = float;
-    static constexpr bool h16 = false, g16 = false, cons = false;
+    static constexpr bool h16 = false, g16 = false, cons = false, comp = false;
 };
 template <> struct Form<2> {
     using R = float; using HT = float; using GT = __half; using AT = float;
-    static constexpr bool h16 = false, g16 = true, cons = true;
+    static constexpr bool h16 = false, g16 = true, cons = true, comp = false;
 };
 template <> struct Form<3> {
     using R = float; using HT = __half; using GT = __half; using AT = float;
-    static constexpr bool h16 = true, g16 = true, cons = true;
+    static constexpr bool h16 = true, g16 = true, cons = true, comp = false;
 };
 template <> struct Form<4> {
     using R = float; using HT = float; using GT = float; using AT = float;
-    static constexpr bool h16 = false, g16 = false, cons = true;
+    static constexpr bool h16 = false, g16 = false, cons = true, comp = false;
+};
+template <> struct Form<5> {
+    using R = float; using HT = float; using GT = float; using AT = float;
+    static constexpr bool h16 = false, g16 = false, cons = true, comp = true;
 };
 
 template <typename T, typename R> __device__ __forceinline__ R ldr(const T* p);
@@ -266,6 +274,17 @@ __device__ __forceinline__ V cdot(int cx, int cy, V x, V y) {
 template <typename V, typename S>
 __device__ __forceinline__ V chem_pot(const Consts<S>& C, V phi, V lap_phi) {
     return V(S(4) * C.beta) * phi * (phi - V(S(1))) * (phi - V(S(0.5))) - V(C.kappa) * lap_phi;
+}
+
+// Chemical potential, Eq. 8, for phi given as an unevaluated sum hi + lo (the
+// conservative forms carry phi to about 2^-48): phi - 1 and phi - 1/2 are formed
+// from hi first, exact where they cancel (Sterbenz), then corrected by lo, so the
+// double-well term keeps FP32 relative precision in the bulk phases where it is
+// small; lap_phi is the Laplacian of hi plus that of lo.
+template <typename V, typename S>
+__device__ __forceinline__ V chem_pot2(const Consts<S>& C, V hi, V lo, V lap_phi) {
+    const V pm1 = (hi - V(S(1))) + lo, pmh = (hi - V(S(0.5))) + lo;
+    return V(S(4) * C.beta) * (hi + lo) * pm1 * pmh - V(C.kappa) * lap_phi;
 }
 
 // 3x3 neighbourhood z[dy+1][dx+1] of a field around a cell.
@@ -521,18 +540,21 @@ template <> struct MonAcc<F2> {
 };
 
 // Block reduction of the monitor sums; thread 0 writes {sum phi, kinetic
-// energy, max |u|^2, non-finite flag} to this block's slot a.mon[blockIdx.x].
-// The last block of instance `inst` to get here (arrival counter) then adds the
-// slots of all of that instance's blocks in work-list order -- thread t takes
-// items t, t + blockDim, ..., then a fixed shuffle / shared-memory tree, so the
-// sums do not depend on which block came last -- and writes the instance's
-// record: max |u|^2 becomes max |u|, plus the non-finite flag, the status word
-// and the time level. No second launch. Every thread of the block calls it.
+// energy, max |u|^2, non-finite flag} to this block's slot a.mon[item]. The
+// instance's record is then formed by a two-level tree without a second launch
+// and without many blocks queueing on one counter: the block counts itself in
+// its sub-group's counter (sub-group = its position within the instance's items
+// modulo kMonSub); the last block of a sub-group adds that sub-group's slots
+// (positions s, s + kMonSub, ... in order) into the sub-group's slot and counts
+// itself at the instance level; the last of those adds the sub-group slots in
+// order and writes the record (max |u|^2 becomes max |u|, plus the non-finite
+// flag, the status word and the time level). Every sum has a fixed order, so the
+// record does not depend on which blocks finish last.
 //
 // The group of threads doing this is a whole block (bar 0, grp 0) or one of the
 // thread groups of the batched kernel (named barrier `bar`, group `grp` < 4,
 // nthr threads, tid its index in the group); item is the work item whose slot
-// the group writes.
+// the group writes, pos its position within its instance's items.
 __device__ __forceinline__ void group_sync(int bar, int nthr) {
     if (bar == 0) {   // the whole block (a compile-time 0 wherever a kernel passes it)
         __syncthreads();
@@ -541,75 +563,98 @@ __device__ __forceinline__ void group_sync(int bar, int nthr) {
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const StepArgs& a, int inst, int item,
-                                                int tid, int nthr, int bar, int grp) {
-    __shared__ double red_all[4][4][8];   // [group][quantity][warp]: up to 8 warps a group
-    __shared__ int last_all[4];
-    double (*red)[8] = red_all[grp];
-    int& is_last = last_all[grp];
-    double v[3];
-    acc.result(v[0], v[1], v[2]);
-    const int lane = tid & 31, warp = tid >> 5;
-    const int nwarps = nthr >> 5;
+// Sums (max for q = 2) of four quantities over a group, fixed tree; result in
+// thread 0's v. red: the group's [4][8] shared scratch.
+__device__ __forceinline__ void group_reduce4(double v[4], int tid, int nthr, int bar, double (*red)[8]) {
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
         v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
         v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+        v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
     }
-    if (lane == 0) { red[0][warp] = v[0]; red[1][warp] = v[1]; red[2][warp] = v[2]; }
+    group_sync(bar, nthr);   // red[] may still be read by an earlier use
+    if (lane == 0) { red[0][warp] = v[0]; red[1][warp] = v[1]; red[2][warp] = v[2]; red[3][warp] = v[3]; }
     group_sync(bar, nthr);
+    if (tid == 0)
+        for (int w = 1; w < nwarps; ++w) {
+            v[0] += red[0][w];
+            v[1] += red[1][w];
+            v[2] = fmax(v[2], red[2][w]);
+            v[3] += red[3][w];
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const StepArgs& a, int inst, int item,
+                                                int pos, int tid, int nthr, int bar, int grp) {
+    __shared__ double red_all[4][4][8];   // [group][quantity][warp]: up to 8 warps a group
+    __shared__ int flag_all[4];
+    double (*red)[8] = red_all[grp];
+    int& flag = flag_all[grp];
+    double v[4];
+    acc.result(v[0], v[1], v[2]);
+    v[3] = 0.0;
+    group_reduce4(v, tid, nthr, bar, red);
     const int* idx = a.mon_csr + a.mon_n + 1;
     const int first = a.mon_csr[inst], items = a.mon_csr[inst + 1] - first;
+    const int nsub = items < kMonSub ? items : kMonSub;
+    const int s = pos % kMonSub;
+    const int in_sub = (items - s + kMonSub - 1) / kMonSub;   // positions s, s + kMonSub, ...
+    int* cnt = a.mon_count + (long long)inst * (kMonSub + 1) * kCounterStride;
     if (tid == 0) {
-        double m = red[0][0], k = red[1][0], u = red[2][0];
-        for (int w = 1; w < nwarps; ++w) { m += red[0][w]; k += red[1][w]; u = fmax(u, red[2][w]); }
         double* out = a.mon + (long long)item * kMonQ;
-        out[0] = m;
-        out[1] = k;
-        out[2] = u;
-        out[3] = (isfinite(m) && isfinite(k)) ? 0.0 : 1.0;
+        out[0] = v[0];
+        out[1] = v[1];
+        out[2] = v[2];
+        out[3] = (isfinite(v[0]) && isfinite(v[1])) ? 0.0 : 1.0;
         __threadfence();                                  // the slot before the count
-        is_last = atomicAdd(a.mon_count + inst, 1) == items - 1;
+        flag = atomicAdd(cnt + s * kCounterStride, 1) == in_sub - 1;
     }
     group_sync(bar, nthr);
-    if (!is_last) return;
+    if (!flag) return;
     __threadfence();                                      // the count before the slots
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < items; j += nthr) {
-        const double* p = a.mon_all + (long long)idx[first + j] * kMonQ;
-        s[0] += __ldcg(p);
-        s[1] += __ldcg(p + 1);
-        s[2] = fmax(s[2], __ldcg(p + 2));
-        s[3] += __ldcg(p + 3);
+    // the sub-group's slots, in order
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < in_sub; j += nthr) {
+        const double* p = a.mon_all + (long long)idx[first + s + j * kMonSub] * kMonQ;
+        w[0] += __ldcg(p);
+        w[1] += __ldcg(p + 1);
+        w[2] = fmax(w[2], __ldcg(p + 2));
+        w[3] += __ldcg(p + 3);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s[0] += __shfl_down_sync(0xffffffffu, s[0], o);
-        s[1] += __shfl_down_sync(0xffffffffu, s[1], o);
-        s[2] = fmax(s[2], __shfl_down_sync(0xffffffffu, s[2], o));
-        s[3] += __shfl_down_sync(0xffffffffu, s[3], o);
-    }
-    group_sync(bar, nthr);                                // red[] is reused
-    if (lane == 0) { red[0][warp] = s[0]; red[1][warp] = s[1]; red[2][warp] = s[2]; red[3][warp] = s[3]; }
-    group_sync(bar, nthr);
+    group_reduce4(w, tid, nthr, bar, red);
     if (tid == 0) {
-        for (int w = 1; w < nwarps; ++w) {
-            s[0] += red[0][w];
-            s[1] += red[1][w];
-            s[2] = fmax(s[2], red[2][w]);
-            s[3] += red[3][w];
+        double* sub = a.mon_sub + ((long long)inst * kMonSub + s) * kMonQ;
+        sub[0] = w[0];
+        sub[1] = w[1];
+        sub[2] = w[2];
+        sub[3] = w[3];
+        cnt[s * kCounterStride] = 0;                      // ready for the next monitored step
+        __threadfence();
+        if (atomicAdd(cnt + kMonSub * kCounterStride, 1) == nsub - 1) {
+            __threadfence();
+            // the instance's record from its sub-group slots, in order
+            double m = 0.0, e = 0.0, u = 0.0, f = 0.0;
+            const double* sb = a.mon_sub + (long long)inst * kMonSub * kMonQ;
+            for (int q = 0; q < nsub; ++q) {
+                m += __ldcg(sb + q * kMonQ);
+                e += __ldcg(sb + q * kMonQ + 1);
+                u = fmax(u, __ldcg(sb + q * kMonQ + 2));
+                f += __ldcg(sb + q * kMonQ + 3);
+            }
+            MonRecord r;
+            r.sum_phi = m;
+            r.kinetic_energy = e;
+            r.max_u = sqrt(u);
+            r.nonfinite = f != 0.0 ? 1 : 0;
+            r.device_status = *(volatile int*)a.status;
+            r.time = a.mon_step + a.time_base[inst];
+            a.mon_rec[inst] = r;
+            if (a.mon_host) a.mon_host[inst] = r;         // caller's pinned host record, written from here
+            cnt[kMonSub * kCounterStride] = 0;
         }
-        MonRecord& r = a.mon_rec[inst];
-        r.sum_phi = s[0];
-        r.kinetic_energy = s[1];
-        r.max_u = sqrt(s[2]);
-        r.nonfinite = s[3] != 0.0 ? 1 : 0;
-        r.device_status = *(volatile int*)a.status;
-        r.time = a.mon_step + a.time_base[inst];
-        if (a.mon_host) a.mon_host[inst] = r;             // caller's pinned host record, written from here
-        a.mon_count[inst] = 0;                            // ready for the next monitored step
     }
 }
 
@@ -947,7 +992,7 @@ __global__ void __launch_bounds__(TX, StepOcc<FORM, TX>::value) step_kernel(cons
         __syncthreads();
         collide_row(Y, g, pux, puy);
     }
-    if constexpr (MON) mon_block_store(mon, a, wk.inst, blockIdx.x, threadIdx.x, TX, 0, 0);
+    if constexpr (MON) mon_block_store(mon, a, wk.inst, blockIdx.x, wk.pad, threadIdx.x, TX, 0, 0);
 }
 
 }  // namespace lbm

@@ -33,7 +33,8 @@ struct DevInst {
 // One thread block's work: a strip of columns [x0, x0 + TX) (clipped to nx) of
 // one instance, marching over nrows rows from ystart in direction dir (+1/-1).
 struct WorkItem {
-    int inst, x0, ystart, nrows, dir, pad;
+    int inst, x0, ystart, nrows, dir, pad;   // pad: D2Q9, the item's position within its
+                                             // instance's items; D3Q15, the tile's y0
 };
 
 // A block's share of the batched step (step_kernel_x2_batched): two work items
@@ -55,12 +56,15 @@ struct StepArgs {
     const WorkItem* work;
     int* status;                        // device status word (0 = ok), see kStatusTimeout
     double* mon;                        // monitor: kMonQ doubles per block of this launch
-    // Per-step monitor, final reduction (kernels with the monitor only): after
-    // storing its slot a block counts itself in mon_count[instance]; the last
-    // block of an instance adds that instance's slots in work-list order and
-    // writes its record, then sets the counter back to zero.
+    // Per-step monitor, final reduction (kernels with the monitor only), a
+    // two-level tree: a block stores its slot and counts itself in the counter
+    // of its sub-group (its position within the instance's items modulo
+    // kMonSub); the last block of a sub-group adds the sub-group's slots into a
+    // sub-slot and counts itself at the instance level; the last of those adds
+    // the sub-slots and writes the record. Counters go back to zero as used.
     double* mon_all;                    // slots of every work item of the plan
-    int* mon_count;                     // per instance: blocks of this step done
+    double* mon_sub;                    // kMonSub sub-slots (kMonQ doubles) per instance
+    int* mon_count;                     // per instance: kMonSub + 1 counters, kCounterStride ints apart
     const int* mon_csr;                 // per instance k: items idx[csr[k] .. csr[k+1]) (idx at csr + n + 1)
     int mon_n;                          // instances
     struct MonRecord* mon_rec;          // one record per instance
@@ -84,6 +88,11 @@ struct MonRecord {
 // Doubles a block of a monitored step writes: sum phi, kinetic energy,
 // max |u|^2, non-finite flag.
 constexpr int kMonQ = 4;
+// Sub-groups of an instance's blocks in the monitor's reduction tree, and the
+// spacing of its counters (one 128-byte line each: the atomics of different
+// counters do not queue on one address).
+constexpr int kMonSub = 8;
+constexpr int kCounterStride = 32;
 
 // Value a kernel writes to the status word when a bounded device wait runs out
 // (equal to LBM_ETIMEOUT of include/lbm.h).

@@ -276,6 +276,23 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
             n.z[dy][2] = F2(b2.y, c2.x);
         }
     };
+    // 3x3 neighbourhood of the low parts of phi around the pair at ring index j
+    // of row M, from the h_0 pair slots of rows M - 1, M, M + 1 (all three are in
+    // the slot window when mu of M is formed; a ghost row beyond a wall is its
+    // mirror, the row next to it)
+    auto lo_nbr = [&](int M, int j, Nbr<F2>& n) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const int r = M - 1 + dy;
+            const float2* s2 = hpairs(ghost(r) ? mirror(r) : r);
+            const float4 a4 = *reinterpret_cast<const float4*>(&s2[j - 2]);   // cells j-2, j-1
+            const float4 b4 = *reinterpret_cast<const float4*>(&s2[j]);       // cells j, j+1
+            const float4 c4 = *reinterpret_cast<const float4*>(&s2[j + 2]);   // cells j+2, j+3
+            n.z[dy][0] = F2(a4.w, b4.y);
+            n.z[dy][1] = F2(b4.y, b4.w);
+            n.z[dy][2] = F2(b4.w, c4.y);
+        }
+    };
     // B. mu of row M (Eq. 8 with the Laplacian of Eq. 30b), same column pairs.
     auto mu_row = [&](int M) {
         float* dst = mrow(M);
@@ -290,7 +307,13 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
             const int j = 2 + 2 * q;
             Nbr<F2> n;
             nbr_pair(r0, r1, r2, j, n);
-            st_pair(dst + j, chem_pot(C, n.z[1][1], n.lap()));
+            if constexpr (F::comp) {   // compensated: phi = hi + lo
+                Nbr<F2> nl;
+                lo_nbr(M, j, nl);
+                st_pair(dst + j, chem_pot2(C, n.z[1][1], nl.z[1][1], n.lap() + nl.lap()));
+            } else {
+                st_pair(dst + j, chem_pot(C, n.z[1][1], n.lap()));
+            }
         };
         if (q0) column(tid);
         if (q1) column(tid + TX);
@@ -315,7 +338,7 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
         if constexpr (F::cons) {
             const float4 l4 = *reinterpret_cast<const float4*>(&hpairs(Y)[jX]);
             lo = F2(l4.y, l4.w);
-            h[0] = lo;
+            h[0] = lo;   // (not stored: the conservative h_0 is formed after the collision)
         }
 #pragma unroll
         for (int i = F::cons ? 1 : 0; i < 9; ++i) h[i] = ld_pair(hplane(Y, i) + jX);   // as stored
@@ -393,11 +416,18 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
     p_row(Y0 - d);
     p_row(Y0);
     group_sync(bar, TX);
-    // the slot of row Y0 - 2d (read only above) takes the first lead row
-    prefetch(Y0 + 2 * d, Y0 + d);
     mu_row(Y0);
     mu_row(Y0 - d);
-    group_sync(bar, TX);
+    if constexpr (F::comp) {
+        // mu of row Y0 - d read the low parts of phi from the h slot of row
+        // Y0 - 2d: every thread must be done with it before it is refilled
+        group_sync(bar, TX);
+        prefetch(Y0 + 2 * d, Y0 + d);   // the slot of row Y0 - 2d takes the first lead row
+    } else {
+        // (issued before the barrier: the slot of row Y0 - 2d was read only above)
+        prefetch(Y0 + 2 * d, Y0 + d);
+        group_sync(bar, TX);
+    }
     for (int k = 0; k < wk.nrows; ++k) {
         const int Y = Y0 + k * d;
         // g and phi*u of the collision pair, loaded before the barriers
@@ -425,7 +455,7 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
         group_sync(bar, TX);
         collide_row(Y, g, pux, puy);
     }
-    if constexpr (MON) mon_block_store(mon, a, wk.inst, item, tid, TX, bar, grp);
+    if constexpr (MON) mon_block_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp);
 }
 
 template <int FORM, int TX, bool MON = false>

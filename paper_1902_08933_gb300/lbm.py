@@ -26,7 +26,7 @@ LBM_IM, LBM_QIM = 0, 1
 LBM_P_MODIFIED_PRINTED, LBM_P_MODIFIED_LITERAL, LBM_P_PREVIOUS = 0, 1, 2
 LBM_FS_MU_GRADPHI, LBM_FS_PHI_GRADMU = 0, 1
 LBM_VISC_INV_LINEAR, LBM_VISC_STEP = 0, 1
-LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C = 0, 1, 2, 3, 4
+LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C, LBM_F32_CC = 0, 1, 2, 3, 4, 5
 LBM_PIPELINE_AUTO, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC, LBM_PIPELINE_TMA, LBM_PIPELINE_PAIRS = 0, 1, 2, 3, 4
 LBM_PIPELINE_BATCHED = 5
 VARIANTS = {0: "plain", 1: "async", 2: "tma", 3: "pairs", 4: "batched"}
@@ -34,9 +34,9 @@ FIELDS = ("phi", "ux", "uy", "p", "rho", "mu", "P")
 FIELDS3 = FIELDS + ("uz",)          # D3Q15 lattices (nz >= 2) also have uz
 FIELD_BITS = {name: 1 << k for k, name in enumerate(FIELDS3)}
 FORMS = {"f64": LBM_F64, "f32": LBM_F32, "f32_g16": LBM_F32_G16, "f32_h16": LBM_F32_H16,
-         "f32_c": LBM_F32_C}
+         "f32_c": LBM_F32_C, "f32_cc": LBM_F32_CC}
 # bytes moved per lattice update (every population read and written once, plus phi*u, p)
-BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176}
+BYTES_PER_LUP = {"f64": 336, "f32": 168, "f32_g16": 140, "f32_h16": 108, "f32_c": 176, "f32_cc": 176}
 
 _STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
            5: "LBM_ETIMEOUT", 6: "LBM_ESTATE", 7: "LBM_EIO"}

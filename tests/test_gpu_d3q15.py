@@ -199,9 +199,9 @@ def test_d3q15_context_rules(L):
     c3 = wl.static_droplet3(8, R=2.0)
     with pytest.raises(L.LbmError):
         L.Simulation([c2, c3], "f64")                   # one lattice a context
-    for form in ("f32_g16", "f32_h16"):
+    for form in ("f32_g16", "f32_h16", "f32_cc"):
         with pytest.raises(L.LbmError):
-            L.Simulation([c3], form)                    # FP16 storage is D2Q9 only
+            L.Simulation([c3], form)                    # FP16 storage and compensated mu: D2Q9 only
     with L.Simulation([c3], "f64", phi0=[wl.initial_phi(c3)]) as sim:
         with pytest.raises(L.LbmError):
             L.lbm_set_monitor(sim.ctx, True)

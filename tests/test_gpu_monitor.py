@@ -7,7 +7,7 @@ import pytest
 from paper_1902_08933_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
-FORMS = ["f64", "f32", "f32_c", "f32_g16", "f32_h16"]
+FORMS = ["f64", "f32", "f32_c", "f32_cc", "f32_g16", "f32_h16"]
 
 
 @pytest.fixture(scope="module")

@@ -177,12 +177,16 @@ def test_bubble_1024x4096_first_steps(L, orc, report):
     with L.Simulation(cfg, "f64", phi0=[phi0]) as sim:
         sim.step(n)
         compare(sim, 0, ref, st, 1e-10, pops=False, report=report, tag="f64_")
-    for form in ("f32", "f32_c", "f32_g16", "f32_h16"):
+    # Bars about three times the errors measured on GB300 (field-max normalised,
+    # 20 steps): f32 phi 6.6e-7, u 7.0e-4, p 2.4e-3; f32_c 7.8e-8, 2.4e-4,
+    # 8.2e-4; f32_cc (compensated mu) 1.6e-9, 9.5e-6, 1.3e-5; FP16 g / h
+    # 6.2e-8 / 8.5e-8, 5.7e-4, 9.8e-4.
+    bars = {"f32": (tol32_phi(n), 7.5e-3), "f32_c": (tol32_phi(n), 2.5e-3), "f32_cc": (1e-8, 5e-5),
+            "f32_g16": (tol32_phi(n), 3e-3), "f32_h16": (3e-7, 3e-3)}
+    for form, (phi_tol, up_tol) in bars.items():
         with L.Simulation(cfg, form, phi0=[phi0]) as sim:
             sim.step(n)
-            check_reduced(sim, ref, n, report, form + "_",
-                          phi_tol=tol32_phi(n) if form in ("f32", "f32_c", "f32_g16") else 1e-3,
-                          up_tol=2e-2 if form in ("f32", "f32_c") else 0.1)
+            check_reduced(sim, ref, n, report, form + "_", phi_tol=phi_tol, up_tol=up_tol)
 
 
 def test_batched_instances_match_oracle(L, orc):
@@ -201,7 +205,7 @@ def test_phi_conserved_all_forms(L, report):
     cfg = wl.rising_bubble(nx=256, ny=512, R=32, cy=128, W=4.0, Re=20.0)
     phi0 = wl.initial_phi(cfg)
     n = 500
-    bounds = {"f64": 1e-13, "f32": n * 2.0 ** -24, "f32_c": 1e-9, "f32_g16": 1e-9,
+    bounds = {"f64": 1e-13, "f32": n * 2.0 ** -24, "f32_c": 1e-9, "f32_cc": 1e-9, "f32_g16": 1e-9,
               "f32_h16": 1e-9}
     for form, tol in bounds.items():
         with L.Simulation(cfg, form, phi0=[phi0]) as sim:

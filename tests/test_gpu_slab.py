@@ -35,7 +35,7 @@ def _case(name):
     return cfg, phi0
 
 
-@pytest.mark.parametrize("form", ["f64", "f32", "f32_c", "f32_g16", "f32_h16"])
+@pytest.mark.parametrize("form", ["f64", "f32", "f32_c", "f32_cc", "f32_g16", "f32_h16"])
 @pytest.mark.parametrize("case,world,ghost", [("bubble", 2, 3), ("bubble", 4, 9), ("droplet", 3, 6)])
 def test_slabs_in_one_context_equal_undivided(L, form, case, world, ghost):
     import torch
