@@ -53,13 +53,18 @@ def test_autotune_leaves_state_and_time_untouched(L):
         assert [L.lbm_time(sim.ctx, k) for k in range(2)] == t0
         m1 = L.lbm_read_monitor(sim.ctx, 0)      # the last record is still the one before
         assert m1["time"] == m0["time"] and m1["sum_phi"] == m0["sum_phi"]
-        # and the run continues exactly like an untuned one
+        # and the run continues exactly like an untuned one switched to the same
+        # shape at that point (load paths may round differently: one cell a
+        # thread or two in packed FP32)
         sim.step(6)
         tuned = [sim.populations(k) for k in range(2)]
+    pipes = {"auto": 0, "plain": 1, "async": 2, "tma": 3, "pairs": 4, "batched": 5}
     with L.Simulation(cfgs, "f32_c", phi0=[wl.initial_phi(c) for c in cfgs]) as ref:
         ref.step(13)
         L.lbm_set_monitor(ref.ctx, True)
         ref.step(1)
+        L.lbm_set_pipeline(ref.ctx, pipes[shape["pipeline"]])
+        L.lbm_set_launch(ref.ctx, shape["tile_x"], shape["rows"])
         ref.step(6)
         plain = [ref.populations(k) for k in range(2)]
     for (ha, ga), (hb, gb) in zip(tuned, plain):
