@@ -171,9 +171,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PIPE_OPS_PER_S = 152 * 2 * 2.07e9
 
 
-def fp64_roofline(mlups):
+def fp64_roofline(mlups, measured_tflops=None):
     """ALU roofline of the FP64 form from the FP64 operation counts per lattice
-    update in the committed ncu summary (None if absent)."""
+    update in the committed ncu summary (None if absent), against the FP64 FMA
+    throughput measured on this GPU (lbm_measure_fp64_fma), else the nominal."""
     path = os.path.join(ROOT, "profiles", "step_kernel_f64_bubble_1024x4096.md")
     if not os.path.exists(path):
         return None
@@ -183,9 +184,12 @@ def fp64_roofline(mlups):
     if not flop or not inst:
         return None
     achieved = float(flop.group(1)) * mlups * 1e6 / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
-            "fp64_pipe_frac": float(inst.group(1)) * mlups * 1e6 / FP64_PIPE_OPS_PER_S}
+    peak = measured_tflops if measured_tflops else FP64_PEAK_TFLOPS
+    kind = ("measured: independent FP64 FMA chains on every SM (lbm_measure_fp64_fma)" if measured_tflops
+            else "nominal: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_kind": kind, "nominal_peak": FP64_PEAK_TFLOPS,
+            "fp64_pipe_frac": float(inst.group(1)) * mlups * 1e6 / (peak * 1e12 / 2)}
 
 
 def rel_err(a, b):
@@ -504,6 +508,7 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
     acc_steps = 200
     ref = None
     forms = {}
+    fp64_peak = lbm.lbm_measure_fp64_fma(stream.cuda_stream)
     for form in ("f64", "f32", "f32_c", "f32_cc", "f32_g16", "f32_h16"):
         with lbm.Simulation(cfg, form, stream=stream.cuda_stream, phi0=[phi0]) as sim:
             sim.step(acc_steps)
@@ -518,7 +523,7 @@ def side_legs(args, lbm, wl, cfg, phi0, stream, hbm_peak):
                            "frac_hbm_algorithmic": ALGO_BYTES_PER_LUP[form] * cells / (ms * 1e-3 / K) / 1e9 / hbm_peak,
                            "steps": K, "launch_shape": shape,
                            "kernel": lbm.lbm_launch_info(sim.ctx, 0)["variant"],
-                           "roofline": fp64_roofline(mlups) if form == "f64" else
+                           "roofline": fp64_roofline(mlups, fp64_peak) if form == "f64" else
                            {"bound": "hbm", "frac": gbs / hbm_peak},
                            "err_vs_f64_after_%d_steps" % acc_steps: (
                                None if form == "f64" else

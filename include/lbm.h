@@ -409,6 +409,15 @@ int64_t lbm_time(const lbm_ctx* ctx, int instance);
 lbm_status lbm_reduce_fields_noalloc(const double* fields_device, int nx, int ny,
                                      void* cuda_stream, double* out_device);
 
+/* Calibration (the paper has no counterpart): the FP64 fused multiply-add
+ * throughput of the current device in TFLOP/s (an FMA counted as two), measured
+ * with a kernel of independent FMA chains on every SM (about 10 ms, after one
+ * warm-up launch, CUDA events on cuda_stream; NULL: the default stream). It is
+ * the peak against which the FP64 storage form's step, bound by the FP64 pipe,
+ * is measured. Allocates and frees a small device buffer; synchronises.
+ * Errors: LBM_EINVAL (NULL tflops), LBM_ECUDA. */
+lbm_status lbm_measure_fp64_fma(void* cuda_stream, double* tflops);
+
 /* Failure-detection check (the paper has no counterpart; this is library
  * infrastructure). Queues on the context's stream one single-thread kernel that
  * arms a transaction mbarrier for 16 bytes no copy will deliver and waits on it

@@ -116,6 +116,7 @@ SIGNATURES = [
     ("lbm_autotune", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("lbm_autotune_shape", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_launch_shape)]),
     ("lbm_row_bytes", ctypes.c_size_t, [_VP, ctypes.c_int]),
+    ("lbm_measure_fp64_fma", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     ("lbm_pack_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t]),
     ("lbm_unpack_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t]),
     ("lbm_launches_per_step", ctypes.c_int, [_VP]),
@@ -286,6 +287,13 @@ def lbm_autotune(ctx):
     t, r = ctypes.c_int(), ctypes.c_int()
     _check(library().lbm_autotune(ctx, ctypes.byref(t), ctypes.byref(r)), ctx)
     return t.value, r.value
+
+
+def lbm_measure_fp64_fma(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(library().lbm_measure_fp64_fma(_VP(stream or 0), ctypes.byref(t)))
+    return t.value
 
 
 def lbm_row_bytes(ctx, instance: int) -> int:

@@ -28,6 +28,7 @@ int main(void) {
     if (lbm_sp_create(&sp, LBM_F64, 0, &sctx) != LBM_EINVAL || sctx != 0) return 3;
     if (lbm_step(0, 1) != LBM_EINVAL || lbm_sp_step(0, 1) != LBM_EINVAL) return 4;
     if (lbm_autotune_shape(0, 0, 0) != LBM_EINVAL) return 5;
+    if (lbm_measure_fp64_fma(0, 0) != LBM_EINVAL) return 6;
     lbm_destroy(0);
     lbm_sp_destroy(0);
     printf("ok %d %d %d %d\n", (int)sizeof(lbm_params), (int)sizeof(lbm_sp_params),
