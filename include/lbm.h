@@ -431,6 +431,21 @@ lbm_status lbm_measure_fp64_fma(void* cuda_stream, double* tflops);
  * rounds out of range), LBM_ECUDA (launch failed). */
 lbm_status lbm_inject_wait_timeout(lbm_ctx* ctx, int rounds);
 
+/* Failure-detection check of the batched launch's own wait (library
+ * infrastructure, as above). In a context whose plan is the batched launch
+ * (LBM_PIPELINE_BATCHED, or LBM_PIPELINE_AUTO with several instances that all
+ * take the paired kernel), queues one launch of two steps in which every work
+ * item of the second step waits for one finished item more than its instance
+ * has: the first step runs, each wait of the second gives up after `rounds`
+ * rounds (1 <= rounds <= 2^21), records a timeout in the status word, stops the
+ * launch handing out work and skips its item. Nothing faults or hangs and the
+ * CUDA context stays usable; the state is then suspect, the time levels are not
+ * advanced, and lbm_sync, lbm_get_fields and lbm_diagnostics return
+ * LBM_ETIMEOUT until lbm_load restores a checkpoint. Asynchronous. Errors:
+ * LBM_EINVAL (NULL context, rounds out of range), LBM_ESTATE (an instance not
+ * initialised, or the plan is not the batched launch), LBM_ECUDA. */
+lbm_status lbm_inject_batched_wait_timeout(lbm_ctx* ctx, int rounds);
+
 /* Waits for all queued work. Returns LBM_ECUDA if it failed, LBM_ETIMEOUT if a
  * bounded device wait of the step kernel ran out (the state is then suspect;
  * the status stays set until lbm_load replaces the whole state). lbm_get_fields

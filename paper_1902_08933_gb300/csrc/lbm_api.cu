@@ -139,6 +139,12 @@ struct lbm_ctx {
     std::vector<char> ready;
     long long S = 0, max_cells = 0;
     DevInst* d_inst = nullptr;
+    // The two buffer sets (time levels) of h, h_0, g and p, in one allocation:
+    // set b at state + b * set_bytes, each array at the same offset in both, so
+    // that one signed byte offset takes every array to the other set (what the
+    // batched launch's odd steps add, see StepArgs::set_delta).
+    void* state = nullptr;
+    long long set_bytes = 0;
     void* h[2] = {nullptr, nullptr};
     void* h0[2] = {nullptr, nullptr};     // conservative forms: h_0 as float2
     void* g[2] = {nullptr, nullptr};
@@ -158,7 +164,8 @@ struct lbm_ctx {
     // and the queue counters the kernel takes them with
     lbm::BlockDesc* d_desc = nullptr;
     int ndesc = 0;
-    int* d_queue = nullptr;
+    int* d_queue = nullptr;        // batched queue: next, blocks finished, abort
+    int* d_done = nullptr;         // batched: items finished a launch, per instance
     bool plan_dirty = true;
     // CUDA graph of 2 * graph_pairs steps starting from cur == 0 (built on first use,
     // dropped when the plan changes)
@@ -218,6 +225,7 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.phiu = c->phiu;
     a.p_in = c->p[in];
     a.p_out = c->p[1 - in];
+    a.set_delta = in == 0 ? c->set_bytes : -c->set_bytes;
     a.S = c->S;
     a.inst = c->d_inst;
     a.work = nullptr;
@@ -234,6 +242,12 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.desc = c->d_desc;
     a.ndesc = c->ndesc;
     a.queue = c->d_queue;
+    a.done = c->d_done;
+    a.items_csr = c->d_mon_csr;
+    a.ninst = c->n;
+    a.nsteps = 1;
+    a.wait_limit = lbm::kWaitLimit;
+    a.wait_extra = 0;
     a.mon_host = nullptr;
     return a;
 }
@@ -416,63 +430,96 @@ lbm_status plan(lbm_ctx* c) {
     return finish_plan(c);
 }
 
-// Batched plan: the paired kernel's work items of every instance -- strips of
-// 128 columns (the batched kernel's group width; narrower instances take one
-// strip), runs of rows with alternating directions -- paired into block
-// descriptors (items of equal run length together) and sorted by run length,
-// longest first, so the queue hands out the long descriptors first and the
-// short ones fill the tail. Run length: about four descriptors per resident
-// block, unless set by lbm_set_launch (its strip width does not apply here).
+// Batched plan: the paired kernel's work items of every instance, runs of rows
+// with alternating directions. Instances wider than 128 columns are cut into
+// strips of 256 (wide items: one a block descriptor, all 128 threads on it --
+// the strip width of the one-instance launch, measured 12 % faster than 128 on
+// the 512 mixed instances); narrower instances, and a last strip of at most 128
+// columns, are narrow items, paired into descriptors (items of equal run length
+// together). The descriptors are sorted by run length, longest first, so the
+// queue hands out the long ones first and the short ones fill the tail. Run
+// length: about one descriptor per resident block a step, at most 64 rows,
+// unless set by lbm_set_launch (its strip width does not apply here) -- long
+// runs re-read fewer halo rows, and the tail of a step is hidden by the next
+// step's items of the instances already done (several steps a launch): on the
+// 512 mixed instances 64-row runs beat 32 by 4 % (FP32) and 16 by 12 %.
 lbm_status plan_batched(lbm_ctx* c, bool, bool, bool, int sms) {
     int occ = 1;
     by_form(c->form, [&](auto F) {
         occ = std::max(1, lbm::batched_occupancy_t<decltype(F)::value>());
         return cudaSuccess;
     });
-    constexpr int kStrip = 128;
+    constexpr int kWideStrip = 256, kNarrowStrip = 128;
+    // strips of one instance: (x0, width) with width > kNarrowStrip for wide ones
+    auto strips_of = [&](const lbm_params& p) {
+        std::vector<std::pair<int, int>> v;
+        for (int x0 = 0; x0 < p.nx;) {
+            const int w = p.nx - x0 > kNarrowStrip ? std::min(kWideStrip, p.nx - x0) : p.nx - x0;
+            v.push_back({x0, w});
+            x0 += w;
+        }
+        return v;
+    };
     int rows = c->rows_req;
     if (rows <= 0) {
-        double group_rows = 0;
-        for (const lbm_params& p : c->params) group_rows += (double)((p.nx + kStrip - 1) / kStrip) * p.ny;
-        rows = (int)std::lround(group_rows / (2.0 * 4.0 * sms * occ));
+        double block_rows = 0;   // rows of whole blocks: a narrow item is half a block
+        for (const lbm_params& p : c->params)
+            for (const auto& sw : strips_of(p)) block_rows += (sw.second > kNarrowStrip ? 1.0 : 0.5) * p.ny;
+        rows = (int)std::lround(block_rows / (1.0 * sms * occ));
         rows = std::max(8, std::min(64, rows));
     }
-    std::vector<WorkItem> items;
+    std::vector<WorkItem> wide, narrow;
     for (int k = 0; k < c->n; ++k) {
         const lbm_params& p = c->params[k];
         const int r = std::min(rows, p.ny);
-        const int strips = (p.nx + kStrip - 1) / kStrip, nchunks = (p.ny + r - 1) / r;
-        for (int st = 0; st < strips; ++st)
+        const int nchunks = (p.ny + r - 1) / r;
+        for (const auto& sw : strips_of(p))
             for (int ch = 0; ch < nchunks; ++ch) {
                 const int y0 = ch * r, y1 = std::min(p.ny, y0 + r);
                 WorkItem w;
                 w.inst = k;
-                w.x0 = st * kStrip;
+                w.x0 = sw.first;
                 w.nrows = y1 - y0;
                 w.dir = (ch % 2 == 0) ? -1 : 1;
                 w.ystart = w.dir < 0 ? y1 - 1 : y0;
                 w.pad = 0;
-                items.push_back(w);
+                (sw.second > kNarrowStrip ? wide : narrow).push_back(w);
             }
     }
-    std::stable_sort(items.begin(), items.end(), [](const WorkItem& x, const WorkItem& y) { return x.nrows > y.nrows; });
-    c->work = items;
+    auto longer = [](const WorkItem& x, const WorkItem& y) { return x.nrows > y.nrows; };
+    std::stable_sort(narrow.begin(), narrow.end(), longer);
+    c->work = wide;
+    c->work.insert(c->work.end(), narrow.begin(), narrow.end());
     std::vector<lbm::BlockDesc> host;
-    for (int j = 0; j < (int)items.size(); j += 2) {
-        lbm::BlockDesc d;
-        d.item[0] = j;
-        d.item[1] = j + 1 < (int)items.size() ? j + 1 : -1;
-        host.push_back(d);   // items sorted by run length: so are the descriptors
+    std::vector<int> len;
+    for (int j = 0; j < (int)wide.size(); ++j) {
+        host.push_back({{j, lbm::kDescWide}});
+        len.push_back(wide[j].nrows);
+    }
+    const int nw = (int)wide.size(), nn = (int)narrow.size();
+    for (int j = 0; j < nn; j += 2) {
+        host.push_back({{nw + j, j + 1 < nn ? nw + j + 1 : -1}});
+        len.push_back(narrow[j].nrows);   // the longer of the two
+    }
+    std::vector<int> order(host.size());
+    for (int i = 0; i < (int)order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return len[x] > len[y]; });
+    {
+        std::vector<lbm::BlockDesc> sorted;
+        for (int i : order) sorted.push_back(host[i]);
+        host.swap(sorted);
     }
     c->ndesc = (int)host.size();
     c->launches.clear();
-    c->launches.push_back({kStrip, 0, (int)std::min<long long>(c->ndesc, (long long)sms * occ), lbm::kBatched});
+    c->launches.push_back({kNarrowStrip, 0, (int)std::min<long long>(c->ndesc, (long long)sms * occ), lbm::kBatched});
     cudaFree(c->d_desc);
     c->d_desc = nullptr;
     LBM_CK(c, cudaMalloc(&c->d_desc, host.size() * sizeof(lbm::BlockDesc)));
     LBM_CK(c, cudaMemcpy(c->d_desc, host.data(), host.size() * sizeof(lbm::BlockDesc), cudaMemcpyHostToDevice));
-    if (!c->d_queue) LBM_CK(c, cudaMalloc(&c->d_queue, 2 * sizeof(int)));
-    LBM_CK(c, cudaMemset(c->d_queue, 0, 2 * sizeof(int)));
+    if (!c->d_queue) LBM_CK(c, cudaMalloc(&c->d_queue, 4 * sizeof(int)));
+    LBM_CK(c, cudaMemset(c->d_queue, 0, 4 * sizeof(int)));
+    if (!c->d_done) LBM_CK(c, cudaMalloc(&c->d_done, (size_t)c->n * sizeof(int)));
+    LBM_CK(c, cudaMemset(c->d_done, 0, (size_t)c->n * sizeof(int)));
     return finish_plan(c);
 }
 
@@ -625,12 +672,7 @@ lbm_status ensure_out(lbm_ctx* c, size_t cells) {
 }
 
 void release(lbm_ctx* c) {
-    for (int b = 0; b < 2; ++b) {
-        cudaFree(c->h[b]);
-        cudaFree(c->h0[b]);
-        cudaFree(c->g[b]);
-        cudaFree(c->p[b]);
-    }
+    cudaFree(c->state);
     cudaFree(c->phiu);
     cudaFree(c->sc.phi);
     cudaFree(c->sc.mu);
@@ -639,6 +681,7 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_work);
     cudaFree(c->d_desc);
     cudaFree(c->d_queue);
+    cudaFree(c->d_done);
     cudaFree(c->d_tmp);
     cudaFree(c->d_out);
     cudaFree(c->d_partials);
@@ -727,13 +770,22 @@ lbm_status lbm_create(const lbm_params* params, int n_instances, int precision, 
     };
     auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
     const size_t S = (size_t)c->S;
-    for (int b = 0; b < 2; ++b) {
-        if ((e = alloc(&c->h[b], h_planes(precision, c->q) * S * h_elem(precision))) != cudaSuccess ||
-            (e = alloc(&c->g[b], c->q * S * g_elem(precision))) != cudaSuccess ||
-            (e = alloc(&c->p[b], S * a_elem(precision))) != cudaSuccess)
+    {
+        auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t hb = up(h_planes(precision, c->q) * S * h_elem(precision));
+        const size_t h0b = conservative(precision) ? up(S * 2 * sizeof(float)) : 0;
+        const size_t gb = up(c->q * S * g_elem(precision));
+        const size_t pb = up(S * a_elem(precision));
+        c->set_bytes = (long long)(hb + h0b + gb + pb);
+        if ((e = alloc(&c->state, 2 * (size_t)c->set_bytes)) != cudaSuccess)
             return cleanup(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
-        if (conservative(precision) && (e = alloc(&c->h0[b], S * 2 * sizeof(float))) != cudaSuccess)
-            return cleanup(LBM_ENOMEM);
+        for (int b = 0; b < 2; ++b) {
+            char* set = static_cast<char*>(c->state) + b * c->set_bytes;
+            c->h[b] = set;
+            c->h0[b] = h0b ? set + hb : nullptr;
+            c->g[b] = set + hb + h0b;
+            c->p[b] = set + hb + h0b + gb;
+        }
     }
     if (d3 && ((e = alloc(&c->sc.phi, S * a_elem(precision))) != cudaSuccess ||
                (e = alloc(&c->sc.mu, S * a_elem(precision))) != cudaSuccess ||
@@ -853,6 +905,26 @@ bool d3_unfused(const lbm_ctx* c) {
     return c->pipeline == LBM_PIPELINE_PLAIN || (c->pipeline == LBM_PIPELINE_AUTO && c->form == LBM_F64);
 }
 
+// The plan is the one batched launch (step_kernel_x2_batched), which can run
+// several steps a launch.
+bool batched_plan(const lbm_ctx* c) {
+    return !c->d3 && c->launches.size() == 1 && c->launches[0].variant == lbm::kBatched;
+}
+
+// Queues `nsteps` steps of a batched plan as one launch, the first reading buffer
+// set `in`; wait_extra / wait_limit as in StepArgs (0 / the library's limit).
+cudaError_t enqueue_batched(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, int wait_limit = lbm::kWaitLimit) {
+    const auto& L = c->launches[0];
+    StepArgs a = step_args(c, in);
+    a.work = c->d_work + L.offset;
+    a.nsteps = nsteps;
+    a.wait_extra = wait_extra;
+    a.wait_limit = wait_limit;
+    return by_form(c->form, [&](auto F) {
+        return lbm::launch_step_t<decltype(F)::value>(L.tx, a, L.count, c->stream, L.variant, false);
+    });
+}
+
 // Queues one time step (all launches of the plan) reading buffer set `in`; with
 // `monitor` the step kernels also write their monitor slots, reduced per instance.
 cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
@@ -918,6 +990,8 @@ bool build_graph(lbm_ctx* c) {
             if (e == cudaSuccess) e = cudaEventRecord(c->join[i], c->side[i]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->join[i], 0);
         }
+    } else if (batched_plan(c)) {
+        e = enqueue_batched(c, 0, steps);   // one launch for all the steps
     } else {
         for (int t = 0; t < steps && e == cudaSuccess; ++t) e = enqueue_step(c, t & 1);
     }
@@ -969,6 +1043,13 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
                 left -= c->graph_steps;   // even: parity unchanged
             }
         }
+    }
+    while (left > 0 && batched_plan(c)) {   // the rest in launches of up to 256 steps
+        const int n = std::min(left, 256);
+        cudaError_t e = enqueue_batched(c, c->cur, n);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+        c->cur ^= n & 1;
+        left -= n;
     }
     for (; left > 0; --left) {
         cudaError_t e = enqueue_step(c, c->cur);
@@ -1449,16 +1530,21 @@ lbm_status lbm_autotune_shape(lbm_ctx* c, int flags, lbm_launch_shape* out) {
         seen.push_back(sig);
         ++trials;
         // warm-up (captures the graph of this plan), then the best of two timings
+        // of whole graph replays from buffer parity 0 -- the way lbm_step runs long
+        // step counts: a plan of several launch classes runs them as concurrent
+        // graph branches there, one after the other in direct launches
+        if (c->cur == 1 && (st = lbm_step(c, 1)) != LBM_OK) break;
         if ((st = lbm_step(c, 2)) != LBM_OK) break;
+        const int nt = std::max(8, c->use_graphs && c->graph ? c->graph_steps : 0);
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {
             cudaEventRecord(e0, c->stream);
-            st = lbm_step(c, 8);
+            st = lbm_step(c, nt);
             cudaEventRecord(e1, c->stream);
             cudaEventSynchronize(e1);
             float t = 0.f;
             cudaEventElapsedTime(&t, e0, e1);
-            ms = std::min(ms, t / 8.f);
+            ms = std::min(ms, t / (float)nt);
         }
         if (st != LBM_OK) break;
         if (trials == 1) deflt = ms;
@@ -1554,6 +1640,23 @@ __global__ void wait_timeout_kernel(int rounds, int* status) {
 }
 
 }  // namespace
+
+lbm_status lbm_inject_batched_wait_timeout(lbm_ctx* c, int rounds) {
+    if (!c) return LBM_EINVAL;
+    if (rounds < 1 || rounds > lbm::kWaitLimit)
+        return fail(c, LBM_EINVAL, "rounds must be in 1 .. 2^21");
+    for (int k = 0; k < c->n; ++k)
+        if (!c->ready[k]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    lbm_status st = sticky(c);
+    if (st != LBM_OK) return st;
+    if (c->plan_dirty && (st = plan(c)) != LBM_OK) return st;
+    if (!batched_plan(c)) return fail(c, LBM_ESTATE, "the context does not run the batched launch");
+    // two steps; every item of the second waits for one finished item more than
+    // its instance has, so each of those waits runs out after `rounds` rounds
+    LBM_CK(c, enqueue_batched(c, c->cur, 2, 1, rounds));
+    return LBM_OK;
+}
 
 lbm_status lbm_inject_wait_timeout(lbm_ctx* c, int rounds) {
     if (!c) return LBM_EINVAL;

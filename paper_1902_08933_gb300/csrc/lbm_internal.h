@@ -37,9 +37,11 @@ struct WorkItem {
                                              // instance's items; D3Q15, the tile's y0
 };
 
-// A block's share of the batched step (step_kernel_x2_batched): two work items
-// (strips of up to 128 columns) that two groups of 64 threads march side by
-// side; an unused entry is -1.
+// A block's share of the batched step (step_kernel_x2_batched): one work item
+// of up to 256 columns that all 128 threads march (item[1] == kDescWide), or two
+// of up to 128 columns that two groups of 64 threads march side by side (an
+// unused entry is -1).
+constexpr int kDescWide = -2;
 struct BlockDesc {
     int item[2];
 };
@@ -72,10 +74,22 @@ struct StepArgs {
     const int64_t* time_base;           // per instance: time level - steps of the context
     long long mon_step;                 // steps of the context before the monitored step
     // batched step only: block descriptors, their number, and the queue
-    // counters {next descriptor, blocks finished} (zero between steps)
+    // counters {next (step, descriptor), blocks finished, abort} (zero between
+    // launches). One launch runs nsteps steps: step s reads the buffers above
+    // when s is even, the *_out ones when s is odd, and an item of step s > 0
+    // first waits (bounded: wait_limit rounds) until done[inst], the items of
+    // its instance finished in this launch, reaches s x (items_csr[inst + 1] -
+    // items_csr[inst]) + wait_extra (0; a test sets 1 to make the wait run out).
     const BlockDesc* desc;
     int ndesc;
     int* queue;
+    int* done;
+    const int* items_csr;
+    long long set_delta;   // bytes from each *_in array to its *_out array (the same for all)
+    int ninst;
+    int nsteps;
+    int wait_limit;
+    int wait_extra;
 };
 
 // Device layout of lbm_monitor (include/lbm.h; the host checks size and offsets).

@@ -60,13 +60,26 @@ cudaError_t launch_step_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t
     if (nwork <= 0) return cudaSuccess;
     if (monitor && a.mon == nullptr) return cudaErrorInvalidValue;
     if constexpr (kHasTma<FORM>) {
-        if (variant == kBatched) {   // nwork = blocks of the persistent grid
-            if (a.desc == nullptr || a.queue == nullptr) return cudaErrorInvalidValue;
-            if (monitor)
+        if (variant == kBatched) {   // nwork = blocks of the persistent grid (at most those resident)
+            if (a.desc == nullptr || a.queue == nullptr || a.done == nullptr) return cudaErrorInvalidValue;
+            if (monitor) {
+                if (a.nsteps != 1) return cudaErrorInvalidValue;
                 step_kernel_x2_batched<FORM, true><<<nwork, 128, X2Batched<FORM>::bytes, s>>>(a);
-            else
-                step_kernel_x2_batched<FORM><<<nwork, 128, X2Batched<FORM>::bytes, s>>>(a);
-            return cudaGetLastError();
+                return cudaGetLastError();
+            }
+            // several steps: the blocks wait on one another's items, so the grid
+            // is launched cooperatively (all of it resident at once)
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(nwork);
+            cfg.blockDim = dim3(128);
+            cfg.dynamicSmemBytes = X2Batched<FORM>::bytes;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = a.nsteps > 1 ? 1 : 0;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, step_kernel_x2_batched<FORM, false>, a);
         }
         if (variant == kPairs) {
             switch (tile_x) {

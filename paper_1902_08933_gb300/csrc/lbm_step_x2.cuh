@@ -79,24 +79,30 @@ struct X2Occ {
 };
 
 // One work item (a strip of 2 TX columns of one instance, a run of rows) marched
-// by a group of TX threads: a whole thread block (step_kernel_x2: barrier 0, the
-// one __syncthreads uses) or one of the thread groups of the batched kernel
-// (step_kernel_x2_batched: named barrier 1 + group). smem_raw is the group's own
-// X2Smem<FORM, TX> region, tid the thread's index in the group, item the work
-// item's index in StepArgs::work (and of its monitor slot).
-template <int FORM, int TX, bool MON>
+// by a group of TX threads (32, 64 or 128): a whole thread block (step_kernel_x2:
+// barrier 0, the one __syncthreads uses; TX its compile-time block size, so the
+// layout below folds to constants) or a thread group of the batched kernel
+// (step_kernel_x2_batched: named barrier 1 + group, TX 128 or 64 chosen per block
+// descriptor). smem_raw is the group's own region in the X2Smem<FORM, TX> layout,
+// tid the thread's index in the group, item the work item's index in
+// StepArgs::work (and of its monitor slot); swap: the step reads the *_out
+// buffers of a and writes the *_in ones (odd steps of a batched launch).
+template <int FORM, bool MON>
 __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned char* smem_raw, int tid,
-                                        int bar, int grp) {
+                                        int bar, int grp, const int TX, const bool swap = false) {
     using F = Form<FORM>;
     using HT = typename F::HT;
     using GT = typename F::GT;
-    using L = X2Smem<FORM, TX>;
     static_assert(sizeof(typename F::R) == 4, "the paired kernel serves the FP32-arithmetic forms");
-    constexpr int SW = L::SW, RW = L::RW;
+    // X2Smem<FORM, TX>'s layout for this group width
+    const int SW = 2 * TX, RW = SW + 8;
+    const size_t H0B = F::cons ? (size_t)RW * sizeof(float2) : 0;
+    const size_t HPB = (size_t)RW * sizeof(HT);
+    const size_t SLOT = H0B + (F::cons ? 8 : 9) * HPB;
     float* phiR = reinterpret_cast<float*>(smem_raw);   // [8][RW]
     float* muR = phiR + 8 * RW;                          // [4][RW]
     float* pR = muR + 4 * RW;                            // [4][RW]
-    unsigned char* hR = smem_raw + L::RINGS;             // [4] slots of L::SLOT bytes
+    unsigned char* hR = smem_raw + (size_t)16 * RW * sizeof(float);   // [4] slots of SLOT bytes
 
     const WorkItem wk = a.work[item];
     Consts<float> C;
@@ -106,14 +112,20 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
     const int w = min(SW, nx - x0);
     const int base = (int)C.base;
     const long long S = a.S;
-    const HT* hin = static_cast<const HT*>(a.h_in);
-    HT* hout = static_cast<HT*>(a.h_out);
-    const float2* h0in = static_cast<const float2*>(a.h0_in);
-    float2* h0out = static_cast<float2*>(a.h0_out);
-    const GT* gin = static_cast<const GT*>(a.g_in);
-    GT* gout = static_cast<GT*>(a.g_out);
-    const float* p_in = static_cast<const float*>(a.p_in);
-    float* p_out = static_cast<float*>(a.p_out);
+    // the two buffer sets lie set_delta bytes apart, every array at the same
+    // offset in both: a swapped step moves all the pointers by that one amount
+    const long long sw = swap ? a.set_delta : 0;
+    auto moved = [sw](const void* p, long long sign) {
+        return static_cast<const void*>(static_cast<const char*>(p) + sign * sw);
+    };
+    const HT* hin = static_cast<const HT*>(moved(a.h_in, 1));
+    HT* hout = static_cast<HT*>(const_cast<void*>(moved(a.h_out, -1)));
+    const float2* h0in = static_cast<const float2*>(moved(a.h0_in, 1));
+    float2* h0out = static_cast<float2*>(const_cast<void*>(moved(a.h0_out, -1)));
+    const GT* gin = static_cast<const GT*>(moved(a.g_in, 1));
+    GT* gout = static_cast<GT*>(const_cast<void*>(moved(a.g_out, -1)));
+    const float* p_in = static_cast<const float*>(moved(a.p_in, 1));
+    float* p_out = static_cast<float*>(const_cast<void*>(moved(a.p_out, -1)));
     float* phiu = static_cast<float*>(a.phiu);
     // FP16 planes hold their values times a power-of-two scale (hs, gs); the
     // arithmetic keeps h and g in those units (collide_emit / macroscopic with
@@ -129,10 +141,10 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
     auto prow = [&](int y) { return phiR + ((y + 64) & 7) * RW; };
     auto mrow = [&](int y) { return muR + ((y + 64) & 3) * RW; };
     auto qrow = [&](int y) { return pR + ((y + 64) & 3) * RW; };
-    auto hslot = [&](int y) { return hR + ((y + 64) & 3) * L::SLOT; };
+    auto hslot = [&](int y) { return hR + ((y + 64) & 3) * SLOT; };
     // plane i (i >= 1 for conservative forms) of the h slot of row y, storage type
     auto hplane = [&](int y, int i) {
-        return reinterpret_cast<HT*>(hslot(y) + L::H0B + (F::cons ? i - 1 : i) * L::HPB);
+        return reinterpret_cast<HT*>(hslot(y) + H0B + (F::cons ? i - 1 : i) * HPB);
     };
     auto hpairs = [&](int y) { return reinterpret_cast<float2*>(hslot(y)); };   // conservative h_0
     // population i of the cell pair at c as stored (FP16: still scaled by gs)
@@ -461,52 +473,114 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
 template <int FORM, int TX, bool MON = false>
 __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    x2_item<FORM, TX, MON>(a, blockIdx.x, smem_raw, threadIdx.x, 0, 0);
+    x2_item<FORM, MON>(a, blockIdx.x, smem_raw, threadIdx.x, 0, 0, TX);
 }
 
 // ---------------------------------------------------------------------------
-// The batched step: every instance of a context in one persistent launch.
-// Blocks of 128 threads take block descriptors (BlockDesc: two work items,
-// strips of up to 128 columns) from a queue -- an atomic counter over the
-// descriptors, which the planner sorts longest run first -- until it runs dry.
-// Each item runs on its own group of 64 threads with its own shared-memory
-// region and its own named barrier, so the two groups march independently
-// (different instances, run lengths and directions); the block meets again
-// only between descriptors. One group size for every instance keeps one code
-// path (mixing 32-, 64- and 128-thread paths in one kernel made the register
-// allocator spill). The last block to finish sets the queue back to zero for
-// the next step.
+// The batched step: every instance of a context, several steps, in one
+// persistent launch. Blocks of 128 threads take (step, block descriptor) pairs
+// from a queue -- an atomic counter over nsteps x ndesc, step-major; within a
+// step the planner sorts the descriptors longest run first -- until it runs
+// dry. A descriptor holds either one wide item (a strip of up to 256 columns,
+// marched by all 128 threads; item[1] == kDescWide) or two narrow ones (strips
+// of up to 128 columns, each on its own group of 64 threads with its own
+// shared-memory region and named barrier, so the two groups march
+// independently: different instances, run lengths and directions). Both kinds
+// go through one inlined x2_item with the group width as a run-time value (two
+// inlined bodies, one a width, made the register allocator spill).
+// Steps overlap across instances: an item of step s > 0 waits only until every
+// item of its own instance's step s - 1 has finished (a per-instance counter of
+// finished items), so no grid-wide step boundary leaves SMs idle in a tail. The
+// wait is safe: items are handed out in step order, so every item waited for
+// was taken earlier by a running block, and the earliest unfinished one waits
+// for nothing. It is bounded all the same: after wait_limit rounds the group
+// records a timeout in the status word, raises the abort flag (every block
+// then stops taking work) and skips its item. The last block to finish sets
+// the queue and the counters back to zero for the next launch.
 // Three resident blocks a SM (up to 168 registers a thread) for every form: at
 // four, the FP16-h form's batched kernel spilled at its 128-register cap and ran
 // at 23.2k MLUPS on the 512 mixed instances.
 template <int FORM>
 struct X2Batched {
-    static constexpr size_t bytes = 2 * X2Smem<FORM, 64>::bytes;
+    static constexpr size_t narrow = X2Smem<FORM, 64>::bytes;    // one group of 64
+    static constexpr size_t wide = X2Smem<FORM, 128>::bytes;     // the block as one group
+    static constexpr size_t bytes = 2 * narrow > wide ? 2 * narrow : wide;
     static constexpr int by_smem = (int)((228u * 1024u) / (bytes + 1024u));
     static constexpr int occ = by_smem < 3 ? by_smem : 3;
 };
 
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 template <int FORM, bool MON = false>
 __global__ void __launch_bounds__(128, X2Batched<FORM>::occ) step_kernel_x2_batched(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_desc;
+    __shared__ int s_desc, s_abort;
+    __shared__ int s_skip[2];
     const int tid = threadIdx.x;
-    const int g = tid >> 6;   // thread group: 0 or 1
+    const int g = tid >> 6;   // narrow thread group: 0 or 1
+    const int total = a.nsteps * a.ndesc;
+    volatile int* abort_flag = a.queue + 2;
     for (;;) {
-        if (tid == 0) s_desc = atomicAdd(a.queue, 1);
+        if (tid == 0) {
+            s_desc = atomicAdd(a.queue, 1);
+            s_abort = *abort_flag;
+        }
         __syncthreads();
-        const int q = s_desc;
-        if (q >= a.ndesc) break;
-        const int item = a.desc[q].item[g];
-        if (item >= 0)
-            x2_item<FORM, 64, MON>(a, item, smem_raw + g * X2Smem<FORM, 64>::bytes, tid & 63, 1 + g, g);
-        __syncthreads();   // both groups are done with their regions; s_desc may change
+        const int gq = s_desc;
+        if (gq >= total || s_abort) break;
+        const int s = gq / a.ndesc, q = gq - s * a.ndesc;
+        const int i0 = a.desc[q].item[0], i1 = a.desc[q].item[1];
+        const bool wide = i1 == kDescWide;
+        const int item = (wide || g == 0) ? i0 : i1;
+        const int gt = wide ? tid : tid & 63, nthr = wide ? 128 : 64, bar = wide ? 1 : 1 + g, grp = wide ? 0 : g;
+        int inst = -1;
+        bool run = item >= 0;
+        if (run) {
+            inst = a.work[item].inst;
+            if (s > 0) {   // every item of this instance's step s - 1 finished
+                if (gt == 0) {
+                    const int need = s * (a.items_csr[inst + 1] - a.items_csr[inst]) + a.wait_extra;
+                    int ok = 0;
+                    for (int it = 0; it < a.wait_limit; ++it) {
+                        if (ld_acquire_gpu(a.done + inst) >= need) {
+                            ok = 1;
+                            break;
+                        }
+                        if (*abort_flag) break;
+                        __nanosleep(64);
+                    }
+                    if (!ok) {
+                        atomicExch(a.status, kStatusTimeout);
+                        atomicExch(a.queue + 2, 1);
+                    }
+                    __threadfence();
+                    s_skip[grp] = !ok;
+                }
+                group_sync(bar, nthr);
+                run = !s_skip[grp];
+            }
+            if (run)
+                x2_item<FORM, MON>(a, item, smem_raw + (wide ? 0 : g * X2Batched<FORM>::narrow), gt, bar, grp,
+                                   nthr, !MON && (s & 1) != 0);   // a monitored launch runs one step
+        }
+        __syncthreads();   // the groups are done with their regions and stores; s_desc may change
+        if (run && gt == 0) {   // publish: one more item of this instance finished
+            __threadfence();
+            atomicAdd(a.done + inst, 1);
+        }
     }
     if (tid == 0) {
         __threadfence();
         if (atomicAdd(a.queue + 1, 1) == (int)gridDim.x - 1) {   // every block is past the queue
+            for (int k = 0; k < a.ninst; ++k) a.done[k] = 0;
             a.queue[0] = 0;
             a.queue[1] = 0;
+            a.queue[2] = 0;
+            __threadfence();
         }
     }
 }

@@ -123,6 +123,7 @@ SIGNATURES = [
     ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
     ("lbm_reduce_fields_noalloc", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     ("lbm_inject_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lbm_inject_batched_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lbm_sync", ctypes.c_int, [_VP]),
     ("lbm_last_error", ctypes.c_char_p, [_VP]),
     ("lbm_destroy", None, [_VP]),
@@ -342,6 +343,10 @@ def lbm_reduce_fields_noalloc(fields_dev_ptr: int, nx: int, ny: int, stream, out
 
 def lbm_inject_wait_timeout(ctx, rounds: int):
     _check(library().lbm_inject_wait_timeout(ctx, int(rounds)), ctx)
+
+
+def lbm_inject_batched_wait_timeout(ctx, rounds: int):
+    _check(library().lbm_inject_batched_wait_timeout(ctx, int(rounds)), ctx)
 
 
 def lbm_sync(ctx):

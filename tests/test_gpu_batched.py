@@ -1,14 +1,15 @@
 """The batched launch (LBM_PIPELINE_BATCHED, the default for several instances):
 every instance of a context advanced by ONE persistent kernel launch a step, whose
-blocks take descriptors of two 128-column strips from an on-device queue.
+blocks take descriptors from an on-device queue: one strip of up to 256 columns
+on the whole block, or two strips of up to 128 columns on two thread groups.
 
 It runs the same per-cell arithmetic as the per-class paired kernels
 (LBM_PIPELINE_PAIRS, one launch per strip width), only split into other strips
 and scheduled differently, so the populations must agree bit for bit; the
 per-class kernels are held to the oracle in test_gpu_parity.py. Mixed grids:
-wider than one strip with a ragged last strip (160, 300), exactly one strip
-(128), narrower (96, 64, 34), walls and periodic y, odd ny, both march
-directions (runs of 5 rows).
+one wide strip (160), a wide strip and a narrow ragged last one (300), exactly
+one narrow strip (128), narrower (96, 64, 34), walls and periodic y, odd ny,
+both march directions (runs of 5 rows).
 """
 import numpy as np
 import pytest
