@@ -95,11 +95,12 @@ def test_batched_512_for_5000_steps(L, orc, report):
     for form in CONSERVATIVE:
         assert summary[form]["mass_drift_max"] < 1e-6, (form, summary[form])
     # Fields and the Laplace jump against the FP64 form after 5000 steps. The
-    # per-step storage rounding of h (|h_i| ~ 1, 2^-24 FP32, 2^-11 FP16) walks phi,
-    # and the flow (bubbles rising, droplets relaxing) carries the differences on:
-    # measured phi up to 4.2e-4 (FP32) / 1.0e-2 (FP16 g), Delta p median 2e-5 /
-    # 2e-4, worst single droplet 1.5e-3 (two-float h_0) / 4e-2 (FP16; the bulk
-    # thresholds phi > 1 - 1e-3, phi < 1e-3 move with phi). Bars: 2.5x those.
+    # flow (bubbles rising, droplets relaxing) carries the reduced-precision
+    # differences on: measured phi up to 4.2e-4 (FP32) / 1.0e-2 (FP16 g). The
+    # jump of a droplet settles within ~1000 steps at an offset that then stays
+    # (the FP32 arithmetic's quasi-equilibrium): median 2e-5 / 2e-4, worst single
+    # droplet 1.5e-3 (two-float h_0) / 4e-2 (FP16), much the same with geometric
+    # bulk masks as with the phi thresholds. Bars: 2.5x those.
     bars = {"f32": (1e-3, 0.2, 1e-3), "f32_c": (1e-3, 1e-2, 1e-4), "f32_cc": (1e-3, 1e-2, 1e-4),
             "f32_g16": (2.5e-2, 0.1, 5e-4), "f32_h16": (2.5e-2, 0.1, 5e-4)}
     for form, (b_phi, b_dp, b_dp_med) in bars.items():
