@@ -57,8 +57,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32_c", choices=list(BYTES_PER_LUP))
-    ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs"],
-                    help="load path of the step kernel (lbm_set_pipeline)")
+    ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs", "batched"],
+                    help="load path / kernel of the step (lbm_set_pipeline); also for --kernel-run on "
+                         "the D3Q15 bubble (async: the fused march, plain: the three-kernel step) and "
+                         "the batched instances")
     ap.add_argument("--kernel-run", default=None,
                     choices=["bubble3d", "source_flow", "source_flow_remark1", "source_flow_remark2",
                              "source_flow_remark4", "batched"],
@@ -317,8 +319,10 @@ def kernel_run(args):
             spcfg.update(scheme=1, force_x=1e-6, drag_lin=1e-3, drag_quad=0.1)
         sim = lbm.SourceFlow(spcfg, form, stream=stream.cuda_stream, source=src)
         bpl = {0: 76, 1: 132, 2: 132, 4: 160}[model] * (2 if form == "f64" else 1)
+    if args.pipeline != "auto" and args.kernel_run in ("batched", "bubble3d"):
+        lbm.lbm_set_pipeline(sim.ctx, getattr(lbm, "LBM_PIPELINE_" + args.pipeline.upper()))
     shape = None
-    if args.kernel_run == "batched" and not args.no_tune:
+    if args.kernel_run == "batched" and not args.no_tune and args.pipeline == "auto":
         sim.step(2)
         shape = lbm.lbm_autotune_shape(sim.ctx)
     sim.step(max(args.warmup, 2))
@@ -371,7 +375,7 @@ def main():
     sim = lbm.Simulation(cfg, args.form, stream=stream.cuda_stream, phi0=[phi0])
     lbm.lbm_set_pipeline(sim.ctx, {"auto": lbm.LBM_PIPELINE_AUTO, "plain": lbm.LBM_PIPELINE_PLAIN,
                                    "async": lbm.LBM_PIPELINE_ASYNC, "tma": lbm.LBM_PIPELINE_TMA,
-                                   "pairs": lbm.LBM_PIPELINE_PAIRS}[args.pipeline])
+                                   "pairs": lbm.LBM_PIPELINE_PAIRS, "batched": lbm.LBM_PIPELINE_BATCHED}[args.pipeline])
     shape = None
     if args.pipeline == "auto" and not args.no_tune:
         sim.step(2)
