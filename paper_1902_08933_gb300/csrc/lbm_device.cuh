@@ -586,6 +586,15 @@ __device__ __forceinline__ void group_reduce4(double v[4], int tid, int nthr, in
         }
 }
 
+// Atomic add at GPU scope with acquire-release ordering: the caller's earlier
+// writes are visible to any thread that sees the new count, and the caller
+// sees the writes of every thread whose add came before its own.
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 template <typename R>
 __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const StepArgs& a, int inst, int item,
                                                 int pos, int tid, int nthr, int bar, int grp) {
@@ -609,12 +618,13 @@ __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const Step
         out[1] = v[1];
         out[2] = v[2];
         out[3] = (isfinite(v[0]) && isfinite(v[1])) ? 0.0 : 1.0;
-        __threadfence();                                  // the slot before the count
-        flag = atomicAdd(cnt + s * kCounterStride, 1) == in_sub - 1;
+        // release: the slot before the count; acquire (for the last): the
+        // sub-group's other slots before the reads below, which the barrier
+        // orders after this thread's acquire
+        flag = atom_add_acq_rel_gpu(cnt + s * kCounterStride, 1) == in_sub - 1;
     }
     group_sync(bar, nthr);
     if (!flag) return;
-    __threadfence();                                      // the count before the slots
     // the sub-group's slots, in order
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (int j = tid; j < in_sub; j += nthr) {
@@ -632,29 +642,41 @@ __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const Step
         sub[2] = w[2];
         sub[3] = w[3];
         cnt[s * kCounterStride] = 0;                      // ready for the next monitored step
-        __threadfence();
-        if (atomicAdd(cnt + kMonSub * kCounterStride, 1) == nsub - 1) {
-            __threadfence();
-            // the instance's record from its sub-group slots, in order
-            double m = 0.0, e = 0.0, u = 0.0, f = 0.0;
-            const double* sb = a.mon_sub + (long long)inst * kMonSub * kMonQ;
-            for (int q = 0; q < nsub; ++q) {
-                m += __ldcg(sb + q * kMonQ);
-                e += __ldcg(sb + q * kMonQ + 1);
-                u = fmax(u, __ldcg(sb + q * kMonQ + 2));
-                f += __ldcg(sb + q * kMonQ + 3);
-            }
-            MonRecord r;
-            r.sum_phi = m;
-            r.kinetic_energy = e;
-            r.max_u = sqrt(u);
-            r.nonfinite = f != 0.0 ? 1 : 0;
-            r.device_status = *(volatile int*)a.status;
-            r.time = a.mon_step + a.time_base[inst];
-            a.mon_rec[inst] = r;
-            if (a.mon_host) a.mon_host[inst] = r;         // caller's pinned host record, written from here
-            cnt[kMonSub * kCounterStride] = 0;
-        }
+        flag = atom_add_acq_rel_gpu(cnt + kMonSub * kCounterStride, 1) == nsub - 1;
+    }
+    group_sync(bar, nthr);   // (every thread read the first flag before group_reduce4's barriers)
+    if (!flag || tid >= 32) return;
+    // the instance's record from its sub-group slots: lane q < nsub of the
+    // group's first warp loads slot q (the loads in parallel), lane 0 adds them
+    // in order q = 0, 1, ...
+    double sv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (tid < nsub) {
+        const double* sb = a.mon_sub + ((long long)inst * kMonSub + tid) * kMonQ;
+        sv[0] = __ldcg(sb);
+        sv[1] = __ldcg(sb + 1);
+        sv[2] = __ldcg(sb + 2);
+        sv[3] = __ldcg(sb + 3);
+    }
+    double m = 0.0, e = 0.0, u = 0.0, f = 0.0;
+    for (int q = 0; q < nsub; ++q) {
+        const double a0 = __shfl_sync(0xffffffffu, sv[0], q), a1 = __shfl_sync(0xffffffffu, sv[1], q);
+        const double a2 = __shfl_sync(0xffffffffu, sv[2], q), a3 = __shfl_sync(0xffffffffu, sv[3], q);
+        m += a0;
+        e += a1;
+        u = fmax(u, a2);
+        f += a3;
+    }
+    if (tid == 0) {
+        MonRecord r;
+        r.sum_phi = m;
+        r.kinetic_energy = e;
+        r.max_u = sqrt(u);
+        r.nonfinite = f != 0.0 ? 1 : 0;
+        r.device_status = *(volatile int*)a.status;
+        r.time = a.mon_step + a.time_base[inst];
+        a.mon_rec[inst] = r;
+        if (a.mon_host) a.mon_host[inst] = r;             // caller's pinned host record, written from here
+        cnt[kMonSub * kCounterStride] = 0;
     }
 }
 
