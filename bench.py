@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32_c", choices=list(BYTES_PER_LUP))
-    ap.add_argument("--pipeline", default="auto", choices=["auto", "plain", "async", "tma", "pairs", "batched"],
+    ap.add_argument("--pipeline", default="auto",
+                    choices=["auto", "plain", "async", "tma", "pairs", "batched", "persistent"],
                     help="load path / kernel of the step (lbm_set_pipeline); also for --kernel-run on "
                          "the D3Q15 bubble (async: the fused march, plain: the three-kernel step) and "
                          "the batched instances")
@@ -150,8 +151,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------- helpers
 def traffic_record(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source
-    has not changed since it was captured (else None)."""
+    """DRAM bytes per step from the committed ncu summary (key: the storage form,
+    plus "/persistent" for the several-steps-a-launch kernel, whose launch is
+    divided by the steps it ran), if the kernel source has not changed since it
+    was captured (else None)."""
     h = hashlib.sha256()
     for name in ("lbm_device.cuh", "lbm_step_x2.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1902_08933_gb300", "csrc", name), "rb").read())
@@ -161,7 +164,7 @@ def traffic_record(kernel_key):
         return None
     text = open(path).read()
     m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9.eE+]+)" % re.escape(kernel_key), text)
+    t = re.search(r"traffic_bytes_per_step\[%s\]:\s*([0-9.eE+]+)" % re.escape(kernel_key), text)
     if not m or not t or m.group(1) != sha:
         return None
     return float(t.group(1))
@@ -375,7 +378,8 @@ def main():
     sim = lbm.Simulation(cfg, args.form, stream=stream.cuda_stream, phi0=[phi0])
     lbm.lbm_set_pipeline(sim.ctx, {"auto": lbm.LBM_PIPELINE_AUTO, "plain": lbm.LBM_PIPELINE_PLAIN,
                                    "async": lbm.LBM_PIPELINE_ASYNC, "tma": lbm.LBM_PIPELINE_TMA,
-                                   "pairs": lbm.LBM_PIPELINE_PAIRS, "batched": lbm.LBM_PIPELINE_BATCHED}[args.pipeline])
+                                   "pairs": lbm.LBM_PIPELINE_PAIRS, "batched": lbm.LBM_PIPELINE_BATCHED,
+                                   "persistent": lbm.LBM_PIPELINE_PERSISTENT}[args.pipeline])
     shape = None
     if args.pipeline == "auto" and not args.no_tune:
         sim.step(2)
@@ -390,10 +394,12 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    n0 = lbm.lbm_step_launch_count(sim.ctx)
     e0.record(stream)
     sim.step(args.steps)
     e1.record(stream)
     e1.synchronize()
+    n_launches = lbm.lbm_step_launch_count(sim.ctx) - n0
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
@@ -405,10 +411,13 @@ def main():
     d = sim.diagnostics()
     sim.close()
     value = world * cells * args.steps / (ms * 1e-3) / 1e6
-    per_launch_s = ms * 1e-3 / (args.steps * launches)
-    achieved = ALGO_BYTES_PER_LUP[args.form] * cells / per_launch_s / 1e9
-    achieved_form = BYTES_PER_LUP[args.form] * cells / per_launch_s / 1e9
-    traffic = traffic_record("%s" % args.form)
+    # per step: a launch of the persistent plan runs up to 64 steps, and its
+    # algorithmic bytes over its duration is this same rate
+    per_step_s = ms * 1e-3 / args.steps
+    achieved = ALGO_BYTES_PER_LUP[args.form] * cells / per_step_s / 1e9
+    achieved_form = BYTES_PER_LUP[args.form] * cells / per_step_s / 1e9
+    persistent = (shape or {}).get("pipeline") == "persistent" or args.pipeline == "persistent"
+    traffic = traffic_record(args.form + ("/persistent" if persistent else ""))
     result = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -430,9 +439,12 @@ def main():
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[args.form],
                      "form_bytes_per_lup": BYTES_PER_LUP[args.form],
-                     "frac_form_bytes": achieved_form / hbm_peak},
+                     "frac_form_bytes": achieved_form / hbm_peak,
+                     "kernel": "step_kernel_x2_multi" if persistent else "step_kernel_x2",
+                     "per": "step (bytes of one step over one step's time; a launch runs %.1f steps)" % (
+                         args.steps / max(1, n_launches))},
         "clocks": clk,
-        "gpu_launches": args.steps * launches,
+        "gpu_launches": n_launches,
         "mass_drift": abs(d["sum_phi"] - phi0.sum()) / phi0.sum(),
     }
 

@@ -302,12 +302,23 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
  *                      (FP32-arithmetic forms, instances with nx even, strips
  *                      of at least 64 columns).
  *  LBM_PIPELINE_BATCHED the PAIRS kernel over every instance of the context in
- *                      ONE persistent launch a step: blocks of 128 threads take
- *                      descriptors of two strips of up to 128 columns (two
- *                      thread groups with their own barriers) from an
- *                      on-device queue, longest runs first. The strip width is
- *                      fixed (lbm_set_launch sets the run length only). Only
- *                      when every instance can use PAIRS; else as AUTO.
+ *                      ONE persistent, cooperative launch for up to 64 steps
+ *                      (one node of the captured graph): blocks of 128 threads
+ *                      take (step, descriptor) pairs from an on-device queue,
+ *                      a descriptor one strip of up to 256 columns or two of up
+ *                      to 128 (two thread groups with their own barriers); an
+ *                      item of step s waits (bounded) until its instance has
+ *                      finished step s - 1, so steps overlap across instances.
+ *                      The strip widths are fixed (lbm_set_launch sets the run
+ *                      length only). Only when every instance can use PAIRS;
+ *                      else as AUTO.
+ *  LBM_PIPELINE_PERSISTENT the PAIRS plan (one launch class: the same strip
+ *                      width for every instance), run for up to 64 steps in ONE
+ *                      cooperative launch with one block per work item when
+ *                      every item's block fits on the GPU at once (else as
+ *                      PAIRS): before step s a block waits (bounded) only for
+ *                      the items within reach of its own (3 rows, 2 columns) to
+ *                      finish step s - 1, so no grid-wide step boundary remains.
  *  LBM_PIPELINE_AUTO   (default) BATCHED for contexts of several instances that
  *                      all can use it; otherwise PAIRS where available, else
  *                      ASYNC, else TMA, else PLAIN.
@@ -320,7 +331,7 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int tile_x, int rows);
  * which runs the unfused step (faster there). Both give the same result. */
 enum {
     LBM_PIPELINE_AUTO = 0, LBM_PIPELINE_PLAIN = 1, LBM_PIPELINE_ASYNC = 2, LBM_PIPELINE_TMA = 3,
-    LBM_PIPELINE_PAIRS = 4, LBM_PIPELINE_BATCHED = 5
+    LBM_PIPELINE_PAIRS = 4, LBM_PIPELINE_BATCHED = 5, LBM_PIPELINE_PERSISTENT = 6
 };
 lbm_status lbm_set_pipeline(lbm_ctx* ctx, int mode);
 
@@ -377,6 +388,12 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int* best_tile_x, int* best_rows);
 
 /* Kernel launches queued by one lbm_step(1) (for accounting); 0 on error. */
 int lbm_launches_per_step(const lbm_ctx* ctx);
+
+/* Kernel launches the context's lbm_step calls have queued so far (each kernel
+ * node of a replayed graph counted; a batched or persistent launch that runs
+ * several steps counts once). Read it before and after a run of lbm_step to
+ * count that run's launches. 0 for a NULL context. */
+long long lbm_step_launch_count(const lbm_ctx* ctx);
 
 /* Steps taken by an instance since its lbm_init. */
 int64_t lbm_time(const lbm_ctx* ctx, int instance);

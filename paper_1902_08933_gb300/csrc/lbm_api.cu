@@ -166,6 +166,11 @@ struct lbm_ctx {
     int ndesc = 0;
     int* d_queue = nullptr;        // batched queue: next, blocks finished, abort
     int* d_done = nullptr;         // batched: items finished a launch, per instance
+    bool multi = false;            // persistent plan: several steps a launch
+    long long step_launches = 0;   // kernel launches lbm_step has issued (graph nodes counted)
+    int graph_launches = 0;        // kernel nodes of the captured graph
+    int* d_nbr = nullptr;          // persistent plan: neighbour items, kMaxNbr an item
+    int* d_multi_done = nullptr;   // persistent plan: steps finished per item, then the abort flag
     bool plan_dirty = true;
     // CUDA graph of 2 * graph_pairs steps starting from cur == 0 (built on first use,
     // dropped when the plan changes)
@@ -244,6 +249,7 @@ StepArgs step_args(const lbm_ctx* c, int in) {
     a.queue = c->d_queue;
     a.done = c->d_done;
     a.items_csr = c->d_mon_csr;
+    a.nbr = nullptr;
     a.ninst = c->n;
     a.nsteps = 1;
     a.wait_limit = lbm::kWaitLimit;
@@ -296,7 +302,8 @@ void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, b
         case LBM_PIPELINE_BATCHED:   // (when the batched launch does not apply)
             v = pairs_ok ? lbm::kPairs : (f_async ? lbm::kAsync : (tma_ok ? lbm::kTma : lbm::kPlain));
             break;
-        case LBM_PIPELINE_PAIRS: v = pairs_ok ? lbm::kPairs : lbm::kPlain; break;
+        case LBM_PIPELINE_PAIRS:
+        case LBM_PIPELINE_PERSISTENT: v = pairs_ok ? lbm::kPairs : lbm::kPlain; break;
         case LBM_PIPELINE_ASYNC: v = f_async ? lbm::kAsync : lbm::kPlain; break;
         case LBM_PIPELINE_TMA: v = tma_ok ? lbm::kTma : lbm::kPlain; break;
         default: v = lbm::kPlain; break;
@@ -312,6 +319,7 @@ void choose(const lbm_ctx* c, const lbm_params& p, bool f_pairs, bool f_async, b
 // share a run boundary read its halo rows at the same time (both at their start
 // or both at their end), from L2 rather than HBM.
 lbm_status plan_d3(lbm_ctx* c);
+lbm_status plan_multi(lbm_ctx* c, int sms);
 lbm_status plan_batched(lbm_ctx* c, bool f_pairs, bool f_async, bool f_tma, int sms);
 lbm_status finish_plan(lbm_ctx* c);
 
@@ -427,7 +435,9 @@ lbm_status plan(lbm_ctx* c) {
         c->work.insert(c->work.end(), by_class[k].begin(), by_class[k].end());
     }
     c->ndesc = 0;
-    return finish_plan(c);
+    lbm_status st = finish_plan(c);
+    if (st != LBM_OK) return st;
+    return plan_multi(c, sms);
 }
 
 // Batched plan: the paired kernel's work items of every instance, runs of rows
@@ -521,6 +531,64 @@ lbm_status plan_batched(lbm_ctx* c, bool, bool, bool, int sms) {
     if (!c->d_done) LBM_CK(c, cudaMalloc(&c->d_done, (size_t)c->n * sizeof(int)));
     LBM_CK(c, cudaMemset(c->d_done, 0, (size_t)c->n * sizeof(int)));
     return finish_plan(c);
+}
+
+// The persistent plan (LBM_PIPELINE_PERSISTENT): a paired plan of one launch
+// class whose blocks all fit on the GPU at once runs several steps a launch
+// (step_kernel_x2_multi). Neighbour lists: for each item, the other items of its
+// instance whose columns lie within 2 and whose rows lie within 3 of its own
+// (periodic where the instance is; the reach of one step of the row march: lead
+// rows 2 ahead, pushes 1 row and 1 column out, the phi halo 2 columns). More
+// than kMaxNbr neighbours, or more items than resident blocks: no persistent
+// launch, the plan runs as PAIRS.
+lbm_status plan_multi(lbm_ctx* c, int sms) {
+    c->multi = false;
+    if (c->d3 || c->pipeline != LBM_PIPELINE_PERSISTENT || c->launches.size() != 1 ||
+        c->launches[0].variant != lbm::kPairs)
+        return LBM_OK;
+    const auto& L = c->launches[0];
+    int occ = 0;
+    by_form(c->form, [&](auto F) {
+        occ = lbm::multi_occupancy_t<decltype(F)::value>(L.tx);
+        return cudaSuccess;
+    });
+    if (occ <= 0 || (long long)L.count > (long long)sms * occ) return LBM_OK;
+    struct Box { int inst, x0, x1, y0, y1; };
+    std::vector<Box> box(L.count);
+    for (int k = 0; k < L.count; ++k) {
+        const WorkItem& w = c->work[L.offset + k];
+        const lbm_params& p = c->params[w.inst];
+        const int y0 = w.dir < 0 ? w.ystart - w.nrows + 1 : w.ystart;
+        box[k] = {w.inst, w.x0, std::min(p.nx, w.x0 + L.tx), y0, y0 + w.nrows};
+    }
+    // [a0, a1) and [b0, b1) meet, with b shifted by -n, 0, +n when periodic
+    auto meet = [](int a0, int a1, int b0, int b1, int n, bool periodic) {
+        for (int sh = periodic ? -1 : 0; sh <= (periodic ? 1 : 0); ++sh)
+            if (b0 + sh * n < a1 && a0 < b1 + sh * n) return true;
+        return false;
+    };
+    std::vector<int> nbr((size_t)L.count * lbm::kMaxNbr, -1);
+    for (int k = 0; k < L.count; ++k) {
+        const lbm_params& p = c->params[box[k].inst];
+        const bool per_y = p.bc_y != LBM_BC_BOUNCEBACK;
+        int cnt = 0;
+        for (int m = 0; m < L.count; ++m) {
+            if (m == k || box[m].inst != box[k].inst) continue;
+            if (!meet(box[k].x0 - 2, box[k].x1 + 2, box[m].x0, box[m].x1, p.nx, true)) continue;
+            if (!meet(box[k].y0 - 3, box[k].y1 + 3, box[m].y0, box[m].y1, p.ny, per_y)) continue;
+            if (cnt == lbm::kMaxNbr) return LBM_OK;   // too many: no persistent launch
+            nbr[(size_t)k * lbm::kMaxNbr + cnt++] = m;
+        }
+    }
+    cudaFree(c->d_nbr);
+    c->d_nbr = nullptr;
+    cudaFree(c->d_multi_done);
+    c->d_multi_done = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_nbr, nbr.size() * sizeof(int)));
+    LBM_CK(c, cudaMemcpy(c->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    LBM_CK(c, cudaMalloc(&c->d_multi_done, ((size_t)L.count + 1) * sizeof(int)));
+    c->multi = true;
+    return LBM_OK;
 }
 
 // Uploads the work list and sets up the monitor's per-instance item lists.
@@ -682,6 +750,8 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_desc);
     cudaFree(c->d_queue);
     cudaFree(c->d_done);
+    cudaFree(c->d_nbr);
+    cudaFree(c->d_multi_done);
     cudaFree(c->d_tmp);
     cudaFree(c->d_out);
     cudaFree(c->d_partials);
@@ -925,6 +995,35 @@ cudaError_t enqueue_batched(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, 
     });
 }
 
+// The plan runs several steps a launch, one block per work item (plan_multi).
+bool multi_plan(const lbm_ctx* c) { return c->multi && !c->d3 && c->launches.size() == 1; }
+
+// Queues `nsteps` steps of a persistent plan as one cooperative launch, the
+// first reading buffer set `in`, after zeroing the per-item step counters and
+// the abort flag; wait_extra / wait_limit as in StepArgs.
+cudaError_t enqueue_multi(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, int wait_limit = lbm::kWaitLimit) {
+    const auto& L = c->launches[0];
+    cudaError_t e = cudaMemsetAsync(c->d_multi_done, 0, ((size_t)L.count + 1) * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    StepArgs a = step_args(c, in);
+    a.work = c->d_work + L.offset;
+    a.nbr = c->d_nbr;
+    a.done = c->d_multi_done;
+    a.ndesc = L.count;
+    a.nsteps = nsteps;
+    a.wait_extra = wait_extra;
+    a.wait_limit = wait_limit;
+    return by_form(c->form, [&](auto F) {
+        return lbm::launch_multi_t<decltype(F)::value>(L.tx, a, L.count, c->stream);
+    });
+}
+
+// Kernel launches of one directly launched step of the plan.
+int step_kernels(const lbm_ctx* c) {
+    if (c->d3) return d3_unfused(c) ? 3 * c->n : 1;
+    return (int)c->launches.size();
+}
+
 // Queues one time step (all launches of the plan) reading buffer set `in`; with
 // `monitor` the step kernels also write their monitor slots, reduced per instance.
 cudaError_t enqueue_step(lbm_ctx* c, int in, bool monitor = false, int64_t mon_step = 0) {
@@ -992,6 +1091,8 @@ bool build_graph(lbm_ctx* c) {
         }
     } else if (batched_plan(c)) {
         e = enqueue_batched(c, 0, steps);   // one launch for all the steps
+    } else if (multi_plan(c)) {
+        e = enqueue_multi(c, 0, steps);     // one launch (after the counters' reset) for all the steps
     } else {
         for (int t = 0; t < steps && e == cudaSuccess; ++t) e = enqueue_step(c, t & 1);
     }
@@ -1012,6 +1113,7 @@ bool build_graph(lbm_ctx* c) {
     }
     c->graph = x;
     c->graph_steps = steps;
+    c->graph_launches = nl > 1 ? steps * nl : ((batched_plan(c) || multi_plan(c)) ? 1 : steps * step_kernels(c));
     return true;
 }
 }  // namespace
@@ -1033,6 +1135,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         if (c->cur == 1) {
             cudaError_t e = enqueue_step(c, 1);
             if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+            c->step_launches += step_kernels(c);
             c->cur = 0;
             --left;
         }
@@ -1040,26 +1143,30 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
             while (left >= c->graph_steps) {
                 cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
                 if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+                c->step_launches += c->graph_launches;
                 left -= c->graph_steps;   // even: parity unchanged
             }
         }
     }
-    while (left > 0 && batched_plan(c)) {   // the rest in launches of up to 256 steps
+    while (left > 0 && (batched_plan(c) || multi_plan(c))) {   // the rest in launches of up to 256 steps
         const int n = std::min(left, 256);
-        cudaError_t e = enqueue_batched(c, c->cur, n);
+        cudaError_t e = batched_plan(c) ? enqueue_batched(c, c->cur, n) : enqueue_multi(c, c->cur, n);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+        ++c->step_launches;
         c->cur ^= n & 1;
         left -= n;
     }
     for (; left > 0; --left) {
         cudaError_t e = enqueue_step(c, c->cur);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+        c->step_launches += step_kernels(c);
         c->cur ^= 1;
     }
     if (mon_last) {
         // the record's time level is the monitored step's input level
         cudaError_t e = enqueue_step(c, c->cur, true, c->steps_total + nsteps - 1);
         if (e != cudaSuccess) return cuda_fail(c, e, "monitored step launch");
+        c->step_launches += step_kernels(c);
         c->cur ^= 1;
     }
     c->steps_total += nsteps;
@@ -1446,6 +1553,7 @@ std::string plan_signature(const lbm_ctx* c) {
     for (const auto& L : c->launches)
         sig += std::to_string(L.tx) + ":" + std::to_string(L.count) + ":" + std::to_string(L.variant) + ";";
     for (const WorkItem& w : c->work) sig += std::to_string(w.nrows) + ",";
+    if (c->multi) sig += "multi";
     return sig;
 }
 }  // namespace
@@ -1505,7 +1613,8 @@ lbm_status lbm_autotune_shape(lbm_ctx* c, int flags, lbm_launch_shape* out) {
     // run length; the built-in plan (AUTO, 0, 0) first.
     struct Cand { int pipe, tile, rows; };
     std::vector<Cand> cands{{LBM_PIPELINE_AUTO, 0, 0}};
-    const int pipes[] = {LBM_PIPELINE_PAIRS, LBM_PIPELINE_BATCHED, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC,
+    const int pipes[] = {LBM_PIPELINE_PAIRS, LBM_PIPELINE_PERSISTENT, LBM_PIPELINE_BATCHED, LBM_PIPELINE_PLAIN,
+                         LBM_PIPELINE_ASYNC,
                          LBM_PIPELINE_TMA};
     const int tiles[] = {0, 64, 128, 256};
     const int rows_c[] = {0, 8, 16, 32, 64};
@@ -1610,6 +1719,8 @@ lbm_status lbm_autotune(lbm_ctx* c, int* best_tile_x, int* best_rows) {
     return LBM_OK;
 }
 
+long long lbm_step_launch_count(const lbm_ctx* c) { return c ? c->step_launches : 0; }
+
 int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
     if (c->plan_dirty) {
@@ -1651,10 +1762,12 @@ lbm_status lbm_inject_batched_wait_timeout(lbm_ctx* c, int rounds) {
     lbm_status st = sticky(c);
     if (st != LBM_OK) return st;
     if (c->plan_dirty && (st = plan(c)) != LBM_OK) return st;
-    if (!batched_plan(c)) return fail(c, LBM_ESTATE, "the context does not run the batched launch");
-    // two steps; every item of the second waits for one finished item more than
-    // its instance has, so each of those waits runs out after `rounds` rounds
-    LBM_CK(c, enqueue_batched(c, c->cur, 2, 1, rounds));
+    if (!batched_plan(c) && !multi_plan(c))
+        return fail(c, LBM_ESTATE, "the context runs neither the batched nor the persistent launch");
+    // two steps; every item of the second waits for one finished item (batched)
+    // or step (persistent) more than there are, so each of those waits runs out
+    // after `rounds` rounds
+    LBM_CK(c, batched_plan(c) ? enqueue_batched(c, c->cur, 2, 1, rounds) : enqueue_multi(c, c->cur, 2, 1, rounds));
     return LBM_OK;
 }
 
@@ -1678,7 +1791,7 @@ lbm_status lbm_sync(lbm_ctx* c) {
 
 lbm_status lbm_set_pipeline(lbm_ctx* c, int mode) {
     if (!c) return LBM_EINVAL;
-    if (mode < LBM_PIPELINE_AUTO || mode > LBM_PIPELINE_BATCHED)
+    if (mode < LBM_PIPELINE_AUTO || mode > LBM_PIPELINE_PERSISTENT)
         return fail(c, LBM_EINVAL, "pipeline mode must be one of LBM_PIPELINE_*");
     c->pipeline = mode;
     c->plan_dirty = true;

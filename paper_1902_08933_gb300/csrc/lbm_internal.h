@@ -42,6 +42,8 @@ struct WorkItem {
 // of up to 128 columns that two groups of 64 threads march side by side (an
 // unused entry is -1).
 constexpr int kDescWide = -2;
+// the persistent multi-step plan (step_kernel_x2_multi): neighbour items an item
+constexpr int kMaxNbr = 8;
 struct BlockDesc {
     int item[2];
 };
@@ -85,6 +87,7 @@ struct StepArgs {
     int* queue;
     int* done;
     const int* items_csr;
+    const int* nbr;        // persistent multi-step plan: kMaxNbr neighbour items per item, -1 padded
     long long set_delta;   // bytes from each *_in array to its *_out array (the same for all)
     int ninst;
     int nsteps;
@@ -141,6 +144,9 @@ template <int FORM> cudaError_t launch_step_t(int tile_x, const StepArgs& a, int
 template <int FORM> cudaError_t prepare_step_t();          // opt-in shared memory sizes
 template <int FORM> size_t step_smem_t(int tile_x);
 template <int FORM> int batched_occupancy_t();             // resident blocks per SM, batched kernel
+// several steps of a paired plan in one cooperative launch, and its residency
+template <int FORM> cudaError_t launch_multi_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s);
+template <int FORM> int multi_occupancy_t(int tile_x);
 template <int FORM> int step_occupancy_t(int tile_x, int variant);   // resident blocks per SM
 template <int FORM> bool has_tma_t();                      // the form has a TMA-fed kernel
 template <int FORM> bool has_async_t();                    // the form has the cp.async kernel

@@ -123,6 +123,9 @@ static cudaError_t prep_tx() {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(step_kernel_x2<FORM, TX, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X2Smem<FORM, TX>::bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(step_kernel_x2_multi<FORM, TX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X2Smem<FORM, TX>::bytes);
         }
     }
     return e;
@@ -154,6 +157,64 @@ int batched_occupancy_t() {
         return e == cudaSuccess ? n : 0;
     }
     return 0;
+}
+
+// Several steps of a paired plan in one cooperative launch (step_kernel_x2_multi):
+// nwork items = blocks, all resident (the caller checks multi_occupancy_t).
+template <int FORM, int TX>
+static cudaError_t launch_multi_tx(const StepArgs& a, int nwork, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nwork);
+    cfg.blockDim = dim3(TX);
+    cfg.dynamicSmemBytes = X2Smem<FORM, TX>::bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_kernel_x2_multi<FORM, TX>, a);
+}
+
+template <int FORM>
+cudaError_t launch_multi_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s) {
+    if constexpr (kHasTma<FORM>) {
+        if (nwork <= 0) return cudaSuccess;
+        if (a.nbr == nullptr || a.done == nullptr) return cudaErrorInvalidValue;
+        switch (tile_x) {
+            case 64: return launch_multi_tx<FORM, 32>(a, nwork, s);
+            case 128: return launch_multi_tx<FORM, 64>(a, nwork, s);
+            case 256: return launch_multi_tx<FORM, 128>(a, nwork, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// resident blocks per SM of the multi-step paired kernel for a strip width
+template <int FORM>
+int multi_occupancy_t(int tile_x) {
+    int n = 0;
+    if constexpr (kHasTma<FORM>) {
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (tile_x) {
+            case 64:
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_x2_multi<FORM, 32>, 32,
+                                                                  X2Smem<FORM, 32>::bytes);
+                break;
+            case 128:
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_x2_multi<FORM, 64>, 64,
+                                                                  X2Smem<FORM, 64>::bytes);
+                break;
+            case 256:
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_x2_multi<FORM, 128>, 128,
+                                                                  X2Smem<FORM, 128>::bytes);
+                break;
+            default: break;
+        }
+        if (e != cudaSuccess) n = 0;
+    }
+    return n;
 }
 
 template <int FORM>
@@ -254,6 +315,8 @@ cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h, do
     template cudaError_t prepare_step_t<F>();                                                 \
     template size_t step_smem_t<F>(int);                                                      \
     template int batched_occupancy_t<F>();                                                    \
+    template cudaError_t launch_multi_t<F>(int, const StepArgs&, int, cudaStream_t);          \
+    template int multi_occupancy_t<F>(int);                                                   \
     template int step_occupancy_t<F>(int, int);                                               \
     template bool has_tma_t<F>();                                                             \
     template bool has_async_t<F>();                                                           \

@@ -476,6 +476,73 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2(con
     x2_item<FORM, MON>(a, blockIdx.x, smem_raw, threadIdx.x, 0, 0, TX);
 }
 
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Several steps of one plan of work items in one persistent launch (the
+// LBM_PIPELINE_PERSISTENT plan of a context whose items all fit on the GPU at
+// once): block b owns work item b for every step, and before step s > 0 waits
+// only until each of its neighbour items (a.nbr[b * kMaxNbr ..], -1 padded:
+// the items whose rows and columns lie within the 3 rows and 2 columns one step
+// reads or writes around item b) has finished step s - 1, counted in a.done
+// (zeroed before the launch). Those are exactly the items that read what step
+// s of b overwrites and wrote what it reads, so no grid-wide step boundary is
+// needed; neighbours stay within one step of each other. The launch is
+// cooperative (every block resident), so every wait ends; each is bounded all
+// the same (a.wait_limit rounds): one that runs out records a timeout in the
+// status word, raises the abort flag a.done[a.ndesc] and the block leaves, as
+// do the blocks waiting on it. Odd steps read the other buffer set (swap).
+template <int FORM, int TX>
+__global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2_multi(const StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_bad;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    int* abort_flag = a.done + a.ndesc;
+    for (int s = 0; s < a.nsteps; ++s) {
+        if (s > 0) {
+            if (tid < 32) {
+                int ok = 1;
+                if (tid < kMaxNbr) {
+                    const int n = a.nbr[b * kMaxNbr + tid];
+                    if (n >= 0) {
+                        const int need = s + a.wait_extra;
+                        ok = 0;
+                        for (int it = 0; it < a.wait_limit; ++it) {
+                            if (ld_acquire_gpu(a.done + n) >= need) {
+                                ok = 1;
+                                break;
+                            }
+                            if (*reinterpret_cast<volatile int*>(abort_flag)) break;
+                            __nanosleep(64);
+                        }
+                        __threadfence();
+                    }
+                }
+                const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+                if (tid == 0) {
+                    if (bad) {
+                        atomicExch(a.status, kStatusTimeout);
+                        atomicExch(abort_flag, 1);
+                    }
+                    s_bad = bad != 0;
+                }
+            }
+            __syncthreads();
+            if (s_bad) return;
+        }
+        x2_item<FORM, false>(a, b, smem_raw, tid, 0, 0, TX, (s & 1) != 0);
+        __syncthreads();   // every thread's stores of step s issued
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.done + b, 1);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The batched step: every instance of a context, several steps, in one
 // persistent launch. Blocks of 128 threads take (step, block descriptor) pairs
@@ -508,12 +575,6 @@ struct X2Batched {
     static constexpr int by_smem = (int)((228u * 1024u) / (bytes + 1024u));
     static constexpr int occ = by_smem < 3 ? by_smem : 3;
 };
-
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 template <int FORM, bool MON = false>
 __global__ void __launch_bounds__(128, X2Batched<FORM>::occ) step_kernel_x2_batched(const StepArgs a) {

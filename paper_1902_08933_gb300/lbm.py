@@ -29,6 +29,7 @@ LBM_VISC_INV_LINEAR, LBM_VISC_STEP = 0, 1
 LBM_F64, LBM_F32, LBM_F32_G16, LBM_F32_H16, LBM_F32_C, LBM_F32_CC = 0, 1, 2, 3, 4, 5
 LBM_PIPELINE_AUTO, LBM_PIPELINE_PLAIN, LBM_PIPELINE_ASYNC, LBM_PIPELINE_TMA, LBM_PIPELINE_PAIRS = 0, 1, 2, 3, 4
 LBM_PIPELINE_BATCHED = 5
+LBM_PIPELINE_PERSISTENT = 6
 VARIANTS = {0: "plain", 1: "async", 2: "tma", 3: "pairs", 4: "batched"}
 FIELDS = ("phi", "ux", "uy", "p", "rho", "mu", "P")
 FIELDS3 = FIELDS + ("uz",)          # D3Q15 lattices (nz >= 2) also have uz
@@ -120,6 +121,7 @@ SIGNATURES = [
     ("lbm_pack_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t]),
     ("lbm_unpack_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t]),
     ("lbm_launches_per_step", ctypes.c_int, [_VP]),
+    ("lbm_step_launch_count", ctypes.c_longlong, [_VP]),
     ("lbm_time", ctypes.c_int64, [_VP, ctypes.c_int]),
     ("lbm_reduce_fields_noalloc", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     ("lbm_inject_wait_timeout", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -315,7 +317,7 @@ def lbm_unpack_rows(ctx, instance: int, y0: int, nrows: int, dev_ptr: int, nbyte
 
 
 LBM_TUNE_NO_CACHE = 1
-PIPELINES = {0: "auto", 1: "plain", 2: "async", 3: "tma", 4: "pairs", 5: "batched"}
+PIPELINES = {0: "auto", 1: "plain", 2: "async", 3: "tma", 4: "pairs", 5: "batched", 6: "persistent"}
 
 
 def lbm_autotune_shape(ctx, flags: int = 0) -> dict:
@@ -329,6 +331,11 @@ def lbm_autotune_shape(ctx, flags: int = 0) -> dict:
 
 def lbm_launches_per_step(ctx) -> int:
     return library().lbm_launches_per_step(ctx)
+
+
+def lbm_step_launch_count(ctx) -> int:
+    """Kernel launches the context's lbm_step calls have queued so far."""
+    return library().lbm_step_launch_count(ctx)
 
 
 def lbm_time(ctx, instance) -> int:
