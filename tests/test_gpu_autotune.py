@@ -58,7 +58,7 @@ def test_autotune_leaves_state_and_time_untouched(L):
         # thread or two in packed FP32)
         sim.step(6)
         tuned = [sim.populations(k) for k in range(2)]
-    pipes = {"auto": 0, "plain": 1, "async": 2, "tma": 3, "pairs": 4, "batched": 5}
+    pipes = {name: mode for mode, name in L.PIPELINES.items()}
     with L.Simulation(cfgs, "f32_c", phi0=[wl.initial_phi(c) for c in cfgs]) as ref:
         ref.step(13)
         L.lbm_set_monitor(ref.ctx, True)
