@@ -216,6 +216,18 @@ lbm_status lbm_read_monitor(lbm_ctx* ctx, int instance, lbm_monitor* out);
  * memory the device cannot write), LBM_ESTATE (monitor off), as lbm_step. */
 lbm_status lbm_step_monitored(lbm_ctx* ctx, int nsteps, lbm_monitor* host_records);
 
+/* lbm_step with the monitor's record of EVERY step written straight into caller
+ * memory: host_records holds nsteps x n_instances records (pinned host memory
+ * the device can write), record [k * n_instances + instance] that of step k of
+ * the call (time = lbm_time before the call + k). Under the persistent plan
+ * (LBM_PIPELINE_PERSISTENT) up to 64 steps run in one launch and the last
+ * block of each step to finish reduces that step's sums while the others are
+ * already on later steps, so the records cost little more than the sums;
+ * otherwise each step is a monitored launch as in lbm_step_monitored. The
+ * records are valid once the stream has passed the call; the last step's are
+ * kept for lbm_read_monitor. Errors: as lbm_step_monitored. */
+lbm_status lbm_step_monitored_all(lbm_ctx* ctx, int nsteps, lbm_monitor* host_records);
+
 /* As lbm_read_monitor without the wait: queues on the context's stream the copy
  * of the record into host_out (caller-owned; pinned memory, e.g. from
  * cudaMallocHost, keeps the copy asynchronous) and returns. The record is valid

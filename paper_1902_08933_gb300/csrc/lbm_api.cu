@@ -171,6 +171,8 @@ struct lbm_ctx {
     int graph_launches = 0;        // kernel nodes of the captured graph
     int* d_nbr = nullptr;          // persistent plan: neighbour items, kMaxNbr an item
     int* d_multi_done = nullptr;   // persistent plan: steps finished per item, then the abort flag
+    double* d_mon_multi = nullptr; // persistent plan, every step monitored: [64 steps][items][kMonQ] slots
+    int* d_mon_multi_cnt = nullptr;   // ... and [64 steps][instances] counters
     bool plan_dirty = true;
     // CUDA graph of 2 * graph_pairs steps starting from cur == 0 (built on first use,
     // dropped when the plan changes)
@@ -541,6 +543,9 @@ lbm_status plan_batched(lbm_ctx* c, bool, bool, bool, int sms) {
 // rows 2 ahead, pushes 1 row and 1 column out, the phi halo 2 columns). More
 // than kMaxNbr neighbours, or more items than resident blocks: no persistent
 // launch, the plan runs as PAIRS.
+// steps of one monitored persistent launch (slots and counters are kept per step)
+constexpr int kMultiSteps = 64;
+
 lbm_status plan_multi(lbm_ctx* c, int sms) {
     c->multi = false;
     if (c->d3 || c->pipeline != LBM_PIPELINE_PERSISTENT || c->launches.size() != 1 ||
@@ -584,6 +589,12 @@ lbm_status plan_multi(lbm_ctx* c, int sms) {
     c->d_nbr = nullptr;
     cudaFree(c->d_multi_done);
     c->d_multi_done = nullptr;
+    cudaFree(c->d_mon_multi);
+    c->d_mon_multi = nullptr;
+    cudaFree(c->d_mon_multi_cnt);
+    c->d_mon_multi_cnt = nullptr;
+    LBM_CK(c, cudaMalloc(&c->d_mon_multi, (size_t)kMultiSteps * L.count * lbm::kMonQ * sizeof(double)));
+    LBM_CK(c, cudaMalloc(&c->d_mon_multi_cnt, (size_t)kMultiSteps * c->n * sizeof(int)));
     LBM_CK(c, cudaMalloc(&c->d_nbr, nbr.size() * sizeof(int)));
     LBM_CK(c, cudaMemcpy(c->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
     LBM_CK(c, cudaMalloc(&c->d_multi_done, ((size_t)L.count + 1) * sizeof(int)));
@@ -752,6 +763,8 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_done);
     cudaFree(c->d_nbr);
     cudaFree(c->d_multi_done);
+    cudaFree(c->d_mon_multi);
+    cudaFree(c->d_mon_multi_cnt);
     cudaFree(c->d_tmp);
     cudaFree(c->d_out);
     cudaFree(c->d_partials);
@@ -1001,10 +1014,19 @@ bool multi_plan(const lbm_ctx* c) { return c->multi && !c->d3 && c->launches.siz
 // Queues `nsteps` steps of a persistent plan as one cooperative launch, the
 // first reading buffer set `in`, after zeroing the per-item step counters and
 // the abort flag; wait_extra / wait_limit as in StepArgs.
-cudaError_t enqueue_multi(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, int wait_limit = lbm::kWaitLimit) {
+// With host_records (device view of pinned host memory; nsteps <= 64) every
+// step's monitor record goes there, [step][instance] (the monitor must be on).
+cudaError_t enqueue_multi(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, int wait_limit = lbm::kWaitLimit,
+                          lbm::MonRecord* host_records = nullptr) {
     const auto& L = c->launches[0];
     cudaError_t e = cudaMemsetAsync(c->d_multi_done, 0, ((size_t)L.count + 1) * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
+    const bool monitor = host_records != nullptr;
+    if (monitor) {
+        if (nsteps > kMultiSteps || !c->d_mon) return cudaErrorInvalidValue;
+        e = cudaMemsetAsync(c->d_mon_multi_cnt, 0, (size_t)nsteps * c->n * sizeof(int), c->stream);
+        if (e != cudaSuccess) return e;
+    }
     StepArgs a = step_args(c, in);
     a.work = c->d_work + L.offset;
     a.nbr = c->d_nbr;
@@ -1013,8 +1035,18 @@ cudaError_t enqueue_multi(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, in
     a.nsteps = nsteps;
     a.wait_extra = wait_extra;
     a.wait_limit = wait_limit;
+    if (monitor) {
+        a.mon = c->d_mon_multi;
+        a.mon_count = c->d_mon_multi_cnt;
+        a.mon_csr = c->d_mon_csr;
+        a.mon_n = c->n;
+        a.mon_rec = reinterpret_cast<lbm::MonRecord*>(c->d_mon);
+        a.time_base = c->d_time_base;
+        a.mon_step = c->steps_total;
+        a.mon_host = host_records;
+    }
     return by_form(c->form, [&](auto F) {
-        return lbm::launch_multi_t<decltype(F)::value>(L.tx, a, L.count, c->stream);
+        return lbm::launch_multi_t<decltype(F)::value>(L.tx, a, L.count, c->stream, monitor);
     });
 }
 
@@ -1193,6 +1225,51 @@ lbm_status lbm_step_monitored(lbm_ctx* c, int nsteps, lbm_monitor* host_records)
     const lbm_status st = lbm_step(c, nsteps);
     c->mon_host_dev = nullptr;
     return st;
+}
+
+lbm_status lbm_step_monitored_all(lbm_ctx* c, int nsteps, lbm_monitor* host_records) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 1) return fail(c, LBM_EINVAL, "nsteps < 1");
+    if (!host_records) return fail(c, LBM_EINVAL, "host_records is NULL");
+    if (!c->monitor || !c->d_mon) return fail(c, LBM_ESTATE, "the per-step monitor is off (lbm_set_monitor)");
+    for (int k = 0; k < c->n; ++k)
+        if (!c->ready[k]) return fail(c, LBM_ESTATE, "instance not initialised");
+    LBM_CK(c, cudaSetDevice(c->device));
+    void* dptr = nullptr;
+    if (cudaHostGetDevicePointer(&dptr, host_records, 0) != cudaSuccess || !dptr) {
+        cudaGetLastError();
+        return fail(c, LBM_EINVAL, "host_records must be pinned host memory the device can write "
+                                   "(cudaMallocHost / cudaHostAlloc)");
+    }
+    lbm_status st = sticky(c);
+    if (st != LBM_OK) return st;
+    if (c->plan_dirty && (st = plan(c)) != LBM_OK) return st;
+    lbm::MonRecord* hd = static_cast<lbm::MonRecord*>(dptr);
+    for (int done = 0; done < nsteps;) {
+        if (multi_plan(c)) {   // up to 64 steps a launch, every step's record from it
+            const int k = std::min(nsteps - done, kMultiSteps);
+            cudaError_t e = enqueue_multi(c, c->cur, k, 0, lbm::kWaitLimit, hd + (long long)done * c->n);
+            if (e != cudaSuccess) return cuda_fail(c, e, "monitored step launch");
+            ++c->step_launches;
+            c->cur ^= k & 1;
+            c->steps_total += k;
+            done += k;
+        } else {   // one monitored step a launch
+            c->mon_host_dev = hd + (long long)done * c->n;
+            cudaError_t e = enqueue_step(c, c->cur, true, c->steps_total);
+            c->mon_host_dev = nullptr;
+            if (e != cudaSuccess) return cuda_fail(c, e, "monitored step launch");
+            c->step_launches += step_kernels(c);
+            c->cur ^= 1;
+            ++c->steps_total;
+            ++done;
+        }
+    }
+    for (int k = 0; k < c->n; ++k) {
+        c->time[k] += nsteps;
+        c->mon_time[k] = c->time[k] - 1;
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_set_monitor(lbm_ctx* c, int enable) {

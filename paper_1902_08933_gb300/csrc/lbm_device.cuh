@@ -680,6 +680,61 @@ __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const Step
     }
 }
 
+// Monitor of every step of a persistent launch (step_kernel_x2_multi with the
+// record of each step): the group reduces its item's sums of step s into slot
+// a.mon[(s * a.ndesc + item) * kMonQ] and counts itself in the (step,
+// instance) counter a.mon_count[s * a.mon_n + inst] (zeroed before the launch);
+// the last of the instance's items of that step adds all of its slots in the
+// order of the instance's item list (each thread a fixed subset, then the
+// group's fixed tree) and writes the record of step s: into
+// a.mon_host[s * a.mon_n + inst] (the caller's pinned host records) and, for the
+// launch's last step, a.mon_rec[inst]. Steps of a persistent launch overlap, so
+// this runs while other blocks are already on later steps.
+template <typename R>
+__device__ __forceinline__ void mon_step_store(const MonAcc<R>& acc, const StepArgs& a, int inst, int item,
+                                               int tid, int nthr, int bar, int grp, int s) {
+    __shared__ double sred_all[4][4][8];
+    __shared__ int sflag_all[4];
+    double (*red)[8] = sred_all[grp];
+    int& flag = sflag_all[grp];
+    double v[4];
+    acc.result(v[0], v[1], v[2]);
+    v[3] = 0.0;
+    group_reduce4(v, tid, nthr, bar, red);
+    const int* idx = a.mon_csr + a.mon_n + 1;
+    const int first = a.mon_csr[inst], items = a.mon_csr[inst + 1] - first;
+    if (tid == 0) {
+        double* out = a.mon + ((long long)s * a.ndesc + item) * kMonQ;
+        out[0] = v[0];
+        out[1] = v[1];
+        out[2] = v[2];
+        out[3] = (isfinite(v[0]) && isfinite(v[1])) ? 0.0 : 1.0;
+        flag = atom_add_acq_rel_gpu(a.mon_count + (long long)s * a.mon_n + inst, 1) == items - 1;
+    }
+    group_sync(bar, nthr);
+    if (!flag) return;
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < items; j += nthr) {
+        const double* p = a.mon + ((long long)s * a.ndesc + idx[first + j]) * kMonQ;
+        w[0] += __ldcg(p);
+        w[1] += __ldcg(p + 1);
+        w[2] = fmax(w[2], __ldcg(p + 2));
+        w[3] += __ldcg(p + 3);
+    }
+    group_reduce4(w, tid, nthr, bar, red);
+    if (tid == 0) {
+        MonRecord r;
+        r.sum_phi = w[0];
+        r.kinetic_energy = w[1];
+        r.max_u = sqrt(w[2]);
+        r.nonfinite = w[3] != 0.0 ? 1 : 0;
+        r.device_status = *(volatile int*)a.status;
+        r.time = a.mon_step + s + a.time_base[inst];
+        if (s == a.nsteps - 1) a.mon_rec[inst] = r;
+        if (a.mon_host) a.mon_host[(long long)s * a.mon_n + inst] = r;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The fused step kernel. Rings in shared memory (slots by row number, powers of
 // two so a slot is one AND):

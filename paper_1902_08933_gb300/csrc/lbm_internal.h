@@ -145,7 +145,8 @@ template <int FORM> cudaError_t prepare_step_t();          // opt-in shared memo
 template <int FORM> size_t step_smem_t(int tile_x);
 template <int FORM> int batched_occupancy_t();             // resident blocks per SM, batched kernel
 // several steps of a paired plan in one cooperative launch, and its residency
-template <int FORM> cudaError_t launch_multi_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s);
+template <int FORM> cudaError_t launch_multi_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s,
+                                               bool monitor);
 template <int FORM> int multi_occupancy_t(int tile_x);
 template <int FORM> int step_occupancy_t(int tile_x, int variant);   // resident blocks per SM
 template <int FORM> bool has_tma_t();                      // the form has a TMA-fed kernel

@@ -126,6 +126,9 @@ static cudaError_t prep_tx() {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(step_kernel_x2_multi<FORM, TX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X2Smem<FORM, TX>::bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(step_kernel_x2_multi<FORM, TX, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X2Smem<FORM, TX>::bytes);
         }
     }
     return e;
@@ -162,7 +165,7 @@ int batched_occupancy_t() {
 // Several steps of a paired plan in one cooperative launch (step_kernel_x2_multi):
 // nwork items = blocks, all resident (the caller checks multi_occupancy_t).
 template <int FORM, int TX>
-static cudaError_t launch_multi_tx(const StepArgs& a, int nwork, cudaStream_t s) {
+static cudaError_t launch_multi_tx(const StepArgs& a, int nwork, cudaStream_t s, bool monitor) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nwork);
     cfg.blockDim = dim3(TX);
@@ -173,18 +176,20 @@ static cudaError_t launch_multi_tx(const StepArgs& a, int nwork, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (monitor) return cudaLaunchKernelEx(&cfg, step_kernel_x2_multi<FORM, TX, true>, a);
     return cudaLaunchKernelEx(&cfg, step_kernel_x2_multi<FORM, TX>, a);
 }
 
 template <int FORM>
-cudaError_t launch_multi_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s) {
+cudaError_t launch_multi_t(int tile_x, const StepArgs& a, int nwork, cudaStream_t s, bool monitor) {
     if constexpr (kHasTma<FORM>) {
         if (nwork <= 0) return cudaSuccess;
         if (a.nbr == nullptr || a.done == nullptr) return cudaErrorInvalidValue;
+        if (monitor && (a.mon == nullptr || a.mon_count == nullptr || a.mon_csr == nullptr)) return cudaErrorInvalidValue;
         switch (tile_x) {
-            case 64: return launch_multi_tx<FORM, 32>(a, nwork, s);
-            case 128: return launch_multi_tx<FORM, 64>(a, nwork, s);
-            case 256: return launch_multi_tx<FORM, 128>(a, nwork, s);
+            case 64: return launch_multi_tx<FORM, 32>(a, nwork, s, monitor);
+            case 128: return launch_multi_tx<FORM, 64>(a, nwork, s, monitor);
+            case 256: return launch_multi_tx<FORM, 128>(a, nwork, s, monitor);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -315,7 +320,7 @@ cudaError_t launch_populations_t(const AuxArgs& a, int ncells, double* out_h, do
     template cudaError_t prepare_step_t<F>();                                                 \
     template size_t step_smem_t<F>(int);                                                      \
     template int batched_occupancy_t<F>();                                                    \
-    template cudaError_t launch_multi_t<F>(int, const StepArgs&, int, cudaStream_t);          \
+    template cudaError_t launch_multi_t<F>(int, const StepArgs&, int, cudaStream_t, bool);    \
     template int multi_occupancy_t<F>(int);                                                   \
     template int step_occupancy_t<F>(int, int);                                               \
     template bool has_tma_t<F>();                                                             \

@@ -87,9 +87,10 @@ struct X2Occ {
 // tid the thread's index in the group, item the work item's index in
 // StepArgs::work (and of its monitor slot); swap: the step reads the *_out
 // buffers of a and writes the *_in ones (odd steps of a batched launch).
-template <int FORM, bool MON>
+template <int FORM, int MON>
 __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned char* smem_raw, int tid,
-                                        int bar, int grp, const int TX, const bool swap = false) {
+                                        int bar, int grp, const int TX, const bool swap = false,
+                                        const int step = 0) {
     using F = Form<FORM>;
     using HT = typename F::HT;
     using GT = typename F::GT;
@@ -467,7 +468,8 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
         group_sync(bar, TX);
         collide_row(Y, g, pux, puy);
     }
-    if constexpr (MON) mon_block_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp);
+    if constexpr (MON == 1) mon_block_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp);
+    if constexpr (MON == 2) mon_step_store(mon, a, wk.inst, item, tid, TX, bar, grp, step);
 }
 
 template <int FORM, int TX, bool MON = false>
@@ -496,7 +498,8 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
 // the same (a.wait_limit rounds): one that runs out records a timeout in the
 // status word, raises the abort flag a.done[a.ndesc] and the block leaves, as
 // do the blocks waiting on it. Odd steps read the other buffer set (swap).
-template <int FORM, int TX>
+// MON: every step's monitor record as well (mon_step_store).
+template <int FORM, int TX, bool MON = false>
 __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2_multi(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_bad;
@@ -534,7 +537,7 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2_mul
             __syncthreads();
             if (s_bad) return;
         }
-        x2_item<FORM, false>(a, b, smem_raw, tid, 0, 0, TX, (s & 1) != 0);
+        x2_item<FORM, MON ? 2 : 0>(a, b, smem_raw, tid, 0, 0, TX, (s & 1) != 0, s);
         __syncthreads();   // every thread's stores of step s issued
         if (tid == 0) {
             __threadfence();

@@ -103,6 +103,7 @@ SIGNATURES = [
     ("lbm_read_monitor", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_monitor)]),
     ("lbm_read_monitor_async", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     ("lbm_step_monitored", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("lbm_step_monitored_all", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     ("lbm_get_fields", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _DP]),
     ("lbm_get_fields_device", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint, _VP]),
     ("lbm_diagnostics", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_diag)]),
@@ -224,6 +225,13 @@ def lbm_step_monitored(ctx, nsteps: int, host_records_ptr: int):
     """lbm_step whose monitored last step writes the records (one lbm_monitor per
     instance) into pinned host memory at host_records_ptr, from the GPU."""
     _check(library().lbm_step_monitored(ctx, int(nsteps), _VP(host_records_ptr)), ctx)
+
+
+def lbm_step_monitored_all(ctx, nsteps: int, host_records_ptr: int):
+    """lbm_step writing the record of every step (nsteps x instances lbm_monitor
+    records, [step][instance]) into pinned host memory at host_records_ptr, from
+    the GPU."""
+    _check(library().lbm_step_monitored_all(ctx, int(nsteps), _VP(host_records_ptr)), ctx)
 
 
 def lbm_read_monitor_async(ctx, instance: int, host_record_ptr: int):

@@ -85,3 +85,43 @@ def test_persistent_wait_timeout_is_reported_and_checkpoint_recovers(L, tmp_path
         sim.step(20)
         for a, b in zip(sim.populations(0), expected):
             np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode", ["PERSISTENT", "PAIRS"])
+def test_every_step_record(L, mode):
+    # lbm_step_monitored_all: the record of every step, [step][instance], written
+    # from the GPU -- inside the persistent launch (steps overlapping) or one
+    # monitored launch a step. Each record is the step's input level: it equals
+    # the diagnostics of an unmonitored run stopped there (to the rounding of a
+    # different summation order), and monitoring leaves the state bit for bit.
+    import ctypes
+    import torch
+    cfg = wl.rising_bubble(nx=256, ny=144, R=18, cy=48, W=4.0, Re=8.0)
+    phi0 = wl.initial_phi(cfg)
+    cells = cfg["nx"] * cfg["ny"]
+    size = ctypes.sizeof(L.lbm_monitor)
+    nsteps = 70                                      # more than one launch of 64
+    buf = torch.zeros(nsteps * size, dtype=torch.uint8).pin_memory()
+    with L.Simulation([cfg], "f32_c", phi0=[phi0]) as sim, L.Simulation([cfg], "f32_c", phi0=[phi0]) as ref:
+        for s in (sim, ref):
+            L.lbm_set_pipeline(s.ctx, getattr(L, "LBM_PIPELINE_" + mode))
+        sim.step(5)
+        ref.step(5)
+        L.lbm_set_monitor(sim.ctx, True)
+        L.lbm_step_monitored_all(sim.ctx, nsteps, buf.data_ptr())
+        sim.sync()
+        for k in range(nsteps):
+            r = L.lbm_monitor.from_address(buf.data_ptr() + k * size)
+            d = ref.diagnostics(0)
+            assert r.time == 5 + k and r.nonfinite == 0 and r.device_status == 0, (k, r.time)
+            # the bars of the monitor against the diagnostics for the FP32 forms
+            # (the diagnostics recompute u in FP64 from the stored state)
+            assert abs(r.sum_phi - d["sum_phi"]) <= cells * 2.0 ** -24, k
+            assert abs(r.kinetic_energy - d["kinetic_energy"]) <= 1e-4 * d["kinetic_energy"], k
+            assert abs(r.max_u - d["max_u"]) <= 1e-4 * d["max_u"], k
+            ref.step(1)
+        m = L.lbm_read_monitor(sim.ctx, 0)
+        last = L.lbm_monitor.from_address(buf.data_ptr() + (nsteps - 1) * size)
+        assert m["time"] == last.time and m["sum_phi"] == last.sum_phi
+        for a, b in zip(sim.populations(0), ref.populations(0)):
+            assert np.array_equal(a, b)
