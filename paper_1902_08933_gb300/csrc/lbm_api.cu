@@ -172,7 +172,8 @@ struct lbm_ctx {
     int* d_nbr = nullptr;          // persistent plan: neighbour items, kMaxNbr an item
     int* d_multi_done = nullptr;   // persistent plan: steps finished per item, then the abort flag
     double* d_mon_multi = nullptr; // persistent plan, every step monitored: [64 steps][items][kMonQ] slots
-    int* d_mon_multi_cnt = nullptr;   // ... and [64 steps][instances] counters
+    int* d_mon_multi_cnt = nullptr;   // ... [64 steps][instances][kMonSub + 1] counters
+    double* d_mon_multi_sub = nullptr;  // ... and [64 steps][instances][kMonSub][kMonQ] sub-group slots
     bool plan_dirty = true;
     // CUDA graph of 2 * graph_pairs steps starting from cur == 0 (built on first use,
     // dropped when the plan changes)
@@ -593,8 +594,12 @@ lbm_status plan_multi(lbm_ctx* c, int sms) {
     c->d_mon_multi = nullptr;
     cudaFree(c->d_mon_multi_cnt);
     c->d_mon_multi_cnt = nullptr;
+    cudaFree(c->d_mon_multi_sub);
+    c->d_mon_multi_sub = nullptr;
     LBM_CK(c, cudaMalloc(&c->d_mon_multi, (size_t)kMultiSteps * L.count * lbm::kMonQ * sizeof(double)));
-    LBM_CK(c, cudaMalloc(&c->d_mon_multi_cnt, (size_t)kMultiSteps * c->n * sizeof(int)));
+    LBM_CK(c, cudaMalloc(&c->d_mon_multi_cnt, (size_t)kMultiSteps * c->n * (lbm::kMonSub + 1) * sizeof(int)));
+    LBM_CK(c, cudaMalloc(&c->d_mon_multi_sub,
+                         (size_t)kMultiSteps * c->n * lbm::kMonSub * lbm::kMonQ * sizeof(double)));
     LBM_CK(c, cudaMalloc(&c->d_nbr, nbr.size() * sizeof(int)));
     LBM_CK(c, cudaMemcpy(c->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
     LBM_CK(c, cudaMalloc(&c->d_multi_done, ((size_t)L.count + 1) * sizeof(int)));
@@ -765,6 +770,7 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_multi_done);
     cudaFree(c->d_mon_multi);
     cudaFree(c->d_mon_multi_cnt);
+    cudaFree(c->d_mon_multi_sub);
     cudaFree(c->d_tmp);
     cudaFree(c->d_out);
     cudaFree(c->d_partials);
@@ -1024,7 +1030,8 @@ cudaError_t enqueue_multi(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, in
     const bool monitor = host_records != nullptr;
     if (monitor) {
         if (nsteps > kMultiSteps || !c->d_mon) return cudaErrorInvalidValue;
-        e = cudaMemsetAsync(c->d_mon_multi_cnt, 0, (size_t)nsteps * c->n * sizeof(int), c->stream);
+        e = cudaMemsetAsync(c->d_mon_multi_cnt, 0, (size_t)nsteps * c->n * (lbm::kMonSub + 1) * sizeof(int),
+                            c->stream);
         if (e != cudaSuccess) return e;
     }
     StepArgs a = step_args(c, in);
@@ -1037,6 +1044,7 @@ cudaError_t enqueue_multi(lbm_ctx* c, int in, int nsteps, int wait_extra = 0, in
     a.wait_limit = wait_limit;
     if (monitor) {
         a.mon = c->d_mon_multi;
+        a.mon_sub = c->d_mon_multi_sub;
         a.mon_count = c->d_mon_multi_cnt;
         a.mon_csr = c->d_mon_csr;
         a.mon_n = c->n;

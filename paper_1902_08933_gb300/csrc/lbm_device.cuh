@@ -681,18 +681,22 @@ __device__ __forceinline__ void mon_block_store(const MonAcc<R>& acc, const Step
 }
 
 // Monitor of every step of a persistent launch (step_kernel_x2_multi with the
-// record of each step): the group reduces its item's sums of step s into slot
-// a.mon[(s * a.ndesc + item) * kMonQ] and counts itself in the (step,
-// instance) counter a.mon_count[s * a.mon_n + inst] (zeroed before the launch);
-// the last of the instance's items of that step adds all of its slots in the
-// order of the instance's item list (each thread a fixed subset, then the
-// group's fixed tree) and writes the record of step s: into
-// a.mon_host[s * a.mon_n + inst] (the caller's pinned host records) and, for the
-// launch's last step, a.mon_rec[inst]. Steps of a persistent launch overlap, so
-// this runs while other blocks are already on later steps.
+// record of each step), the two-level tree of mon_block_store kept per step s
+// of the launch: the group reduces its item's sums into slot
+// a.mon[(s * a.ndesc + item) * kMonQ] and counts itself in its sub-group's
+// counter (sub-group = its position pos within the instance's items modulo
+// kMonSub; counters a.mon_count[(s * a.mon_n + inst) * (kMonSub + 1) + ...],
+// zeroed before the launch); the last of a sub-group adds the sub-group's slots
+// in order into a.mon_sub[((s * a.mon_n + inst) * kMonSub + sub) * kMonQ] and
+// counts itself at the instance level; the last of those adds the sub-group
+// slots in order and writes the record of step s: into a.mon_host[s * a.mon_n +
+// inst] (the caller's pinned host records) and, for the launch's last step,
+// a.mon_rec[inst]. Steps of a persistent launch overlap, so this runs while
+// other blocks are on later steps; the two levels keep the work of the block
+// that finishes a step last short, since its neighbours wait for it.
 template <typename R>
 __device__ __forceinline__ void mon_step_store(const MonAcc<R>& acc, const StepArgs& a, int inst, int item,
-                                               int tid, int nthr, int bar, int grp, int s) {
+                                               int pos, int tid, int nthr, int bar, int grp, int s) {
     __shared__ double sred_all[4][4][8];
     __shared__ int sflag_all[4];
     double (*red)[8] = sred_all[grp];
@@ -703,35 +707,68 @@ __device__ __forceinline__ void mon_step_store(const MonAcc<R>& acc, const StepA
     group_reduce4(v, tid, nthr, bar, red);
     const int* idx = a.mon_csr + a.mon_n + 1;
     const int first = a.mon_csr[inst], items = a.mon_csr[inst + 1] - first;
+    const int nsub = items < kMonSub ? items : kMonSub;
+    const int sg = pos % kMonSub;
+    const int in_sub = (items - sg + kMonSub - 1) / kMonSub;   // positions sg, sg + kMonSub, ...
+    const long long si = (long long)s * a.mon_n + inst;
+    int* cnt = a.mon_count + si * (kMonSub + 1);
+    double* slot = a.mon + (long long)s * a.ndesc * kMonQ;
     if (tid == 0) {
-        double* out = a.mon + ((long long)s * a.ndesc + item) * kMonQ;
+        double* out = slot + (long long)item * kMonQ;
         out[0] = v[0];
         out[1] = v[1];
         out[2] = v[2];
         out[3] = (isfinite(v[0]) && isfinite(v[1])) ? 0.0 : 1.0;
-        flag = atom_add_acq_rel_gpu(a.mon_count + (long long)s * a.mon_n + inst, 1) == items - 1;
+        flag = atom_add_acq_rel_gpu(cnt + sg, 1) == in_sub - 1;
     }
     group_sync(bar, nthr);
     if (!flag) return;
     double w[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < items; j += nthr) {
-        const double* p = a.mon + ((long long)s * a.ndesc + idx[first + j]) * kMonQ;
+    for (int j = tid; j < in_sub; j += nthr) {
+        const double* p = slot + (long long)idx[first + sg + j * kMonSub] * kMonQ;
         w[0] += __ldcg(p);
         w[1] += __ldcg(p + 1);
         w[2] = fmax(w[2], __ldcg(p + 2));
         w[3] += __ldcg(p + 3);
     }
     group_reduce4(w, tid, nthr, bar, red);
+    double* subs = a.mon_sub + si * kMonSub * kMonQ;
+    if (tid == 0) {
+        double* sub = subs + sg * kMonQ;
+        sub[0] = w[0];
+        sub[1] = w[1];
+        sub[2] = w[2];
+        sub[3] = w[3];
+        flag = atom_add_acq_rel_gpu(cnt + kMonSub, 1) == nsub - 1;
+    }
+    group_sync(bar, nthr);   // (every thread read the first flag before group_reduce4's barriers)
+    if (!flag || tid >= 32) return;
+    // the record from the sub-group slots: lane q < nsub loads slot q, lane 0
+    // adds them in order q = 0, 1, ...
+    double sv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (tid < nsub) {
+        sv[0] = __ldcg(subs + tid * kMonQ);
+        sv[1] = __ldcg(subs + tid * kMonQ + 1);
+        sv[2] = __ldcg(subs + tid * kMonQ + 2);
+        sv[3] = __ldcg(subs + tid * kMonQ + 3);
+    }
+    double m = 0.0, e = 0.0, u = 0.0, f = 0.0;
+    for (int q = 0; q < nsub; ++q) {
+        m += __shfl_sync(0xffffffffu, sv[0], q);
+        e += __shfl_sync(0xffffffffu, sv[1], q);
+        u = fmax(u, __shfl_sync(0xffffffffu, sv[2], q));
+        f += __shfl_sync(0xffffffffu, sv[3], q);
+    }
     if (tid == 0) {
         MonRecord r;
-        r.sum_phi = w[0];
-        r.kinetic_energy = w[1];
-        r.max_u = sqrt(w[2]);
-        r.nonfinite = w[3] != 0.0 ? 1 : 0;
+        r.sum_phi = m;
+        r.kinetic_energy = e;
+        r.max_u = sqrt(u);
+        r.nonfinite = f != 0.0 ? 1 : 0;
         r.device_status = *(volatile int*)a.status;
         r.time = a.mon_step + s + a.time_base[inst];
         if (s == a.nsteps - 1) a.mon_rec[inst] = r;
-        if (a.mon_host) a.mon_host[(long long)s * a.mon_n + inst] = r;
+        if (a.mon_host) a.mon_host[si] = r;
     }
 }
 

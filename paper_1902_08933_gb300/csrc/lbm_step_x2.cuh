@@ -469,7 +469,7 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
         collide_row(Y, g, pux, puy);
     }
     if constexpr (MON == 1) mon_block_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp);
-    if constexpr (MON == 2) mon_step_store(mon, a, wk.inst, item, tid, TX, bar, grp, step);
+    if constexpr (MON == 2) mon_step_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp, step);
 }
 
 template <int FORM, int TX, bool MON = false>
