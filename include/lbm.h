@@ -377,12 +377,14 @@ typedef struct lbm_launch_shape {
 enum { LBM_TUNE_NO_CACHE = 1 };
 
 /* Autotuner. Times, on the context's current state, every distinct plan among
- * load paths (LBM_PIPELINE_PAIRS, BATCHED, PLAIN, ASYNC, TMA -- i.e. one or two
- * cells per thread, one launch per strip width or one for the whole context)
- * x strip widths {built-in, 64, 128, 256} x run lengths {built-in, 8, 16, 32,
- * 64}, the built-in plan (AUTO, 0, 0) first; plans that launch the same work
- * are timed once (two warm-up steps, then the best of two 8-step timings with
- * CUDA events). Keeps the fastest (lbm_set_pipeline / lbm_set_launch) and
+ * load paths (LBM_PIPELINE_PAIRS, PERSISTENT, BATCHED, PLAIN, ASYNC, TMA --
+ * i.e. one or two cells per thread, one launch per strip width or one for the
+ * whole context, one step or several a launch) x strip widths {built-in, 64,
+ * 128, 256} x run lengths {built-in, 8, 16, 32, 64}, the built-in plan (AUTO,
+ * 0, 0) first; plans that launch the same work are timed once (from buffer
+ * parity 0, a warm-up that captures the plan's graph, then the best of three
+ * timings with CUDA events over one replay of that graph -- at least 8 steps --
+ * the way lbm_step runs long step counts). Keeps the fastest (lbm_set_pipeline / lbm_set_launch) and
  * stores it in a process-wide cache keyed by device, storage form and the
  * instances' sizes and boundaries, which later calls on a context of the same
  * key use without trials (flags = LBM_TUNE_NO_CACHE forces the trials). The

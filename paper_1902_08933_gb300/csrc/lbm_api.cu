@@ -1723,7 +1723,7 @@ lbm_status lbm_autotune_shape(lbm_ctx* c, int flags, lbm_launch_shape* out) {
         if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
         seen.push_back(sig);
         ++trials;
-        // warm-up (captures the graph of this plan), then the best of two timings
+        // warm-up (captures the graph of this plan), then the best of three timings
         // of whole graph replays from buffer parity 0 -- the way lbm_step runs long
         // step counts: a plan of several launch classes runs them as concurrent
         // graph branches there, one after the other in direct launches
@@ -1731,7 +1731,7 @@ lbm_status lbm_autotune_shape(lbm_ctx* c, int flags, lbm_launch_shape* out) {
         if ((st = lbm_step(c, 2)) != LBM_OK) break;
         const int nt = std::max(8, c->use_graphs && c->graph ? c->graph_steps : 0);
         float ms = 1e30f;
-        for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {
+        for (int rep = 0; rep < 3 && st == LBM_OK; ++rep) {
             cudaEventRecord(e0, c->stream);
             st = lbm_step(c, nt);
             cudaEventRecord(e1, c->stream);
