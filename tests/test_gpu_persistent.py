@@ -26,9 +26,13 @@ def L():
 
 def cases():
     # walls with a ragged last strip and runs of both directions; periodic in
-    # both directions (wrap of the neighbour lists in x and y)
+    # both directions (wrap of the neighbour lists in x and y); tiny grids, where
+    # a single strip's few short runs are each other's neighbours across the
+    # periodic seam, or a walled strip has just two runs
     return [(wl.rising_bubble(nx=300, ny=170, R=20, cy=55, W=4.0, Re=8.0), 31),
-            (wl.static_droplet(n=128, R=30), 23)]
+            (wl.static_droplet(n=128, R=30), 23),
+            (wl.static_droplet(n=32, R=8.0), 17),
+            (wl.rising_bubble(nx=64, ny=20, R=5.0, cy=7.0, W=4.0, Re=5.0), 19)]
 
 
 def run(L, cfg, form, mode, steps, graphs=True, rows=0):
