@@ -469,7 +469,17 @@ __device__ __forceinline__ void x2_item(const StepArgs& a, int item, unsigned ch
         collide_row(Y, g, pux, puy);
     }
     if constexpr (MON == 1) mon_block_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp);
-    if constexpr (MON == 2) mon_step_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp, step);
+    if constexpr (MON == 2) {
+        // persistent launch: publish this item's step first (the monitor's tree
+        // reads only the monitor buffers), so the neighbour items' next step
+        // need not wait for the reduction
+        group_sync(bar, TX);
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.done + item, 1);
+        }
+        mon_step_store(mon, a, wk.inst, item, wk.pad, tid, TX, bar, grp, step);
+    }
 }
 
 template <int FORM, int TX, bool MON = false>
@@ -539,7 +549,7 @@ __global__ void __launch_bounds__(TX, X2Occ<FORM, TX>::value) step_kernel_x2_mul
         }
         x2_item<FORM, MON ? 2 : 0>(a, b, smem_raw, tid, 0, 0, TX, (s & 1) != 0, s);
         __syncthreads();   // every thread's stores of step s issued
-        if (tid == 0) {
+        if (!MON && tid == 0) {   // (the monitored item publishes itself, before its monitor tree)
             __threadfence();
             atomicAdd(a.done + b, 1);
         }
